@@ -1,0 +1,390 @@
+"""Pins for the FP64 oracle: each test checks it against something other than itself.
+
+* the matrices the paper prints (golden fixtures under tests/golden/);
+* the Appendix listing, restated with ``scipy.signal.convolve2d`` (a library 2-D convolution
+  with MATLAB's conv2 'same' semantics) and numpy's first-index argmin;
+* closed forms derived by hand from the Sec. IV-B kernels (affine ramps, the paraboloid x^2,
+  impulses, step edges, a square);
+* exact invariants (contrast, D4 symmetry, the max principle of the explicit update);
+* a scalar recursion worked by hand for the primal-dual update of Sec. V-C;
+* numpy's float16 rounding for the storage emulation.
+"""
+from fractions import Fraction
+import os
+
+import numpy as np
+import pytest
+from scipy.signal import convolve2d, correlate2d
+
+import oracle
+from paper_1903_07189_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_blocks(name):
+    """Parse a golden kernel file into {name: (rows of Fractions, denominator)}."""
+    blocks, cur, rows, den = {}, None, [], 1
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("/"):
+                den = int(line[1:])
+                continue
+            parts = line.split()
+            if len(parts) == 1 and not parts[0].lstrip("-").replace("/", "").isdigit():
+                if cur is not None:
+                    blocks[cur] = (rows, den)
+                cur, rows, den = parts[0], [], 1
+            else:
+                rows.append([Fraction(p) for p in parts])
+    blocks[cur] = (rows, den)
+    return {k: np.array([[float(v) / d for v in r] for r in rows]) for k, (rows, d) in blocks.items()}
+
+
+PRINTED = _read_blocks("kernels_h1_h8.txt")
+APPENDIX = _read_blocks("appendix_k1_k2.txt")
+K4 = _read_blocks("laplace_k4.txt")["k4"]
+
+
+# ---------------------------------------------------------------- kernel table (Sec. IV-B)
+def test_printed_kernels_shape():
+    """Each printed h_i: centre -1, off-centre weights >= 0 summing to 1, six taps (Sec. IV-D)."""
+    for i in range(1, 9):
+        k = PRINTED[f"h{i}"]
+        assert k[1, 1] == -1.0
+        off = k.copy()
+        off[1, 1] = 0
+        assert (off >= 0).all()
+        assert abs(off.sum() - 1.0) < 1e-15
+        assert np.count_nonzero(k) == 6
+
+
+def test_oracle_kernel_table_is_the_printed_one():
+    for i in range(8):
+        np.testing.assert_allclose(oracle.kernel(i), PRINTED[f"h{i + 1}"], rtol=0, atol=1e-16)
+
+
+def test_antipodal_kernels_average_to_k4():
+    """h1+h3 = h2+h4 = h5+h7 = h6+h8 = 2*k4 (k4 of Eq. kernel3)."""
+    for a, b in [(1, 3), (2, 4), (5, 7), (6, 8)]:
+        np.testing.assert_allclose(PRINTED[f"h{a}"] + PRINTED[f"h{b}"], 2 * K4, atol=1e-15)
+        np.testing.assert_allclose(oracle.kernel(a - 1) + oracle.kernel(b - 1), 2 * K4, atol=1e-15)
+
+
+# ------------------------------------------------- the Appendix listing, via scipy's conv2
+def _appendix_wmc(u, boundary):
+    """Restatement of the Appendix function with a library convolution.
+
+    The kernels are scaled to integers (x12) so that integer images are evaluated exactly;
+    the listing's order of the eight convolutions and its first-minimum rule are kept.
+    """
+    k1 = APPENDIX["k1"] * 12
+    k2 = APPENDIX["k2"] * 12
+    ks = [k1, np.fliplr(k1), k1.T, np.flipud(k1.T), k2, np.fliplr(k2), np.flipud(k2), np.rot90(k2, 2)]
+    if boundary == "zero":
+        dist = np.stack([convolve2d(u, k, mode="same", boundary="fill", fillvalue=0) for k in ks], -1)
+    else:
+        up = np.pad(u, 1, mode="edge")
+        dist = np.stack([convolve2d(up, k, mode="valid") for k in ks], -1)
+    ind = np.argmin(np.abs(dist), axis=-1)  # first minimum, like MATLAB's min
+    return np.take_along_axis(dist, ind[..., None], -1)[..., 0] / 12.0, dist / 12.0
+
+
+@pytest.mark.parametrize("boundary", ["zero", "replicate"])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (6, 1), (2, 2), (5, 5), (13, 17), (32, 24)])
+def test_matches_appendix_on_integer_images(boundary, shape):
+    """Integer images: both sides are exact, so values and tie choices must agree bit for bit."""
+    rng = np.random.default_rng(hash(shape) % 2**32)
+    for trial in range(4):
+        hi = [2, 5, 50, 1000][trial]
+        u = rng.integers(-hi, hi + 1, size=shape).astype(np.float64)
+        want, _ = _appendix_wmc(u, boundary)
+        got = oracle.wmc_eval(u, boundary)
+        assert np.array_equal(got, want), (boundary, shape, hi)
+
+
+@pytest.mark.parametrize("boundary", ["zero", "replicate"])
+def test_matches_appendix_on_real_images(boundary):
+    """Real-valued images: same candidate sets; the same value wherever the minimum is clear."""
+    u = synth.make_image(40, 56, seed=7, sigma=0.05).astype(np.float64)
+    want, dist = _appendix_wmc(u, boundary)
+    got, cand, _ = oracle.wmc_eval(u, boundary, candidates=True)
+    np.testing.assert_allclose(np.sort(cand, -1), np.sort(dist, -1), rtol=0, atol=1e-14)
+    mags = np.sort(np.abs(dist), -1)
+    clear = (mags[..., 1] - mags[..., 0]) > 1e-12
+    assert clear.mean() > 0.99
+    np.testing.assert_allclose(got[clear], want[clear], rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------------------- closed forms, derived by hand
+def test_affine_candidates_closed_form():
+    """U = a x + b y + c (x = column, y = row): interior d_1..d_8 =
+    -2a/3, -2b/3, 2a/3, 2b/3, -(a+b)/2, (a-b)/2, (a+b)/2, -(a-b)/2."""
+    rng = np.random.default_rng(1)
+    y, x = np.mgrid[0:9, 0:11].astype(np.float64)
+    for _ in range(20):
+        a, b, c = rng.normal(size=3)
+        u = a * x + b * y + c
+        _, cand, _ = oracle.wmc_eval(u, "replicate", candidates=True)
+        want = np.array([-2 * a / 3, -2 * b / 3, 2 * a / 3, 2 * b / 3,
+                         -(a + b) / 2, (a - b) / 2, (a + b) / 2, -(a - b) / 2])
+        np.testing.assert_allclose(cand[1:-1, 1:-1], np.broadcast_to(want, cand[1:-1, 1:-1].shape),
+                                   rtol=0, atol=1e-12)
+
+
+def test_affine_magnitude_and_zero_directions():
+    """|H^w| = min(2|a|/3, 2|b|/3, |a+b|/2, |a-b|/2); zero exactly along the 8 normals."""
+    y, x = np.mgrid[0:7, 0:7].astype(np.float64)
+    for a, b in [(3, 0), (0, -5), (2, 2), (4, -4), (3, 1), (-2, 7), (1, 2)]:
+        u = a * x + b * y + 0.25
+        hw = oracle.wmc_eval(u, "replicate")[1:-1, 1:-1]
+        mag = min(2 * abs(a) / 3, 2 * abs(b) / 3, abs(a + b) / 2, abs(a - b) / 2)
+        np.testing.assert_allclose(np.abs(hw), mag, rtol=0, atol=1e-12)
+        if a == 0 or b == 0 or abs(a) == abs(b):
+            assert np.all(hw == 0)
+
+
+def test_ramp_canonical_tie_choice():
+    """U = x + 2y: candidates +-2/3, +-4/3, +-3/2, +-1/2 in the interior.  The minimum |d| = 1/2
+    is shared by d_6 = -1/2 and d_8 = +1/2 (an opposite-sign tie).  The Appendix's list, read as
+    correlation kernels, is (h3, h1, h4, h2, h7, h8, h6, h5): h8 comes before h6, so its first
+    minimum is d_8 = +1/2."""
+    y, x = np.mgrid[0:5, 0:5].astype(np.float64)
+    hw, cand, idx = oracle.wmc_eval(x + 2 * y, "replicate", candidates=True)
+    assert np.all(hw[1:-1, 1:-1] == 0.5)
+    assert np.all(idx[1:-1, 1:-1] == 8)
+
+
+def test_paraboloid_x2():
+    """U = x^2: d_2 = d_4 = 2/3 everywhere inside; d_1 = 2/3 - 4x/3, d_3 = 2/3 + 4x/3,
+    d_5 = d_8 = 2/3 - x, d_6 = d_7 = 2/3 + x."""
+    y, x = np.mgrid[0:8, 0:9].astype(np.float64)
+    _, cand, _ = oracle.wmc_eval(x ** 2, "replicate", candidates=True)
+    xi = x[1:-1, 1:-1]
+    want = np.stack([2 / 3 - 4 * xi / 3, 2 / 3 + 0 * xi, 2 / 3 + 4 * xi / 3, 2 / 3 + 0 * xi,
+                     2 / 3 - xi, 2 / 3 + xi, 2 / 3 + xi, 2 / 3 - xi], -1)
+    np.testing.assert_allclose(cand[1:-1, 1:-1], want, rtol=0, atol=1e-12)
+
+
+def test_paraboloid_vertex():
+    """U = (x-3)^2 + (y-3)^2: every d_i = 4/3 at the vertex."""
+    y, x = np.mgrid[0:7, 0:7].astype(np.float64)
+    _, cand, _ = oracle.wmc_eval((x - 3) ** 2 + (y - 3) ** 2, "replicate", candidates=True)
+    np.testing.assert_allclose(cand[3, 3], np.full(8, 4 / 3), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("boundary", ["replicate", "zero"])
+def test_impulse(boundary):
+    """A unit impulse: -1 at the impulse (all d_i = -1), 0 at every other pixel (some half
+    window avoids it)."""
+    u = np.zeros((7, 8))
+    u[3, 4] = 1
+    hw = oracle.wmc_eval(u, boundary)
+    want = np.zeros_like(u)
+    want[3, 4] = -1
+    assert np.array_equal(hw, want)
+
+
+def test_step_edges_vanish():
+    """Axis-aligned steps vanish everywhere (replicate keeps them steps); diagonal steps vanish
+    at interior pixels: the half window on one side of the edge sees a constant."""
+    y, x = np.mgrid[0:12, 0:13].astype(np.float64)
+    for u in [(x >= 5) * 1.0, (y >= 4) * 2.0, (x < 7) * -3.0]:
+        assert np.all(oracle.wmc_eval(u, "replicate") == 0)
+    for u in [(x + y >= 9) * 1.0, (x - y >= 2) * 1.5, (x + y < 12) * 1.0]:
+        assert np.all(oracle.wmc_eval(u, "replicate")[1:-1, 1:-1] == 0)
+
+
+def test_square_corners():
+    """A 3x3 square of ones in a 5x5 zero image: -1/6 at its four corners (h7 or a rotation
+    of it sees 1/6 + 2/3 + 0 - 1), 0 everywhere else."""
+    u = np.zeros((5, 5))
+    u[1:4, 1:4] = 1
+    hw = oracle.wmc_eval(u, "replicate")
+    want = np.zeros((5, 5))
+    for yy, xx in [(1, 1), (1, 3), (3, 1), (3, 3)]:
+        want[yy, xx] = -1 / 6
+    np.testing.assert_allclose(hw, want, rtol=0, atol=1e-15)
+
+
+def test_constant_image():
+    for bnd in ["replicate", "zero"]:
+        hw = oracle.wmc_eval(np.full((4, 6), 2.5), bnd)
+        if bnd == "replicate":
+            assert np.all(hw == 0)
+        else:
+            assert np.all(hw[1:-1, 1:-1] == 0)
+
+
+# --------------------------------------------------------------------------- invariances
+def test_contrast_homogeneity_bitwise():
+    """H^w(alpha U) = alpha H^w(U) bit for bit when alpha is +-2^k (Sec. III-B, exact here)."""
+    u = synth.make_image(33, 29, seed=3).astype(np.float64)
+    hw = oracle.wmc_eval(u)
+    for alpha in [2.0, -2.0, 0.5, -0.25, 1024.0, -1.0]:
+        assert np.array_equal(oracle.wmc_eval(alpha * u), alpha * hw)
+
+
+def test_contrast_homogeneity_general():
+    u = synth.make_image(33, 29, seed=3).astype(np.float64)
+    hw, cand, _ = oracle.wmc_eval(u, candidates=True)
+    mags = np.sort(np.abs(cand), -1)
+    clear = (mags[..., 1] - mags[..., 0]) > 1e-9
+    for alpha in [3.7, -0.3]:
+        np.testing.assert_allclose(oracle.wmc_eval(alpha * u)[clear], alpha * hw[clear], rtol=1e-12,
+                                   atol=1e-14)
+
+
+def test_offset_invariance():
+    u = synth.make_image(20, 20, seed=4).astype(np.float64)
+    np.testing.assert_allclose(oracle.wmc_eval(u + 3.0), oracle.wmc_eval(u), atol=1e-13)
+    ui = np.random.default_rng(0).integers(0, 9, (9, 9)).astype(np.float64)
+    assert np.array_equal(oracle.wmc_eval(ui + 7), oracle.wmc_eval(ui))
+
+
+@pytest.mark.parametrize("op", ["rot90", "rot180", "rot270", "fliplr", "flipud", "transpose"])
+def test_d4_equivariance_off_ties(op):
+    """The kernel set is closed under the dihedral group, so H^w(R U) = R H^w(U) wherever the
+    minimum |d_i| is unique (Sec. IV-A: eight normals 45 degrees apart)."""
+    f = {"rot90": lambda a: np.rot90(a, 1), "rot180": lambda a: np.rot90(a, 2),
+         "rot270": lambda a: np.rot90(a, 3), "fliplr": np.fliplr, "flipud": np.flipud,
+         "transpose": lambda a: a.T}[op]
+    u = synth.make_image(24, 31, seed=5).astype(np.float64)
+    hw, cand, _ = oracle.wmc_eval(u, candidates=True)
+    mags = np.sort(np.abs(cand), -1)
+    clear = f((mags[..., 1] - mags[..., 0]) > 1e-9)
+    got = oracle.wmc_eval(np.ascontiguousarray(f(u)))
+    np.testing.assert_allclose(got[clear], f(hw)[clear], rtol=0, atol=1e-13)
+
+
+# --------------------------------------------------------------------- flows (Sec. V-B, MCF)
+def test_max_principle():
+    """With step*(1+lambda) <= 1 every step is a convex combination of neighbours and f, so all
+    iterates stay inside [min f, max f]."""
+    f = synth.make_image(30, 30, seed=6, sigma=0.1).astype(np.float64)
+    lo, hi = f.min(), f.max()
+    for lam, step in [(1.0, 0.5), (1.0, 0.25), (2.0, 1 / 3), (0.5, 0.5)]:
+        for it in [1, 5, 40]:
+            u = oracle.denoise(f, lam, step, it)
+            assert u.min() >= lo - 1e-12 and u.max() <= hi + 1e-12
+
+
+def test_one_step_by_hand():
+    """One step, lambda = 1, step = 1/4, on a 3x3 image with a single 1 in the middle:
+    H^w = -1 there and 0 elsewhere, so U^1 = f + (1/4)(H^w - (f - f)) = f + H^w/4."""
+    f = np.zeros((3, 3))
+    f[1, 1] = 1
+    u1 = oracle.denoise(f, 1.0, 0.25, 1)
+    want = f.copy()
+    want[1, 1] = 0.75
+    np.testing.assert_allclose(u1, want, atol=1e-16)
+
+
+def test_two_steps_by_hand():
+    """Second step of the same problem: now U = 0.75 at the centre, f = 1 there.  The centre's
+    d_i are all -0.75; every neighbour still has a half window that avoids the centre, so
+    U^2 = U^1 + (1/4)(-0.75 - (0.75 - 1)) at the centre = 0.75 - 0.125 = 0.625."""
+    f = np.zeros((3, 3))
+    f[1, 1] = 1
+    u2 = oracle.denoise(f, 1.0, 0.25, 2)
+    want = np.zeros((3, 3))
+    want[1, 1] = 0.625
+    np.testing.assert_allclose(u2, want, atol=1e-16)
+
+
+def test_denoise_contrast_bitwise():
+    f = synth.make_image(26, 19, seed=8).astype(np.float64)
+    u = oracle.denoise(f, 1.0, 0.25, 10)
+    for alpha in [2.0, -0.5]:
+        assert np.array_equal(oracle.denoise(alpha * f, 1.0, 0.25, 10), alpha * u)
+
+
+def test_resume():
+    """denoise(f, n + m) == m more steps from U^n, bit for bit (the state is (U, f))."""
+    f = synth.make_image(21, 23, seed=9).astype(np.float64)
+    un = oracle.denoise(f, 1.2, 0.2, 7)
+    assert np.array_equal(oracle.denoise(f, 1.2, 0.2, 12), oracle.denoise(f, 1.2, 0.2, 5, u0=un))
+
+
+def test_mcf_fixed_points():
+    y, x = np.mgrid[0:9, 0:10].astype(np.float64)
+    for u in [np.full((9, 10), 0.3), (x >= 4) * 1.0, (y >= 6) * 1.0]:
+        assert np.array_equal(oracle.mcf(u, 0.5, 20), u)
+
+
+def test_mcf_is_flow_without_data_term():
+    u = synth.make_image(15, 15, seed=10).astype(np.float64)
+    hw = oracle.wmc_eval(u)
+    np.testing.assert_allclose(oracle.mcf(u, 0.3, 1), u + 0.3 * hw, atol=1e-16)
+
+
+def test_energies():
+    y, x = np.mgrid[0:8, 0:8].astype(np.float64)
+    step = (x >= 3) * 1.0
+    e = oracle.energies(step, step, step)
+    assert e == (0.0, 0.0, 0.0)
+    imp = np.zeros((6, 6))
+    imp[2, 3] = 2.0
+    e = oracle.energies(imp, np.zeros((6, 6)), np.ones((6, 6)))
+    assert e[0] == pytest.approx(2.0, abs=1e-15)       # only the impulse: |H^w| = 2
+    assert e[1] == pytest.approx(0.5 * 4.0, abs=1e-15)  # 1/2 * 2^2
+    assert e[2] == pytest.approx(35 * 1.0 + 1.0, abs=1e-15)
+
+
+# ------------------------------------------------------------------ primal-dual (Sec. V-C)
+def test_primal_dual_scalar_by_hand():
+    """lambda = 0 (no regulariser): the update is pointwise.  f = 0, U^0 = 1, alpha = 0.5,
+    step = 0.1:  r = 1 -> d^1 = 0.5, U^1 = 1 - 0.1 (1 - 0)/0.5 = 0.8;
+    r = 0.8 + 0.5 = 1.3 -> d^2 = 0.5, U^2 = 0.8 - 0.1 (1 - 0.5)/0.5 = 0.7."""
+    f = np.zeros((3, 4))
+    u0 = np.ones((3, 4))
+    u1, d1 = oracle.l1_primal_dual(f, 0.0, 0.1, 0.5, 1, u0=u0)
+    np.testing.assert_allclose(u1, 0.8, atol=1e-15)
+    np.testing.assert_allclose(d1, 0.5, atol=1e-15)
+    u2, d2 = oracle.l1_primal_dual(f, 0.0, 0.1, 0.5, 2, u0=u0)
+    np.testing.assert_allclose(u2, 0.7, atol=1e-15)
+    np.testing.assert_allclose(d2, 0.5, atol=1e-15)
+
+
+def test_primal_dual_inside_clip():
+    """|r| <= alpha throughout: d^{t+1} = r.  f = 0, U^0 = 0.1, alpha = 1, step = 0.1, lambda = 0:
+    d^1 = 0.1, U^1 = 0.1 - 0.1 * 0.2 = 0.08;  d^2 = 0.08 + 0.1 = 0.18,
+    U^2 = 0.08 - 0.1 * (0.36 - 0.1) = 0.054."""
+    f = np.zeros((2, 2))
+    u2, d2 = oracle.l1_primal_dual(f, 0.0, 0.1, 1.0, 2, u0=np.full((2, 2), 0.1))
+    np.testing.assert_allclose(u2, 0.054, atol=1e-15)
+    np.testing.assert_allclose(d2, 0.18, atol=1e-15)
+
+
+def test_primal_dual_constant_is_fixed():
+    f = np.full((5, 6), 0.4)
+    u, d = oracle.l1_primal_dual(f, 2.0, 0.1, 0.3, 10)
+    np.testing.assert_allclose(u, f, atol=1e-16)
+    assert np.all(d == 0)
+
+
+# ------------------------------------------------------------------- storage emulation
+def test_round_f16_matches_numpy():
+    rng = np.random.default_rng(11)
+    vals = np.concatenate([rng.normal(size=2000), rng.normal(size=200) * 1e-6,
+                           rng.normal(size=200) * 3e4, [6.1e-5, 5.96e-8, 2.98e-8, 65519.0, 65520.0, 1.0],
+                           1 + (2 * np.arange(50) + 1) * 2.0 ** -11])
+    np.testing.assert_array_equal(oracle.round_storage(vals, "f16"),
+                                  vals.astype(np.float16).astype(np.float64))
+
+
+def test_round_bf16_ties_and_carries():
+    # bf16 keeps 8 significant bits: 1 + k/128 are representable; halfway points go to even.
+    assert oracle.round_storage(np.array([1 + 1 / 256]), "bf16")[0] == 1.0
+    assert oracle.round_storage(np.array([1 + 3 / 256]), "bf16")[0] == 1 + 4 / 256
+    assert oracle.round_storage(np.array([1 + 1 / 256 + 1e-12]), "bf16")[0] == 1 + 1 / 128
+    assert oracle.round_storage(np.array([255.5 * 2 ** -7 * 2]), "bf16")[0] == 4.0
+    assert oracle.round_storage(np.array([-0.3]), "bf16")[0] == -0.30078125
+
+
+def test_round_f32_matches_cast():
+    vals = np.random.default_rng(12).normal(size=1000)
+    np.testing.assert_array_equal(oracle.round_storage(vals, "f32"), vals.astype(np.float32).astype(np.float64))
