@@ -1,0 +1,291 @@
+#!/usr/bin/env python3
+"""Benchmark: WMC denoising throughput on GB300 (gigapixel-iterations per second).
+
+One step = the whole hot path on one 4096 x 4096 FP32 synthetic image (64 bumps, 32 shapes,
+sigma 0.02, seed 1): one H^w evaluation pass (wmc_eval), 500 Jacobi iterations of the
+L2-denoising flow (wmc_denoise: lambda 1, step 0.25, replicate boundary) and the FP64
+energies (wmc_energy).  value = H*W*500 / step time (the evaluation pass and the energies
+are inside the timed step but not counted as work).  L2 is flushed (256 MiB write) before
+every timed step, outside the events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded crop of the same
+workload.  Under torchrun (N > 1) every rank denoises its own image (independent replicas:
+weak scaling, no communication) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gigapixel-iterations/s of WMC denoising (1 GB300) and % of HBM roofline"
+UNIT = "Gpix-iter/s"
+H = W = 4096
+ITERS = 500
+LAM = 1.0
+STEP = 0.25
+SIGMA = 0.02
+WORKLOAD = (f"{H}x{W} f32 synthetic image (64 bumps + 32 shapes, sigma {SIGMA}, seed 1): "
+            f"1 WMC eval pass + {ITERS} L2-denoising iterations (lambda {LAM}, step {STEP}, "
+            f"replicate) + FP64 energies")
+BYTES_PER_PX_LAUNCH = 12  # read U, read f, write U (FP32): algorithmic bytes of one pass
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--steps-per-launch", type=int, default=0)
+    ap.add_argument("--iters", type=int, default=ITERS, help="override (profiling runs only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(u, crop: int, iters: int):
+    """Oracle throughput (Gpix-iter/s) on a crop x crop corner of the image, `iters` steps."""
+    import oracle
+    f = np.ascontiguousarray(u[:crop, :crop], dtype=np.float64)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.denoise(f, LAM, STEP, iters)
+    dt = time.perf_counter() - t0
+    return crop * crop * iters / dt / 1e9, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1903_07189_gb300 import synth
+    u = synth.make_image(H, W, seed=1, n_bumps=64, n_shapes=32, sigma=SIGMA)
+    crop, iters = 1024, 16
+    for _ in range(args.warmup):
+        cpu_oracle_rate(u, 128, 2)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt = cpu_oracle_rate(u, crop, iters)
+        rates.append(r)
+        times.append(dt)
+    value = statistics.median(rates)
+    sample = f"{crop}x{crop} top-left crop of the workload image, {iters} iterations per step (oracle, FP64, 1 thread)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1903_07189_gb300 import synth, wmc
+    wmc.load()
+
+    u_host = synth.make_image(H, W, seed=1 + 1000 * rank, n_bumps=64, n_shapes=32, sigma=SIGMA)
+    f = torch.from_numpy(u_host).to(dev)
+    hw = torch.empty_like(f)
+    out = torch.empty_like(f)
+    lib = wmc.load()
+    ws = torch.empty(lib.wmc_denoise_workspace_size(H, W, W, 0), dtype=torch.uint8, device=dev)
+    ews = torch.empty(lib.wmc_energy_workspace_size(H, W), dtype=torch.uint8, device=dev)
+    energies = torch.empty(3, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    iters = args.iters
+    T = args.steps_per_launch or 4
+    n_launch = math.ceil(iters / T)
+
+    def step():
+        wmc.eval(f, out=hw)
+        e0.record()
+        wmc.denoise(f, LAM, STEP, iters, out=out, steps_per_launch=T, workspace=ws)
+        e1.record()
+        wmc.energy(out, f, None, out=energies, workspace=ews)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    d0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    d1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        barrier()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            e0, e1 = d0[k], d1[k]
+            starts[k].record()
+            step()
+            ends[k].record()
+        barrier()
+        wall = time.perf_counter() - wall0
+    clocks = clk.summary()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    den_ms = [a.elapsed_time(b) for a, b in zip(d0, d1)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    units = H * W * iters * args.steps * world
+    value = units / (total_ms * 1e-3) / 1e9
+
+    # dominant kernel: the temporally blocked flow kernel, n_launch launches per denoise call
+    launch_ms = statistics.mean(den_ms) / n_launch
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_PX_LAUNCH * H * W / (launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"wmc::tile_kernel<T={T}> (flow)", "peak_kind": peak_kind,
+                "launch_ms": launch_ms,
+                "effective_gbs_per_iter": BYTES_PER_PX_LAUNCH * H * W * T / (launch_ms * 1e-3) / 1e9}
+
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(u_host).pin_memory()
+        oh = torch.empty_like(fh).pin_memory()
+        hws = torch.empty(wmc.denoise_host_workspace_size(H, W), dtype=torch.uint8, device=dev)
+        st = torch.cuda.current_stream(dev)
+        for _ in range(2):
+            wmc.denoise_host(fh, LAM, STEP, iters, out=oh, workspace=hws, device=dev)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        ne = max(1, min(args.steps, 3))
+        for _ in range(ne):
+            wmc.denoise_host(fh, LAM, STEP, iters, out=oh, workspace=hws, device=dev)
+            st.synchronize()
+        barrier()
+        dt = (time.perf_counter() - t0) / ne
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": H * W * iters * world / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
+               "d2h_bytes_per_step": H * W * 4, "call": "wmc_denoise_host (pinned host f in, U out)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(u_host, 1024, 64)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1024x1024 top-left crop, 64 iterations (FP64 oracle, 1 thread, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "l2": "flushed before each timed step (256 MiB write)",
+                           "steps_per_launch": T, "iters": iters, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * (2 + n_launch), "clocks": clocks,
+                "wall_s_timed_region": wall}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,159 @@
+/*
+ * wmc.h -- C ABI of the GB300 (sm_103a) Weighted Mean Curvature library.
+ *
+ * The operations follow Gong & Goksel, "Weighted Mean Curvature", arXiv 1903.07189:
+ *   - H^w(U): the "Half Laplace Operator" of Sec. IV-B -- eight signed distances
+ *     d_i = h_i * U with the 3x3 half-window kernels h_1..h_8 (Eq. conv), and the one with
+ *     the smallest magnitude, H^w = d_m, m = argmin_i |d_i| (Eq. act);
+ *   - the explicit, Jacobi-ordered WMC flows that apply it to a whole image:
+ *     L2 denoising U^{t+1} = U^t + step (lambda H^w(U^t) - (U^t - f)) (the gradient flow of
+ *     Sec. V-B with A = I, where -dR_area/dU is replaced by H^w), and the mean-curvature flow
+ *     U^{t+1} = U^t + step H^w(U^t) (Eq. MCF);
+ *   - the energies of Eq. wmcr (q = 1) and Eq. 1 (L2 data term), reduced in FP64.
+ *
+ * Conventions shared by every entry point
+ *   Images are single-channel, row-major, h rows by w columns, with a leading dimension
+ *   (row pitch) `ld` counted in ELEMENTS (ld >= w).  Element type: see wmc_dtype_t.  Colour
+ *   images are processed one channel at a time (the paper does so, Sec. V-D).
+ *   Pointers documented as "device" must be CUDA device (or managed) memory readable by the
+ *   current device; "host" pointers are ordinary host memory (pinned memory gives
+ *   asynchronous copies).  The caller owns every buffer; the library never allocates or
+ *   frees memory and keeps no state between calls other than the per-thread error string.
+ *   Work is enqueued on `stream` (NULL = the legacy default stream) and runs asynchronously;
+ *   argument errors are detected on the host and returned before anything is enqueued.
+ *   No function throws; every failure is a status code, with a detail string available from
+ *   wmc_last_error() on the calling thread.
+ *   Boundary: WMC_BOUNDARY_REPLICATE reads the nearest in-image pixel outside the image
+ *   (a discrete Neumann condition, Sec. III-C / IV-A); WMC_BOUNDARY_ZERO reads 0 there (the
+ *   zero padding of the Appendix listing's conv2 'same').
+ *   Ties (several d_i of equal magnitude, e.g. on straight ramps) may resolve to either
+ *   candidate; every returned value is one of the eight d_i up to FP32 rounding.
+ *   Arithmetic is FP32 for every storage type; BF16/FP16 inputs are widened on load and every
+ *   stored result (H^w, or U after each step) is rounded to nearest-even.
+ */
+#ifndef WMC_H
+#define WMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared here so this header needs no CUDA include. */
+struct CUstream_st;
+typedef struct CUstream_st *wmc_stream_t;
+
+typedef enum {
+    WMC_OK = 0,
+    WMC_ERR_INVALID_ARG = 1, /* a size, pitch, pointer, dtype, boundary or scalar is invalid */
+    WMC_ERR_ALIAS = 2,       /* an output overlaps an input it must not overlap */
+    WMC_ERR_UNSUPPORTED = 3, /* valid request this build cannot serve (e.g. no sm_103a GPU) */
+    WMC_ERR_CUDA = 4,        /* a CUDA runtime call failed; see wmc_last_error() */
+    WMC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (batched path) */
+    WMC_ERR_WORKSPACE = 6    /* workspace missing, too small or misaligned */
+} wmc_status_t;
+
+typedef enum { WMC_BOUNDARY_REPLICATE = 0, WMC_BOUNDARY_ZERO = 1 } wmc_boundary_t;
+
+typedef enum { WMC_F32 = 0, WMC_BF16 = 1, WMC_F16 = 2 } wmc_dtype_t;
+
+/* Workspace buffers must start on this many bytes. */
+#define WMC_WORKSPACE_ALIGN 256
+
+/*
+ * Kernel configuration for the flows.  steps_per_launch = T (1..8) Jacobi steps are taken in
+ * on-chip memory per pass over the image (temporal blocking; legal because step t+1 of every
+ * pixel reads only U^t, Eq. MCF / Sec. V-B); 0 = library default.  tile = 0 picks the default
+ * tile shape.  Results do not depend on the configuration: every configuration performs the
+ * same FP32 operations on every pixel, so outputs are bitwise identical.
+ */
+typedef struct {
+    int32_t steps_per_launch;
+    int32_t tile;
+} wmc_config_t;
+
+/* ------------------------------------------------------------------------------------------
+ * wmc_eval: H^w(U) at every pixel (Sec. IV-B, Eq. conv + Eq. act).
+ *   u   device, h x w, pitch ld_u, type dtype           (input U)
+ *   hw  device, h x w, pitch ld_hw, type dtype          (output H^w; must not overlap u)
+ *   h, w >= 0 (either 0: nothing to do), ld_u >= w, ld_hw >= w.
+ * Errors: WMC_ERR_INVALID_ARG (sizes, null pointer with h*w > 0, bad enum),
+ *         WMC_ERR_ALIAS (hw overlaps u), WMC_ERR_CUDA (launch failure).
+ */
+wmc_status_t wmc_eval(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_u, int64_t ld_hw,
+                      wmc_dtype_t dtype, wmc_boundary_t bnd, wmc_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * wmc_denoise: `iters` explicit Jacobi steps of the WMC flow
+ *      U^{t+1} = U^t + step * (lambda * H^w(U^t) - mu * (U^t - f)),
+ *   mu = 1 when f != NULL (L2 denoising, Sec. V-B with A = I),
+ *   mu = 0 when f == NULL (mean-curvature flow, Eq. MCF; lambda then scales the step).
+ *   f    device, h x w, pitch ld (observed image) or NULL
+ *   u0   device, h x w, pitch ld (U^0) or NULL for U^0 = f; may equal u (resume in place)
+ *   u    device, h x w, pitch ld (output U^iters); must not overlap f; if u0 != u it must not
+ *        overlap u0 either
+ *   lambda finite, >= 0 (regularisation weight, Eq. 1); step finite, > 0 (time step delta,
+ *   Eq. MCF -- the paper does not fix it; step*(mu+lambda) <= 1 keeps every iterate inside
+ *   the range of f and U^0, a larger step is accepted but carries no such guarantee);
+ *   iters >= 0 (0 copies U^0 to u).
+ *   workspace: device, >= wmc_denoise_workspace_size() bytes, WMC_WORKSPACE_ALIGN-aligned,
+ *   must not overlap f, u0 or u; may be NULL only if that size is 0.
+ * Errors: WMC_ERR_INVALID_ARG, WMC_ERR_ALIAS, WMC_ERR_WORKSPACE, WMC_ERR_CUDA.
+ */
+size_t wmc_denoise_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype);
+
+wmc_status_t wmc_denoise(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
+                         wmc_dtype_t dtype, float lambda, float step, int32_t iters,
+                         wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
+                         wmc_stream_t stream);
+
+/* As wmc_denoise, with an explicit kernel configuration (NULL = defaults). */
+wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, int32_t w,
+                            int64_t ld, wmc_dtype_t dtype, float lambda, float step,
+                            int32_t iters, wmc_boundary_t bnd, const wmc_config_t *config,
+                            void *workspace, size_t workspace_bytes, wmc_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * wmc_denoise_host: wmc_denoise on HOST buffers.  Copies f (and u0) to the device workspace on
+ * `stream`, runs the flow there and copies U^iters back into u_host; all of it is enqueued on
+ * `stream` and the call returns without waiting (synchronise the stream before reading
+ * u_host; pinned host memory makes the copies asynchronous).
+ *   f_host  host, h x w, pitch ld (may be NULL for the mean-curvature flow, then u0_host is
+ *           required); u0_host host or NULL (U^0 = f); u_host host output, pitch ld.
+ *   workspace: DEVICE memory of wmc_denoise_host_workspace_size() bytes.
+ * Errors: as wmc_denoise.
+ */
+size_t wmc_denoise_host_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype);
+
+wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_host, int32_t h,
+                              int32_t w, int64_t ld, wmc_dtype_t dtype, float lambda, float step,
+                              int32_t iters, wmc_boundary_t bnd, void *workspace,
+                              size_t workspace_bytes, wmc_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * wmc_energy: FP64 reductions of one image (Eq. wmcr with q = 1; the L2 data term of Eq. 1):
+ *   out[0] = sum_p |H^w(U)(p)|,  out[1] = 1/2 sum_p (U - f)^2,  out[2] = sum_p (U - clean)^2
+ *   (out[1] = 0 when f is NULL, out[2] = 0 when clean is NULL).
+ *   u, f, clean: device, h x w, pitch ld, type dtype.  out: DEVICE, 3 doubles, written (not
+ *   accumulated).  Per-thread partial sums run in FP32 over at most 16 pixels and in FP64
+ *   beyond; the summation order is fixed, so repeated calls give identical results.
+ *   workspace: device, >= wmc_energy_workspace_size() bytes, aligned as above.
+ */
+size_t wmc_energy_workspace_size(int32_t h, int32_t w);
+
+wmc_status_t wmc_energy(const void *u, const void *f, const void *clean, int32_t h, int32_t w,
+                        int64_t ld, wmc_dtype_t dtype, wmc_boundary_t bnd, double *out,
+                        void *workspace, size_t workspace_bytes, wmc_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------ */
+const char *wmc_status_string(wmc_status_t status); /* static string, never NULL */
+const char *wmc_last_error(void); /* detail of the last failure on this thread ("" if none) */
+int32_t wmc_version(void);        /* 100 * major + minor */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WMC_H */

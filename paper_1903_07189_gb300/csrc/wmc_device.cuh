@@ -1,0 +1,87 @@
+// wmc_device.cuh -- device-side arithmetic of the WMC Half Laplace Operator (sm_103a).
+//
+// H^w(U) = d_m, m = argmin_i |d_i|, d_i = h_i * U (Sec. IV-B, Eq. conv / Eq. act).
+//
+// The kernels here do not evaluate the eight 6-tap sums one by one.  The eight half windows
+// come in antipodal pairs (h1,h3), (h2,h4), (h5,h7), (h6,h8) whose average is the isotropic
+// Laplace kernel k4 of Eq. kernel3; so with L = k4 * U and the odd parts a_j = d_j - L
+// (j = 1, 2, 5, 6) the candidates are exactly d = L +- a_j.  For one pair the smaller
+// magnitude is ||L| - |a_j||, reached with the value sign(L) (|L| - |a_j|), so
+//     H^w = sign(L) * t*,  t* = the t_j = |L| - |a_j| of smallest magnitude.
+// In exact arithmetic this equals Eq. act (when L = 0 the two candidates of a pair are an
+// opposite-sign tie and either is a valid d_m).  Everything is carried scaled by 12 so that
+// all stencil weights are small integers:
+//     12 L   = (NW + NE + SW + SE) + 2 (N + S + E + W) - 12 C
+//     12 a_1 = (NW + SW - NE - SE) + 2 (W - E)          (h1: west half window)
+//     12 a_2 = (NW + NE - SW - SE) + 2 (N - S)          (h2: north half window)
+//     12 a_5 = (NW - SE) + 2 (N + W - S - E)            (h5: north-west half window)
+//     12 a_6 = (NE - SW) + 2 (N + E - S - W)            (h6: north-east half window)
+// which costs about 30 FP32 operations per pixel instead of ~60 for eight sums and eight
+// compare/selects.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wmc {
+
+// 12 * H^w at the centre of a 3x3 neighbourhood (rows: n* above, s* below).
+__device__ __forceinline__ float half_laplace12(float nw, float n, float ne, float w, float c,
+                                                float e, float sw, float s, float se) {
+    const float p = n - s;   // N - S
+    const float q = w - e;   // W - E
+    const float A = nw - se;
+    const float B = ne - sw;
+    const float corners = (nw + se) + (ne + sw);
+    const float edges = (n + s) + (w + e);
+    const float L = fmaf(-12.0f, c, fmaf(2.0f, edges, corners));
+    const float a1 = fmaf(2.0f, q, A - B);
+    const float a2 = fmaf(2.0f, p, A + B);
+    const float a5 = fmaf(2.0f, p + q, A);
+    const float a6 = fmaf(2.0f, p - q, B);
+    const float aL = fabsf(L);
+    float t = aL - fabsf(a1);
+    const float t2 = aL - fabsf(a2);
+    const float t5 = aL - fabsf(a5);
+    const float t6 = aL - fabsf(a6);
+    t = fabsf(t2) < fabsf(t) ? t2 : t;
+    t = fabsf(t5) < fabsf(t) ? t5 : t;
+    t = fabsf(t6) < fabsf(t) ? t6 : t;
+    // sign(L) * t: flip t's sign bit when L is negative (one LOP3).
+    return __int_as_float(__float_as_int(t) ^ (__float_as_int(L) & 0x80000000));
+}
+
+// ---------------------------------------------------------------- storage types
+template <typename S> struct Store;
+
+template <> struct Store<float> {
+    static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float round(float v) { return v; }
+    static __device__ __forceinline__ void store(float *p, float v) { *p = v; }
+};
+
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16 *p) {
+        return __bfloat162float(__ldg(p));
+    }
+    static __device__ __forceinline__ float round(float v) {
+        return __bfloat162float(__float2bfloat16_rn(v));
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v) {
+        *p = __float2bfloat16_rn(v);
+    }
+};
+
+template <> struct Store<__half> {
+    static __device__ __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float round(float v) {
+        return __half2float(__float2half_rn(v));
+    }
+    static __device__ __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
+enum Boundary { BND_REPLICATE = 0, BND_ZERO = 1 };
+
+}  // namespace wmc

@@ -1,0 +1,217 @@
+"""Python binding of libwmc.so (include/wmc.h): argument marshalling only.
+
+Every entry point here hands device pointers of torch tensors, sizes and the current CUDA
+stream to the C ABI; all stencil work runs in the library's CUDA kernels.  There is no CPU
+fallback: if libwmc.so cannot be loaded, or a call fails, a ``WMCError`` is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+DTYPES = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2}
+BOUNDARY = {"replicate": 0, "zero": 1}
+WORKSPACE_ALIGN = 256
+
+
+class WMCError(RuntimeError):
+    def __init__(self, status: int, func: str, detail: str):
+        self.status = status
+        super().__init__(f"{func} failed: {_STATUS.get(status, status)}: {detail}")
+
+
+_STATUS = {0: "WMC_OK", 1: "WMC_ERR_INVALID_ARG", 2: "WMC_ERR_ALIAS", 3: "WMC_ERR_UNSUPPORTED",
+           4: "WMC_ERR_CUDA", 5: "WMC_ERR_TIMEOUT", 6: "WMC_ERR_WORKSPACE"}
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("steps_per_launch", ctypes.c_int32), ("tile", ctypes.c_int32)]
+
+
+_lib = None
+
+# name -> (restype, argtypes) for every symbol declared in include/wmc.h
+_vp, _i32, _i64, _f32, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+SIGNATURES = {
+    "wmc_eval": (_i32, [_vp, _vp, _i32, _i32, _i64, _i64, _i32, _i32, _vp]),
+    "wmc_denoise_workspace_size": (_sz, [_i32, _i32, _i64, _i32]),
+    "wmc_denoise": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp, _sz, _vp]),
+    "wmc_denoise_ex": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32,
+                              ctypes.POINTER(Config), _vp, _sz, _vp]),
+    "wmc_denoise_host_workspace_size": (_sz, [_i32, _i32, _i64, _i32]),
+    "wmc_denoise_host": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp, _sz,
+                                _vp]),
+    "wmc_energy_workspace_size": (_sz, [_i32, _i32]),
+    "wmc_energy": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _i32, _vp, _vp, _sz, _vp]),
+    "wmc_status_string": (ctypes.c_char_p, [_i32]),
+    "wmc_last_error": (ctypes.c_char_p, []),
+    "wmc_version": (_i32, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libwmc.so (building it first if needed); raises if that is impossible."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise WMCError(3, "load", f"{path} not found; run build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int, func: str):
+    if status != 0:
+        raise WMCError(status, func, load().wmc_last_error().decode())
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _img(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D (H, W)")
+    if t.dtype not in DTYPES:
+        raise ValueError(f"{name}: unsupported dtype {t.dtype}")
+    if t.stride(1) != 1 or (t.size(0) > 1 and t.stride(0) < t.size(1)):
+        raise ValueError(f"{name} must be row-major with unit column stride")
+    return t.data_ptr(), t.size(0), t.size(1), max(t.stride(0), t.size(1))
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    # torch's caching allocator hands out 512-byte aligned blocks, above WORKSPACE_ALIGN.
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+
+
+def eval(u: torch.Tensor, boundary: str = "replicate", out: torch.Tensor | None = None) -> torch.Tensor:
+    """H^w(U) (Sec. IV-B: Eq. conv + Eq. act) of a 2-D CUDA tensor."""
+    p, h, w, ld = _img(u, "u")
+    if out is None:
+        out = torch.empty_like(u, memory_format=torch.contiguous_format)
+    po, ho, wo, ldo = _img(out, "out")
+    if (ho, wo) != (h, w) or out.dtype != u.dtype:
+        raise ValueError("out must match u in shape and dtype")
+    _check(load().wmc_eval(p, po, h, w, ld, ldo, DTYPES[u.dtype], BOUNDARY[boundary], _stream(u.device)),
+           "wmc_eval")
+    return out
+
+
+def default_step(lam: float) -> float:
+    """0.5 / (1 + lambda): half the largest step that keeps the max principle."""
+    return 0.5 / (1.0 + lam)
+
+
+def denoise(f: torch.Tensor | None, lam: float = 1.0, step: float | None = None, iters: int = 100,
+            boundary: str = "replicate", u0: torch.Tensor | None = None, out: torch.Tensor | None = None,
+            steps_per_launch: int = 0, workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """`iters` Jacobi steps of U <- U + step*(lam*H^w(U) - (U - f)) (Sec. V-B, A = I).
+
+    f = None gives the mean-curvature flow U <- U + step*lam*H^w(U) (Eq. MCF) from u0.
+    """
+    ref = f if f is not None else u0
+    if ref is None:
+        raise ValueError("need f or u0")
+    if step is None:
+        step = default_step(lam if f is not None else 0.0)
+    pr, h, w, ld = _img(ref, "f" if f is not None else "u0")
+    pf = _img(f, "f")[0] if f is not None else None
+    pu0 = None
+    if u0 is not None:
+        pu0, h2, w2, ld2 = _img(u0, "u0")
+        if (h2, w2, ld2) != (h, w, ld) or u0.dtype != ref.dtype:
+            raise ValueError("u0 must match f in shape, pitch and dtype")
+    if out is None:
+        out = torch.empty_strided(ref.shape, ref.stride(), dtype=ref.dtype, device=ref.device)
+    po, ho, wo, ldo = _img(out, "out")
+    if (ho, wo, ldo) != (h, w, ld) or out.dtype != ref.dtype:
+        raise ValueError("out must match f in shape, pitch and dtype")
+    lib = load()
+    dt = DTYPES[ref.dtype]
+    need = lib.wmc_denoise_workspace_size(h, w, ld, dt)
+    if workspace is None:
+        workspace = _workspace(need, ref.device)
+    cfg = Config(int(steps_per_launch), 0)
+    _check(lib.wmc_denoise_ex(pf, pu0, po, h, w, ld, dt, float(lam), float(step), int(iters),
+                              BOUNDARY[boundary], ctypes.byref(cfg), workspace.data_ptr(),
+                              workspace.numel(), _stream(ref.device)), "wmc_denoise")
+    return out
+
+
+def mcf(u0: torch.Tensor, step: float = 0.25, iters: int = 100, boundary: str = "replicate", **kw):
+    """Mean-curvature flow U <- U + step*H^w(U) (Eq. MCF)."""
+    return denoise(None, lam=1.0, step=step, iters=iters, boundary=boundary, u0=u0, **kw)
+
+
+def denoise_host(f: torch.Tensor, lam: float = 1.0, step: float | None = None, iters: int = 100,
+                 boundary: str = "replicate", out: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None, device="cuda", stream=None) -> torch.Tensor:
+    """wmc_denoise_host: f and the result live in (preferably pinned) HOST memory; the library
+    copies in, runs the flow and copies out on `stream`.  Returns after enqueueing; the caller
+    synchronises the stream before reading `out`."""
+    if f.is_cuda or f.dim() != 2 or f.dtype not in DTYPES or not f.is_contiguous():
+        raise ValueError("f must be a contiguous 2-D host tensor")
+    h, w = f.shape
+    if out is None:
+        out = torch.empty_like(f, pin_memory=f.is_pinned())
+    if step is None:
+        step = default_step(lam)
+    lib = load()
+    dt = DTYPES[f.dtype]
+    need = lib.wmc_denoise_host_workspace_size(h, w, w, dt)
+    if workspace is None:
+        workspace = _workspace(need, device)
+    st = stream.cuda_stream if stream is not None else _stream(torch.device(device))
+    _check(lib.wmc_denoise_host(f.data_ptr(), None, out.data_ptr(), h, w, w, dt, float(lam), float(step),
+                                int(iters), BOUNDARY[boundary], workspace.data_ptr(), workspace.numel(), st),
+           "wmc_denoise_host")
+    return out
+
+
+def denoise_host_workspace_size(h: int, w: int, dtype=torch.float32) -> int:
+    return load().wmc_denoise_host_workspace_size(h, w, w, DTYPES[dtype])
+
+
+def energy(u: torch.Tensor, f: torch.Tensor | None = None, clean: torch.Tensor | None = None,
+           boundary: str = "replicate", out: torch.Tensor | None = None,
+           workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """(sum|H^w|, 1/2 sum (U-f)^2, sum (U-clean)^2) as a float64 CUDA tensor of 3 values."""
+    p, h, w, ld = _img(u, "u")
+    for t, n in [(f, "f"), (clean, "clean")]:
+        if t is not None:
+            _, h2, w2, ld2 = _img(t, n)
+            if (h2, w2, ld2) != (h, w, ld) or t.dtype != u.dtype:
+                raise ValueError(f"{n} must match u in shape, pitch and dtype")
+    lib = load()
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=u.device)
+    if workspace is None:
+        workspace = _workspace(lib.wmc_energy_workspace_size(h, w), u.device)
+    _check(lib.wmc_energy(p, f.data_ptr() if f is not None else None,
+                          clean.data_ptr() if clean is not None else None, h, w, ld, DTYPES[u.dtype],
+                          BOUNDARY[boundary], out.data_ptr(), workspace.data_ptr(), workspace.numel(),
+                          _stream(u.device)), "wmc_energy")
+    return out
+
+
+def psnr(sse: float, n: int, peak: float = 1.0) -> float:
+    """PSNR in dB from a sum of squared errors over n pixels (FP64, host)."""
+    import math
+    if sse <= 0:
+        return float("inf")
+    return 10.0 * math.log10(peak * peak * n / sse)

@@ -1,0 +1,120 @@
+"""The C ABI on the host: libwmc.so builds and loads, exports every function include/*.h
+declares, and rejects bad arguments before touching the GPU.  No kernel is launched here:
+every call below fails validation, which happens on the host."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1903_07189_gb300 import build, wmc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+OK, INVALID, ALIAS, UNSUPPORTED, CUDA, TIMEOUT, WORKSPACE = range(7)
+
+
+def declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(wmc_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return wmc.load()
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for n in ["wmc_eval", "wmc_denoise", "wmc_energy", "wmc_status_string", "wmc_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(wmc.SIGNATURES)
+
+
+def test_library_is_built_for_sm_103a():
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+    assert os.path.exists(build.LIB)
+
+
+def test_status_strings(lib):
+    assert lib.wmc_status_string(0) == b"WMC_OK"
+    assert lib.wmc_status_string(2) == b"WMC_ERR_ALIAS"
+    assert lib.wmc_status_string(99) == b"WMC_ERR_UNKNOWN"
+    assert lib.wmc_version() >= 100
+
+
+def test_workspace_sizes(lib):
+    assert lib.wmc_denoise_workspace_size(0, 5, 5, 0) == 0
+    assert lib.wmc_denoise_workspace_size(3, 5, 8, 0) == 256
+    assert lib.wmc_denoise_workspace_size(100, 100, 128, 1) == (100 * 128 * 2 + 255) // 256 * 256
+    assert lib.wmc_denoise_workspace_size(4, 5, 4, 0) == 0  # ld < w
+    assert lib.wmc_denoise_host_workspace_size(10, 10, 10, 0) == 4 * 512
+    assert lib.wmc_energy_workspace_size(10, 10) % 256 == 0
+
+
+# Fake, never-dereferenced addresses: every call below is rejected before any launch.
+A, B = 0x10000000, 0x20000000
+
+
+def _err(lib):
+    return lib.wmc_last_error().decode()
+
+
+def test_eval_validation(lib):
+    assert lib.wmc_eval(A, B, -1, 4, 4, 4, 0, 0, None) == INVALID
+    assert lib.wmc_eval(A, B, 4, 4, 3, 4, 0, 0, None) == INVALID and "leading" in _err(lib)
+    assert lib.wmc_eval(A, B, 4, 4, 4, 4, 7, 0, None) == INVALID and "dtype" in _err(lib)
+    assert lib.wmc_eval(A, B, 4, 4, 4, 4, 0, 5, None) == INVALID and "boundary" in _err(lib)
+    assert lib.wmc_eval(None, B, 4, 4, 4, 4, 0, 0, None) == INVALID
+    assert lib.wmc_eval(A, A + 8, 4, 4, 4, 4, 0, 0, None) == ALIAS
+    assert lib.wmc_eval(A, B, 0, 4, 4, 4, 0, 0, None) == OK  # empty: nothing enqueued
+
+
+def _denoise(lib, f, u0, u, h, w, ld, dtype=0, lam=1.0, step=0.25, iters=3, bnd=0, ws=None, wsb=0):
+    return lib.wmc_denoise(f, u0, u, h, w, ld, dtype, lam, step, iters, bnd, ws, wsb, None)
+
+
+def test_denoise_validation(lib):
+    assert _denoise(lib, A, None, B, 4, 4, 4, lam=-1.0) == INVALID and "lambda" in _err(lib)
+    assert _denoise(lib, A, None, B, 4, 4, 4, lam=float("nan")) == INVALID
+    assert _denoise(lib, A, None, B, 4, 4, 4, step=0.0) == INVALID and "step" in _err(lib)
+    assert _denoise(lib, A, None, B, 4, 4, 4, step=float("inf")) == INVALID
+    assert _denoise(lib, A, None, B, 4, 4, 4, iters=-2) == INVALID
+    assert _denoise(lib, None, None, B, 4, 4, 4) == INVALID
+    assert _denoise(lib, A, None, None, 4, 4, 4) == INVALID
+    assert _denoise(lib, A, None, A + 4, 4, 4, 4) == ALIAS and "f" in _err(lib)
+    assert _denoise(lib, A, A + 64, A + 4096, 4, 4, 4, ws=None) == WORKSPACE
+    assert _denoise(lib, A, None, B, 4, 4, 4, ws=0x30000000, wsb=16) == WORKSPACE
+    assert _denoise(lib, A, None, B, 4, 4, 4, ws=0x30000010, wsb=4096) == WORKSPACE and "aligned" in _err(lib)
+    assert _denoise(lib, A, None, B, 4, 4, 4, ws=B, wsb=4096) == ALIAS
+    assert _denoise(lib, A, None, B, 0, 0, 0) == OK
+
+
+def test_denoise_config_validation(lib):
+    cfg = wmc.Config(9, 0)
+    assert lib.wmc_denoise_ex(A, None, B, 4, 4, 4, 0, 1.0, 0.25, 3, 0, ctypes.byref(cfg), 0x30000000, 4096,
+                              None) == INVALID
+    cfg = wmc.Config(2, 3)
+    assert lib.wmc_denoise_ex(A, None, B, 4, 4, 4, 0, 1.0, 0.25, 3, 0, ctypes.byref(cfg), 0x30000000, 4096,
+                              None) == INVALID
+
+
+def test_energy_validation(lib):
+    assert lib.wmc_energy(A, None, None, 4, 4, 4, 0, 0, None, None, 0, None) == INVALID
+    assert lib.wmc_energy(None, None, None, 4, 4, 4, 0, 0, B, 0x30000000, 1 << 20, None) == INVALID
+    assert lib.wmc_energy(A, None, None, 4, 4, 4, 0, 0, B, None, 0, None) == WORKSPACE

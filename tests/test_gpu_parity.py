@@ -1,0 +1,261 @@
+"""GPU parity: libwmc.so (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Eval (Sec. IV-B, Eq. conv / Eq. act) is compared pixel by pixel with tie excusal; the flow
+(Sec. V-B, Eq. MCF) is compared one Jacobi step at a time from the GPU's own U^t (a flip of
+the selection at a near-tie makes long trajectories diverge locally, so per-step parity is
+the gate and whole-trajectory differences are checked against a looser bound and reported).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1903_07189_gb300 import synth
+from parity_util import TOL_REL, tie_check, value_range
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def wmc():
+    from paper_1903_07189_gb300 import wmc as m
+    return m
+
+
+def to_gpu(a, dtype=torch.float32, ld=None):
+    a = np.asarray(a, dtype=np.float32)
+    h, w = a.shape
+    if ld is None or ld == w:
+        return torch.from_numpy(a).to(DEV).to(dtype)
+    buf = torch.full((h, ld), float("nan"), dtype=dtype, device=DEV)
+    buf[:, :w] = torch.from_numpy(a).to(dtype)
+    return buf[:, :w]
+
+
+def host(t):
+    return t.float().cpu().numpy().astype(np.float64)
+
+
+def eval_parity(u32, bnd, ld=None, dtype=torch.float32):
+    ug = to_gpu(u32, dtype, ld)
+    uin = host(ug)  # exactly what the GPU read
+    hw = wmc().eval(ug, bnd)
+    torch.cuda.synchronize()
+    _, cand, _ = oracle.wmc_eval(uin, bnd, candidates=True)
+    R = value_range(uin)
+    extra = None
+    if dtype != torch.float32:
+        # output rounded to storage: half an ulp of the stored value
+        ulp = {torch.bfloat16: 2.0 ** -8, torch.float16: 2.0 ** -11}[dtype]
+        extra = np.abs(host(hw)) * ulp + 1e-30
+    ok, ties, err = tie_check(host(hw), cand, R, extra_tol=extra)
+    return ok, ties, err
+
+
+SHAPES = [(1, 1), (1, 9), (7, 1), (2, 2), (3, 5), (64, 64), (63, 65), (67, 129), (130, 61), (200, 333)]
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_eval_parity_shapes(shape, bnd):
+    u = synth.make_image(*shape, seed=sum(shape), sigma=0.05)
+    ok, ties, err = eval_parity(u, bnd)
+    assert ok.all(), (err, np.argwhere(~ok)[:5])
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_eval_parity_pitched(bnd):
+    u = synth.make_image(61, 70, seed=3, sigma=0.05)
+    ok, _, err = eval_parity(u, bnd, ld=96)
+    assert ok.all(), err
+
+
+def test_eval_parity_pr1_image():
+    """256 x 256, 8 bumps + 4 shapes, sigma 0.05, seed 0 (the small reference workload)."""
+    u = synth.pr1_image()
+    for bnd in ["replicate", "zero"]:
+        ok, ties, err = eval_parity(u, bnd)
+        assert ok.all(), (bnd, err)
+
+
+def test_eval_parity_structured_images():
+    """Ramps (exact opposite-sign ties everywhere), steps, integer images."""
+    y, x = np.mgrid[0:40, 0:50].astype(np.float64)
+    for u in [x + 2 * y, 3 * x - y, (x >= 20) * 1.0, (x + y >= 30) * 1.0, x ** 2 / 100,
+              np.random.default_rng(0).integers(0, 5, (40, 50)).astype(np.float64)]:
+        ok, _, err = eval_parity(u.astype(np.float32), "replicate")
+        assert ok.all(), err
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_eval_parity_reduced_storage(dtype):
+    u = synth.make_image(97, 131, seed=11, sigma=0.05)
+    ok, _, err = eval_parity(u, "replicate", dtype=dtype)
+    assert ok.all(), err
+
+
+def test_eval_full_size_sampled():
+    """4096 x 4096 (64 bumps, 32 shapes, sigma 0.02): 40000 random pixels plus the border."""
+    u = synth.scale_image(0.02)
+    ug = to_gpu(u)
+    hw = host(wmc().eval(ug))
+    uin = u.astype(np.float64)
+    rng = np.random.default_rng(5)
+    n = 40000
+    ys = np.concatenate([rng.integers(0, 4096, n), np.zeros(512, int), np.full(512, 4095),
+                         rng.integers(0, 4096, 1024)])
+    xs = np.concatenate([rng.integers(0, 4096, n), rng.integers(0, 4096, 1024),
+                         np.r_[np.zeros(512, int), np.full(512, 4095)]])
+    _, cand = oracle.eval_points(uin, ys, xs, candidates=True)
+    ok, _, err = tie_check(hw[ys, xs], cand, value_range(uin))
+    assert ok.all(), err
+
+
+# --------------------------------------------------------------------------- flows
+def step_parity(f32, lam, step, bnd, t_list, mcf=False, size_tag=""):
+    """GPU U^t, then one more GPU step, vs the oracle's step from the GPU's own U^t."""
+    fg = to_gpu(f32)
+    fin = host(fg)
+    R = value_range(fin)
+    for t in t_list:
+        if mcf:
+            ut = wmc().mcf(fg, step=step, iters=t, boundary=bnd)
+            ut1 = wmc().mcf(ut, step=step, iters=1, boundary=bnd)
+        else:
+            ut = wmc().denoise(fg, lam, step, t, bnd)
+            ut1 = wmc().denoise(fg, lam, step, 1, bnd, u0=ut)
+        U = host(ut)
+        _, cand, _ = oracle.wmc_eval(U, bnd, candidates=True)
+        mu = 0.0 if mcf else 1.0
+        tr = lambda c: U[..., None] + step * (lam * c - mu * (U[..., None] - fin[..., None]))
+        ok, ties, err = tie_check(host(ut1), cand, R, transform=tr)
+        assert ok.all(), (size_tag, t, err)
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_denoise_step_parity_pr1(bnd):
+    step_parity(synth.pr1_image(), 1.0, 0.25, bnd, [0, 1, 10, 50, 99])
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 40), (33, 1), (5, 7), (67, 129), (131, 70)])
+def test_denoise_step_parity_shapes(shape):
+    step_parity(synth.make_image(*shape, seed=13, sigma=0.08), 1.5, 0.2, "replicate", [0, 3, 9],
+                size_tag=shape)
+
+
+def test_mcf_step_parity():
+    step_parity(synth.make_image(90, 120, seed=14), 1.0, 0.4, "replicate", [0, 5, 20], mcf=True)
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_steps_per_launch_bitwise_invariant(bnd):
+    """T Jacobi steps in shared memory per launch give bit-identical results for T = 1..8
+    (every configuration performs the same FP32 operations per pixel)."""
+    f = to_gpu(synth.make_image(150, 173, seed=15, sigma=0.1))
+    ref = wmc().denoise(f, 1.0, 0.25, 17, bnd, steps_per_launch=1)
+    for T in range(2, 9):
+        got = wmc().denoise(f, 1.0, 0.25, 17, bnd, steps_per_launch=T)
+        assert torch.equal(got, ref), T
+
+
+def test_pr1_trajectory_vs_oracle():
+    """100 iterations, lambda 1, step 0.25, replicate: the whole FP32 trajectory against the
+    FP64 oracle from the same FP32 input.  Selection flips at near-ties make isolated pixels
+    differ by up to step*lambda*2|d|, so the gate is: at most 0.1% of the pixels beyond
+    1e-5 R, and the two results within 80 dB PSNR of each other."""
+    f = synth.pr1_image()
+    fg = to_gpu(f)
+    got = host(wmc().denoise(fg, 1.0, 0.25, 100))
+    want = oracle.denoise(host(fg), 1.0, 0.25, 100)
+    R = value_range(f)
+    d = np.abs(got - want)
+    frac = float((d > TOL_REL * R).mean())
+    mse = float((d ** 2).mean())
+    psnr = 10 * np.log10(R * R / mse) if mse > 0 else np.inf
+    print(f"PR1 trajectory: max {d.max():.3e}  p99.99 {np.quantile(d, 0.9999):.3e}  "
+          f"frac>tol {frac:.2e}  psnr {psnr:.1f} dB")
+    assert frac <= 1e-3
+    assert psnr >= 80
+
+
+def test_denoise_full_size_sampled_step():
+    """4096 x 4096: U^7 on the GPU (T = 4: one full launch + a 3-step remainder), then one more
+    step, checked at 40000 sampled pixels against the oracle's point-wise step."""
+    f = synth.scale_image(0.1)
+    fg = to_gpu(f)
+    ut = wmc().denoise(fg, 1.0, 0.25, 7)
+    ut1 = host(wmc().denoise(fg, 1.0, 0.25, 1, u0=ut))
+    U = host(ut)
+    rng = np.random.default_rng(6)
+    ys = np.concatenate([rng.integers(0, 4096, 40000), [0, 0, 4095, 4095]])
+    xs = np.concatenate([rng.integers(0, 4096, 40000), [0, 4095, 0, 4095]])
+    _, cand = oracle.eval_points(U, ys, xs, candidates=True)
+    Up, fp = U[ys, xs], f.astype(np.float64)[ys, xs]
+    tr = lambda c: Up[:, None] + 0.25 * (1.0 * c - (Up[:, None] - fp[:, None]))
+    ok, _, err = tie_check(ut1[ys, xs], cand, value_range(f), transform=tr)
+    assert ok.all(), err
+
+
+def test_full_size_properties():
+    """4096 x 4096, 20 steps: max principle (step (1 + lambda) <= 1), exact contrast
+    homogeneity for alpha = 2 and -0.5, run-to-run determinism."""
+    f = to_gpu(synth.scale_image(0.1))
+    u = wmc().denoise(f, 1.0, 0.25, 20)
+    assert float(u.min()) >= float(f.min()) and float(u.max()) <= float(f.max())
+    assert torch.equal(wmc().denoise(f, 1.0, 0.25, 20), u)
+    assert torch.equal(wmc().denoise(2 * f, 1.0, 0.25, 20), 2 * u)
+    assert torch.equal(wmc().denoise(-0.5 * f, 1.0, 0.25, 20), -0.5 * u)
+
+
+def test_resume_and_in_place():
+    f = to_gpu(synth.make_image(77, 91, seed=16))
+    full = wmc().denoise(f, 1.0, 0.25, 13)
+    part = wmc().denoise(f, 1.0, 0.25, 6)
+    rest = wmc().denoise(f, 1.0, 0.25, 7, u0=part)
+    assert torch.equal(rest, full)
+    # in place: u0 is u (odd and even launch counts, exercising the copy-back path)
+    for a, b in [(6, 7), (4, 9), (5, 8)]:
+        u = wmc().denoise(f, 1.0, 0.25, a)
+        wmc().denoise(f, 1.0, 0.25, b, u0=u, out=u)
+        assert torch.equal(u, full), (a, b)
+
+
+def test_zero_iterations_copies():
+    f = to_gpu(synth.make_image(20, 30, seed=17))
+    assert torch.equal(wmc().denoise(f, 1.0, 0.25, 0), f)
+
+
+def test_energy_parity():
+    f, clean = synth.make_image(300, 217, seed=18, sigma=0.1, return_clean=True)
+    fg, cg = to_gpu(f), to_gpu(clean)
+    ug = wmc().denoise(fg, 1.0, 0.25, 10)
+    e = wmc().energy(ug, fg, cg).cpu().numpy()
+    want = oracle.energies(host(ug), host(fg), host(cg))
+    np.testing.assert_allclose(e, want, rtol=2e-6)
+    e2 = wmc().energy(ug, fg, cg).cpu().numpy()
+    assert np.array_equal(e, e2)  # fixed summation order
+
+
+def test_host_entry_point_matches_device():
+    f = synth.make_image(129, 257, seed=19)
+    fh = torch.from_numpy(f).pin_memory()
+    out = wmc().denoise_host(fh, 1.0, 0.25, 11)
+    torch.cuda.synchronize()
+    ref = wmc().denoise(torch.from_numpy(f).to(DEV), 1.0, 0.25, 11).cpu()
+    assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_reduced_storage_step(dtype):
+    """One step with BF16/FP16 storage: FP32 arithmetic on the widened inputs, then one
+    round-to-nearest-even store; within half an ulp of the stored value of the oracle step."""
+    f = to_gpu(synth.make_image(111, 97, seed=20, sigma=0.05), dtype)
+    u1 = wmc().denoise(f, 1.0, 0.25, 1)
+    F = host(f)
+    _, cand, _ = oracle.wmc_eval(F, candidates=True)
+    ulp = {torch.bfloat16: 2.0 ** -8, torch.float16: 2.0 ** -11}[dtype]
+    g = host(u1)
+    tr = lambda c: F[..., None] + 0.25 * c
+    ok, _, err = tie_check(g, cand, value_range(F), transform=tr, extra_tol=np.abs(g) * ulp)
+    assert ok.all(), err
