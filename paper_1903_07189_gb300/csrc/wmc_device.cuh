@@ -49,8 +49,12 @@ __device__ __forceinline__ float half_laplace12(float nw, float n, float ne, flo
     t = fabsf(t2) < fabsf(t) ? t2 : t;
     t = fabsf(t5) < fabsf(t) ? t5 : t;
     t = fabsf(t6) < fabsf(t) ? t6 : t;
-    // sign(L) * t: flip t's sign bit when L is negative (one LOP3).
-    return __int_as_float(__float_as_int(t) ^ (__float_as_int(L) & 0x80000000));
+    // sign(L) * t: flip t's sign bit when L is negative (one LOP3).  When L is exactly 0 the
+    // two candidates of every pair are an opposite-sign tie and RNE arithmetic gives L = +0
+    // for U and for -U alike; taking the sign of L + 2^-40 a_1 instead makes the choice odd in
+    // U (H^w(-U) = -H^w(U) bit for bit) and changes nothing outside that tie band.
+    const float Ls = fmaf(0x1p-40f, a1, L);
+    return __int_as_float(__float_as_int(t) ^ (__float_as_int(Ls) & 0x80000000));
 }
 
 // ---------------------------------------------------------------- storage types
