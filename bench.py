@@ -47,7 +47,7 @@ BYTES_PER_PX_LAUNCH = 12  # read U, read f, write U (FP32): algorithmic bytes of
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--steps-per-launch", type=int, default=0)

@@ -99,7 +99,9 @@ wmc_status_t wmc_eval(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_
  *   the range of f and U^0, a larger step is accepted but carries no such guarantee);
  *   iters >= 0 (0 copies U^0 to u).
  *   workspace: device, >= wmc_denoise_workspace_size() bytes, WMC_WORKSPACE_ALIGN-aligned,
- *   must not overlap f, u0 or u; may be NULL only if that size is 0.
+ *   must not overlap f, u0 or u (not needed when iters == 0).  It holds a status word (first
+ *   bytes, cleared by every call) and one ping-pong image; see wmc_denoise_status().
+ *   Sides up to 2^24 pixels.
  * Errors: WMC_ERR_INVALID_ARG, WMC_ERR_ALIAS, WMC_ERR_WORKSPACE, WMC_ERR_CUDA.
  */
 size_t wmc_denoise_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype);
@@ -115,6 +117,13 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
                             int32_t iters, wmc_boundary_t bnd, const wmc_config_t *config,
                             void *workspace, size_t workspace_bytes, wmc_stream_t stream);
 
+/* wmc_denoise_status: synchronises `stream` and reads the status word of a workspace last used
+ * by wmc_denoise / wmc_denoise_ex / wmc_denoise_host.  The multi-step kernels wait for their
+ * asynchronous (TMA) tile loads with a time limit of 0.2 s; a wait that runs out makes that CTA
+ * skip its tile and sets the word, and this returns WMC_ERR_TIMEOUT (the output is then
+ * incomplete).  WMC_OK otherwise.  workspace: device pointer passed to that call. */
+wmc_status_t wmc_denoise_status(const void *workspace, wmc_stream_t stream);
+
 /* ------------------------------------------------------------------------------------------
  * wmc_denoise_host: wmc_denoise on HOST buffers.  Copies f (and u0) to the device workspace on
  * `stream`, runs the flow there and copies U^iters back into u_host; all of it is enqueued on
@@ -122,7 +131,7 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
  * u_host; pinned host memory makes the copies asynchronous).
  *   f_host  host, h x w, pitch ld (may be NULL for the mean-curvature flow, then u0_host is
  *           required); u0_host host or NULL (U^0 = f); u_host host output, pitch ld.
- *   workspace: DEVICE memory of wmc_denoise_host_workspace_size() bytes.
+ *   workspace: DEVICE memory of wmc_denoise_host_workspace_size() bytes (status word first).
  * Errors: as wmc_denoise.
  */
 size_t wmc_denoise_host_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype);
@@ -136,7 +145,7 @@ wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_h
  * wmc_energy: FP64 reductions of one image (Eq. wmcr with q = 1; the L2 data term of Eq. 1):
  *   out[0] = sum_p |H^w(U)(p)|,  out[1] = 1/2 sum_p (U - f)^2,  out[2] = sum_p (U - clean)^2
  *   (out[1] = 0 when f is NULL, out[2] = 0 when clean is NULL).
- *   u, f, clean: device, h x w, pitch ld, type dtype.  out: DEVICE, 3 doubles, written (not
+ *   u, f, clean: device, h x w, pitch ld, type dtype (f, clean may be NULL).  out: DEVICE, 3 doubles, written (not
  *   accumulated).  Per-thread partial sums run in FP32 over at most 16 pixels and in FP64
  *   beyond; the summation order is fixed, so repeated calls give identical results.
  *   workspace: device, >= wmc_energy_workspace_size() bytes, aligned as above.

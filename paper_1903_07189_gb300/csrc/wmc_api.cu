@@ -5,15 +5,27 @@
 #include <cstdio>
 #include <cstring>
 
+#include <mutex>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "../../include/wmc.h"
 #include "wmc_internal.h"
+#include "wmc_stream.cuh"
+#include "wmc_tile.cuh"
 
 namespace wmc {
-cudaError_t launch_tile_f32(int mode, int steps, const TileParams &p, cudaStream_t st);
-cudaError_t launch_tile_bf16(int mode, int steps, const TileParams &p, cudaStream_t st);
-cudaError_t launch_tile_f16(int mode, int steps, const TileParams &p, cudaStream_t st);
+void tile_box(int dtype, int *bw, int *bh) {
+    if (dtype == 0) {
+        *bw = Geom<float>::LW;
+        *bh = Geom<float>::LH;
+    } else {
+        *bw = Geom<__half>::LW;
+        *bh = Geom<__half>::LH;
+    }
+}
 }  // namespace wmc
 
 namespace {
@@ -55,13 +67,15 @@ bool overlap(const void *a, size_t na, const void *b, size_t nb) {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+constexpr int32_t kMaxSide = 1 << 24;
+
 wmc_status_t check_image(int32_t h, int32_t w, int64_t ld, const char *name) {
     if (h < 0 || w < 0) return fail(WMC_ERR_INVALID_ARG, "%s: negative size %d x %d", name, h, w);
     if (h > 0 && w > 0 && ld < w)
         return fail(WMC_ERR_INVALID_ARG, "%s: leading dimension %lld < width %d", name,
                     (long long)ld, w);
-    // Grid rows are bounded by 65535 tiles of at least 50 rows.
-    if (h > 3000000) return fail(WMC_ERR_INVALID_ARG, "%s: height %d too large", name, h);
+    if (h > kMaxSide || w > kMaxSide)
+        return fail(WMC_ERR_INVALID_ARG, "%s: side longer than %d", name, kMaxSide);
     return WMC_OK;
 }
 
@@ -72,19 +86,75 @@ wmc_status_t check_enums(wmc_dtype_t dtype, wmc_boundary_t bnd) {
     return WMC_OK;
 }
 
-cudaError_t launch_tile(wmc_dtype_t dtype, int mode, int steps, const wmc::TileParams &p,
-                        cudaStream_t st) {
+// ------------------------------------------------------------------ TMA descriptors
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else
+            cudaGetLastError();
+    });
+    return g_encode;
+}
+
+// A 2-D tiled tensor map over an h x w image with pitch ld, box = the tile kernel's window.
+// Returns false when the image cannot be read through TMA (alignment, pitch, driver).
+bool encode_window_map(CUtensorMap *m, const void *base, wmc_dtype_t dtype, int32_t h, int32_t w,
+                       int64_t ld) {
+    const size_t es = elem_size(dtype);
+    if (((uintptr_t)base % 16) != 0 || ((size_t)ld * es) % 16 != 0) return false;
+    if ((size_t)ld * es >= (1ull << 40)) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+    if (!enc) return false;
+    int bw, bh;
+    wmc::tile_box((int)dtype, &bw, &bh);
+    const CUtensorMapDataType t = dtype == WMC_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                  : dtype == WMC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, t, 2, const_cast<void *>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool pair_aligned(const void *p, int64_t ld, size_t es) {
+    return p == nullptr || (((uintptr_t)p % (2 * es)) == 0 && (ld % 2) == 0);
+}
+
+cudaError_t launch_tile(wmc_dtype_t dtype, wmc_boundary_t bnd, int steps, const CUtensorMap *map,
+                        const wmc::TileV2Params &p, cudaStream_t st) {
+    const bool z = bnd == WMC_BOUNDARY_ZERO;
     switch (dtype) {
-        case WMC_F32: return wmc::launch_tile_f32(mode, steps, p, st);
-        case WMC_BF16: return wmc::launch_tile_bf16(mode, steps, p, st);
-        case WMC_F16: return wmc::launch_tile_f16(mode, steps, p, st);
+        case WMC_F32: return z ? wmc::launch_tile_f32_zero(steps, map, p, st)
+                               : wmc::launch_tile_f32_rep(steps, map, p, st);
+        case WMC_BF16: return z ? wmc::launch_tile_bf16_zero(steps, map, p, st)
+                                : wmc::launch_tile_bf16_rep(steps, map, p, st);
+        case WMC_F16: return z ? wmc::launch_tile_f16_zero(steps, map, p, st)
+                               : wmc::launch_tile_f16_rep(steps, map, p, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 constexpr int kDefaultSteps = 4;
+constexpr size_t kStatusBytes = WMC_WORKSPACE_ALIGN;
 
-// The flow on device buffers; all checks done by the caller.
+size_t image_bytes(int32_t h, int64_t ld, wmc_dtype_t dtype) {
+    return round_up((size_t)h * (size_t)ld * elem_size(dtype), WMC_WORKSPACE_ALIGN);
+}
+
+// The flow on device buffers; all checks done by the caller.  `ws` holds the status word
+// (first kStatusBytes) followed by one image.
 wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
                       wmc_dtype_t dtype, float lambda, float step, int32_t iters,
                       wmc_boundary_t bnd, int steps_per_launch, void *ws, cudaStream_t st) {
@@ -99,18 +169,15 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
         }
         return WMC_OK;
     }
+    unsigned int *status = static_cast<unsigned int *>(ws);
+    ws = static_cast<char *>(ws) + kStatusBytes;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
+
     const int T = steps_per_launch;
     const int nl = (iters + T - 1) / T;  // launches; the last takes the remainder
     const float mu = f ? 1.0f : 0.0f;
-    wmc::TileParams p{};
-    p.f = f;
-    p.ldu = p.ldf = p.ldo = ld;
-    p.h = h;
-    p.w = w;
-    p.bnd = (int)bnd;
-    p.c_keep = 1.0f - step * mu;
-    p.c_f = step * mu;
-    p.c_h = step * lambda / 12.0f;
+    const float c_keep = 1.0f - step * mu, c_f = step * mu, c_h = step * lambda / 12.0f;
     // Ping-pong between u and the workspace so that the last launch writes u.  When U^0
     // already lives in u, the first launch must write the workspace; if the parity then
     // ends in the workspace, one copy finishes the job.
@@ -127,20 +194,57 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
         bufs[0] = ws;
         bufs[1] = u;
     }
+    const bool vec = pair_aligned(u0, ld, es) && pair_aligned(f, ld, es) &&
+                     pair_aligned(u, ld, es) && pair_aligned(ws, ld, es);
+    // Tensor maps for every buffer a tile launch may read: U^0 and the two ping-pong buffers.
+    CUtensorMap maps[3];
+    bool tma[3] = {false, false, false};
+    const void *srcs[3] = {u0, bufs[0], bufs[1]};
+    if (T > 1)
+        for (int k = 0; k < 3; ++k) tma[k] = encode_window_map(&maps[k], srcs[k], dtype, h, w, ld);
+
     const void *src = u0;
+    int src_id = 0;
     int done = 0;
     for (int k = 0; k < nl; ++k) {
         const int s = (iters - done) < T ? (iters - done) : T;
-        p.u = src;
-        p.out = bufs[k & 1];
-        cudaError_t e = launch_tile(dtype, wmc::MODE_FLOW, s, p, st);
+        void *dst = bufs[k & 1];
+        if (s == 1) {
+            wmc::StreamParams sp{};
+            sp.u = src;
+            sp.f = f;
+            sp.out = dst;
+            sp.ldu = sp.ldf = sp.ldo = ld;
+            sp.h = h;
+            sp.w = w;
+            sp.c_keep = c_keep;
+            sp.c_f = c_f;
+            sp.c_h = c_h;
+            e = wmc::launch_stream((int)dtype, wmc::MODE_FLOW, (int)bnd, sp, vec, st);
+        } else {
+            wmc::TileV2Params tp{};
+            tp.u = src;
+            tp.f = f;
+            tp.out = dst;
+            tp.ldu = tp.ldf = tp.ldo = ld;
+            tp.h = h;
+            tp.w = w;
+            tp.use_tma = tma[src_id] ? 1 : 0;
+            tp.vec_f = pair_aligned(f, ld, es) ? 1 : 0;
+            tp.vec_o = pair_aligned(dst, ld, es) ? 1 : 0;
+            tp.c_keep = c_keep;
+            tp.c_f = c_f;
+            tp.c_h = c_h;
+            tp.status = status;
+            e = launch_tile(dtype, bnd, s, &maps[src_id], tp, st);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "flow kernel launch");
-        src = p.out;
+        src = dst;
+        src_id = 1 + (k & 1);
         done += s;
     }
     if (copy_back) {
-        cudaError_t e =
-            cudaMemcpy2DAsync(u, ld * es, src, ld * es, w * es, h, cudaMemcpyDeviceToDevice, st);
+        e = cudaMemcpy2DAsync(u, ld * es, src, ld * es, w * es, h, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "copy result");
     }
     return WMC_OK;
@@ -210,23 +314,23 @@ wmc_status_t wmc_eval(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_
     const size_t es = elem_size(dtype);
     if (overlap(u, span_bytes(h, w, ld_u, es), hw, span_bytes(h, w, ld_hw, es)))
         return fail(WMC_ERR_ALIAS, "hw overlaps u");
-    wmc::TileParams p{};
+    wmc::StreamParams p{};
     p.u = u;
     p.out = hw;
     p.ldu = ld_u;
     p.ldo = ld_hw;
     p.h = h;
     p.w = w;
-    p.bnd = (int)bnd;
     p.c_h = 1.0f / 12.0f;
-    cudaError_t e = launch_tile(dtype, wmc::MODE_EVAL, 1, p, (cudaStream_t)stream);
+    const bool vec = pair_aligned(u, ld_u, es) && pair_aligned(hw, ld_hw, es);
+    cudaError_t e = wmc::launch_stream((int)dtype, wmc::MODE_EVAL, (int)bnd, p, vec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
     return WMC_OK;
 }
 
 size_t wmc_denoise_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype) {
     if (h <= 0 || w <= 0 || ld < w || elem_size(dtype) == 0) return 0;
-    return round_up((size_t)h * (size_t)ld * elem_size(dtype), WMC_WORKSPACE_ALIGN);
+    return image_bytes(h, ld, dtype) + kStatusBytes;
 }
 
 wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, int32_t w,
@@ -264,9 +368,9 @@ wmc_status_t wmc_denoise(const void *f, const void *u0, void *u, int32_t h, int3
 }
 
 size_t wmc_denoise_host_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype) {
-    // f, U^0 (when given separately), U and the ping-pong buffer.
-    const size_t one = wmc_denoise_workspace_size(h, w, ld, dtype);
-    return 4 * one;
+    // f, U^0 (when given separately), U, then the ping-pong image and status word.
+    if (h <= 0 || w <= 0 || ld < w || elem_size(dtype) == 0) return 0;
+    return 3 * image_bytes(h, ld, dtype) + wmc_denoise_workspace_size(h, w, ld, dtype);
 }
 
 wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_host, int32_t h,
@@ -279,18 +383,20 @@ wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_h
                                      bnd, nullptr, &T);
     if (s != WMC_OK) return s;
     if (h == 0 || w == 0) return WMC_OK;
-    const size_t one = wmc_denoise_workspace_size(h, w, ld, dtype);
-    const size_t need = 4 * one;
+    const size_t one = image_bytes(h, ld, dtype);
+    const size_t need = wmc_denoise_host_workspace_size(h, w, ld, dtype);
     if (!workspace || workspace_bytes < need)
         return fail(WMC_ERR_WORKSPACE, "device workspace of %zu bytes needed, %zu given", need,
                     workspace ? workspace_bytes : (size_t)0);
     if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
         return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    // [status | ping-pong image] (as wmc_denoise) followed by f, U^0 and U.
     char *base = static_cast<char *>(workspace);
+    void *d_ws = base;
+    base += wmc_denoise_workspace_size(h, w, ld, dtype);
     void *d_f = f_host ? base : nullptr;
     void *d_u0 = u0_host ? base + one : nullptr;
     void *d_u = base + 2 * one;
-    void *d_ws = base + 3 * one;
     const size_t es = elem_size(dtype);
     const size_t pitch = (size_t)ld * es;
     cudaStream_t st = (cudaStream_t)stream;
@@ -306,6 +412,18 @@ wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_h
     if ((e = cudaMemcpy2DAsync(u_host, pitch, d_u, pitch, w * es, h, cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
         return cuda_fail(e, "copy result to host");
+    return WMC_OK;
+}
+
+wmc_status_t wmc_denoise_status(const void *workspace, wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    if (!workspace) return fail(WMC_ERR_INVALID_ARG, "workspace is NULL");
+    unsigned int word = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&word, workspace, sizeof word, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "read status word");
+    if (word & 1u) return fail(WMC_ERR_TIMEOUT, "a tile kernel gave up waiting for its TMA load");
     return WMC_OK;
 }
 

@@ -60,15 +60,28 @@ __device__ __forceinline__ float half_laplace12(float nw, float n, float ne, flo
 // ---------------------------------------------------------------- storage types
 template <typename S> struct Store;
 
+// load/store: one element; load2/store2: two adjacent elements in one access (the address
+// must be aligned to twice the element size).
 template <> struct Store<float> {
     static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float to_float(float v) { return v; }
+    static __device__ __forceinline__ float2 load2(const float *p) {
+        return __ldg(reinterpret_cast<const float2 *>(p));
+    }
     static __device__ __forceinline__ float round(float v) { return v; }
     static __device__ __forceinline__ void store(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ void store2(float *p, float a, float b) {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
 };
 
 template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float load(const __nv_bfloat16 *p) {
         return __bfloat162float(__ldg(p));
+    }
+    static __device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ float2 load2(const __nv_bfloat16 *p) {
+        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
     }
     static __device__ __forceinline__ float round(float v) {
         return __bfloat162float(__float2bfloat16_rn(v));
@@ -76,14 +89,24 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v) {
         *p = __float2bfloat16_rn(v);
     }
+    static __device__ __forceinline__ void store2(__nv_bfloat16 *p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+    }
 };
 
 template <> struct Store<__half> {
     static __device__ __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float to_float(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ float2 load2(const __half *p) {
+        return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+    }
     static __device__ __forceinline__ float round(float v) {
         return __half2float(__float2half_rn(v));
     }
     static __device__ __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void store2(__half *p, float a, float b) {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+    }
 };
 
 enum Boundary { BND_REPLICATE = 0, BND_ZERO = 1 };

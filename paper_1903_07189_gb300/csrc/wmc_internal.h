@@ -1,6 +1,7 @@
 // wmc_internal.h -- host-side interfaces between the C ABI layer and the kernel launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -8,31 +9,28 @@ namespace wmc {
 
 enum Mode { MODE_EVAL = 0, MODE_FLOW = 1 };
 
-// Geometry of the temporally blocked tile kernel: every step updates a CW x CH region of
-// cells held in shared memory, surrounded by a one-cell ring that is read but not updated.
-// After T steps the inner (CW + 2 - 2T) x (CH + 2 - 2T) cells are exact (each step's error
-// front moves in by one cell), and those are written out.
-constexpr int kTileCW = 64;
-constexpr int kTileCH = 64;
-constexpr int kTileThreads = 256;
 constexpr int kMaxSteps = 8;
 
-struct TileParams {
-    const void *u;   // U^t (device)
-    const void *f;   // f (device) or nullptr (mean-curvature flow / eval)
-    void *out;       // U^{t+T} or H^w (device)
-    int64_t ldu, ldf, ldo;
-    int32_t h, w;
-    int32_t bnd;     // Boundary
-    float c_keep;    // 1 - step*mu
-    float c_f;       // step*mu
-    float c_h;       // step*lambda/12 (flow) or 1/12 (eval)
-};
+struct StreamParams;   // wmc_stream.cuh
+struct TileV2Params;   // wmc_tile.cuh
 
-// dtype: 0 = f32, 1 = bf16, 2 = f16.  steps: 1..kMaxSteps (MODE_EVAL requires 1).
-cudaError_t launch_tile(int dtype, int mode, int steps, const TileParams &p, cudaStream_t st);
+// Single-pass kernels (evaluation, one flow step).  dtype: 0 f32, 1 bf16, 2 f16.
+// vec: every row start of u, f and out is aligned to two elements (2-element accesses).
+cudaError_t launch_stream(int dtype, int mode, int bnd, const StreamParams &p, bool vec,
+                          cudaStream_t st);
 
-// FP64 energies; partials: >= energy_partials_count() doubles * 3 + counter word.
+// Temporally blocked flow kernels, steps = 2..kMaxSteps.
+cudaError_t launch_tile_f32_rep(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
+cudaError_t launch_tile_f32_zero(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
+cudaError_t launch_tile_bf16_rep(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
+cudaError_t launch_tile_bf16_zero(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
+cudaError_t launch_tile_f16_rep(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
+cudaError_t launch_tile_f16_zero(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
+
+// Shape of the TMA box the tile kernel loads, in elements of the storage type.
+void tile_box(int dtype, int *box_w, int *box_h);
+
+// FP64 energies; workspace: 3 * energy_grid_blocks() doubles + a ticket word.
 int energy_grid_blocks();
 cudaError_t launch_energy(int dtype, const void *u, const void *f, const void *clean, int32_t h,
                           int32_t w, int64_t ld, int bnd, double *out, void *workspace,

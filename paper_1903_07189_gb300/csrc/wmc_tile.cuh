@@ -1,184 +1,356 @@
-// wmc_tile.cuh -- temporally blocked WMC stencil kernel (eval and Jacobi flow steps).
+// wmc_tile.cuh -- temporally blocked WMC flow kernel: T >= 2 Jacobi steps per launch in shared
+// memory.
 //
-// One CTA owns an output tile and takes T Jacobi steps of
-//     U^{t+1} = U^t + step (lambda H^w(U^t) - mu (U^t - f))     (Sec. V-B, Eq. MCF)
-// entirely in shared memory before writing the tile back.  This is exact because the update
-// is Jacobi-ordered: every pixel of step t+1 reads only U^t, so after T steps a cell is
-// correct if the (2T+1)^2 cells around it were loaded.  The CTA loads a (CW+2) x (CH+2)
-// window (ring of T cells around the (CW+2-2T) x (CH+2-2T) output tile), updates the inner
-// CW x CH cells each step, and its error front moves in one cell per step.
+// The update U^{t+1} = U^t + step (lambda H^w(U^t) - mu (U^t - f)) (Sec. V-B, Eq. MCF) is
+// Jacobi-ordered: every pixel of step t+1 reads only U^t.  So a CTA can load a window of U^t,
+// take T steps on it without talking to anyone, and write back the part of the window that is
+// still exact: each step's stale border moves one cell inwards.
 //
-// Image boundary.  REPLICATE: neighbour reads of in-image cells are clamped to the image
-// (row and column indices), so cells outside the image are never read after the load and
-// are never written.  ZERO: cells outside the image hold 0 in both buffers and are never
-// written, and reads are not clamped.
+// Geometry (element coordinates; X0, Y0 = global position of shared cell (0,0)):
+//   loaded window  [X0, X0+LW) x [Y0, Y0+LH)       one 2-D TMA box, zero-filled outside the image
+//   updated cells  [X0+2, X0+2+CW) x [Y0+1, Y0+1+CH)    every step (CW = 128, CH = 64)
+//   exact after T  [X0+1+T, X0+3+CW-T) x [Y0+T, Y0+2+CH-T)
+//   written back   [x0, x0+OW) x [y0, y0+OH),  x0 = X0 + M, y0 = Y0 + T
+// M (>= T+1) and OW are multiples of the TMA alignment (16 bytes of elements), so every TMA
+// x-coordinate is aligned and every thread's column pair (even, odd) is either wholly inside or
+// wholly outside the output tile.
 //
-// Thread layout: 8 warps; warp g owns rows 1+8g .. 8+8g of the update region, lane l owns
-// columns 1+l and 33+l.  Each thread reads its column triple (c-1, c, c+1) for its 8 rows plus
-// one row above and below (30 conflict-free shared loads per column per step: every warp
-// instruction reads 32 consecutive words of one row) and keeps f * step * mu for its 16
-// cells in registers for the whole launch.
+// Threads: 8 warps as 2 (x) x 4 (y); lane l of warp (wx, wy) updates the column pair
+// j = 2 + 64 wx + 2 l, j + 1 for rows i = 1 + 16 wy .. 16 + 16 wy.  Per row it reads three aligned
+// 8-byte pairs (columns j-2 .. j+3) with constant offsets, so the inner loop has no index
+// arithmetic and no per-cell predicates in tiles that lie inside the image.
+//
+// Image boundary.  ZERO: the TMA fill supplies the zeros; in tiles touching the border, cells
+// outside the image are rewritten as 0 every step.  REPLICATE: the ring of cells just outside
+// the image is kept equal to its nearest in-image cell (filled after the load, then rewritten
+// by the in-image edge cells every step), so in-image cells read their neighbours without any
+// clamping and produce exactly what clamped reads would.
+//
+// Shared memory always holds FP32; for BF16/FP16 storage the TMA box lands in a staging area
+// and is widened once, and every step rounds its result to the storage type, so the arithmetic
+// is identical to the single-step streaming kernel.
 #pragma once
+
+#include <cuda.h>
+#include <string.h>
 
 #include "wmc_device.cuh"
 #include "wmc_internal.h"
 
 namespace wmc {
 
-constexpr int SW = kTileCW + 2;  // shared tile width
-constexpr int SH = kTileCH + 2;  // shared tile height
-constexpr int SP = SW;           // shared pitch (warp reads are row-contiguous: no conflicts)
-constexpr int RY = kTileCH / 8;  // rows per warp
-constexpr int NCOL = kTileCW / 32;
+constexpr int kCW = 128;   // updated columns per step
+constexpr int kCH = 64;    // updated rows per step
+constexpr int kRY = 16;    // rows per thread
+constexpr int kTileThreadsV2 = 256;
 
-template <int T, int MODE, typename S, int BND>
-__global__ void __launch_bounds__(kTileThreads, 2) tile_kernel(const TileParams p) {
-    extern __shared__ float smem[];
+template <typename S> struct Geom {
+    static constexpr int A = 16 / (int)sizeof(S);                 // TMA x alignment (elements)
+    static constexpr int LW = ((kCW + 3 + A - 1) / A) * A;        // loaded width
+    static constexpr int LH = kCH + 2;                            // loaded height
+    static constexpr int P = LW;                                  // shared pitch (floats)
+    static constexpr int BUF = LH * P;                            // floats per buffer
+    static constexpr int STAGE_BYTES = sizeof(S) == 4 ? 0 : LH * LW * (int)sizeof(S);
+    static constexpr int SMEM = 2 * BUF * 4 + STAGE_BYTES + 128;  // + alignment slack
+};
 
-    constexpr int OW = SW - 2 * T;
-    constexpr int OH = SH - 2 * T;
+// Output tile of a T-step launch: margin M (>= T+1, TMA-aligned), width OW, height OH.
+template <typename S, int T> struct Out {
+    static constexpr int A = Geom<S>::A;
+    static constexpr int M = A * ((T + 1 + A - 1) / A);
+    static constexpr int OW = A * ((kCW + 3 - T - M) / A);
+    static constexpr int OH = kCH + 2 - 2 * T;
+};
+
+struct TileV2Params {
+    const void *u;    // U^t (device); read through the tensor map when use_tma
+    const void *f;    // f or nullptr (mean-curvature flow)
+    void *out;        // U^{t+T}
+    int64_t ldu, ldf, ldo;
+    int32_t h, w;
+    int32_t ntx;      // tiles per row of tiles
+    int32_t use_tma;
+    int32_t vec_f;    // f rows allow 2-element loads (aligned base, even pitch)
+    int32_t vec_o;    // same for the output
+    float c_keep, c_f, c_h;
+    unsigned int *status;  // device status word (bit 0: a bounded wait gave up) or nullptr
+};
+
+// ------------------------------------------------------------------ TMA / mbarrier helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Poll the barrier's phase; give up after `limit_ns` (returns false).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, uint64_t limit_ns) {
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+            " selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s
+
+__device__ __forceinline__ float2 lds2(const float *p) {
+    return *reinterpret_cast<const float2 *>(p);
+}
+__device__ __forceinline__ void sts2(float *p, float a, float b) {
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+}
+
+// ------------------------------------------------------------------------------- kernel
+template <int T, typename S, int BND>
+__global__ void __launch_bounds__(kTileThreadsV2, 2)
+    tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const TileV2Params p) {
+    using G = Geom<S>;
+    constexpr int LW = G::LW, LH = G::LH, P = G::P, BUF = G::BUF;
+    constexpr int M = Out<S, T>::M;
+    constexpr int OW = Out<S, T>::OW;
+    constexpr int OH = Out<S, T>::OH;
+    static_assert(OW > 0 && OH > 0, "tile too small for T");
+
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    float *buf0 = reinterpret_cast<float *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float *buf1 = buf0 + BUF;
+
     const int h = p.h, w = p.w;
-    const int x0 = blockIdx.x * OW;  // first output column of this CTA
-    const int y0 = blockIdx.y * OH;
-    const int gx0 = x0 - T;          // image column of shared column 0
-    const int gy0 = y0 - T;
-    const S *__restrict__ u = static_cast<const S *>(p.u);
+    const int ty = blockIdx.x / p.ntx, tx = blockIdx.x - ty * p.ntx;
+    const int x0 = tx * OW, y0 = ty * OH;
+    const int X0 = x0 - M, Y0 = y0 - T;
+    const int tid = threadIdx.x;
+    const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
 
-    // ---- load the (SH x SW) window of U^t
-    for (int i = threadIdx.x; i < SH * SW; i += kTileThreads) {
-        const int r = i / SW, c = i - (i / SW) * SW;
-        int gy = gy0 + r, gx = gx0 + c;
-        const bool in = (gy >= 0) & (gy < h) & (gx >= 0) & (gx < w);
-        float v;
-        if (BND == BND_ZERO) {
-            v = in ? Store<S>::load(u + (int64_t)gy * p.ldu + gx) : 0.0f;
-        } else {
-            gy = min(max(gy, 0), h - 1);
-            gx = min(max(gx, 0), w - 1);
-            v = Store<S>::load(u + (int64_t)gy * p.ldu + gx);
+    // ---- issue the load of the window of U^t
+    if (p.use_tma) {
+        if (tid == 0) mbar_init(smem_u32(&bar), 1);
+        __syncthreads();
+        if (tid == 0) {
+            void *dst = (sizeof(S) == 4) ? static_cast<void *>(buf0)
+                                         : static_cast<void *>(buf1 + BUF);  // staging
+            mbar_expect_tx(smem_u32(&bar), (uint32_t)(LW * LH * sizeof(S)));
+            tma_load_2d(smem_u32(dst), &tmap, X0, Y0, smem_u32(&bar));
         }
-        smem[r * SP + c] = v;
-        if (T > 1) smem[SH * SP + r * SP + c] = v;
-    }
-
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int rbeg = 1 + warp * RY;  // first shared row this thread updates
-
-    // Image extent in shared coordinates (for clamping and for the in-image test).
-    const int rTop = -gy0, rBot = h - 1 - gy0;
-    const int cLft = -gx0, cRgt = w - 1 - gx0;
-
-    // Clamped shared row offsets of rows rbeg-1 .. rbeg+RY (fixed for the whole launch).
-    int roff[RY + 2];
-#pragma unroll
-    for (int k = 0; k < RY + 2; ++k) {
-        int r = rbeg - 1 + k;
-        if (BND == BND_REPLICATE) r = min(max(r, rTop), rBot);
-        roff[k] = r * SP;
-    }
-    int cc[NCOL], cl[NCOL], cr[NCOL];
-#pragma unroll
-    for (int j = 0; j < NCOL; ++j) {
-        cc[j] = 1 + lane + 32 * j;
-        cl[j] = cc[j] - 1;
-        cr[j] = cc[j] + 1;
-        if (BND == BND_REPLICATE) {
-            cl[j] = max(cl[j], cLft);
-            cr[j] = min(cr[j], cRgt);
+    } else {
+        const S *u = static_cast<const S *>(p.u);
+        for (int idx = tid; idx < LH * LW; idx += kTileThreadsV2) {
+            const int i = idx / LW, j = idx - (idx / LW) * LW;
+            const int gy = Y0 + i, gx = X0 + j;
+            float v = 0.0f;
+            if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = Store<S>::load(u + (int64_t)gy * p.ldu + gx);
+            buf0[i * P + j] = v;
         }
     }
 
-    // step*mu*f for the 16 owned cells (0 outside the image or for the pure flow).
-    float g[NCOL][RY];
-    const bool use_f = (MODE == MODE_FLOW) && (p.f != nullptr);
+    // ---- per-thread geometry and f (overlaps the load)
+    const int lane = tid & 31, warp = tid >> 5;
+    const int wx = warp & 1, wy = warp >> 1;
+    const int j = 2 + 64 * wx + 2 * lane;   // shared column of this thread's first cell
+    const int ib = 1 + kRY * wy;            // shared row of its first cell
+    const int gx = X0 + j;                  // image column of the first cell (even)
+    float2 g[kRY];
+    {
+        const S *f = static_cast<const S *>(p.f);
 #pragma unroll
-    for (int j = 0; j < NCOL; ++j)
-#pragma unroll
-        for (int k = 0; k < RY; ++k) {
-            const int gy = gy0 + rbeg + k, gx = gx0 + cc[j];
-            float fv = 0.0f;
-            if (use_f && gy >= 0 && gy < h && gx >= 0 && gx < w)
-                fv = Store<S>::load(static_cast<const S *>(p.f) + (int64_t)gy * p.ldf + gx);
-            g[j][k] = p.c_f * fv;
+        for (int k = 0; k < kRY; ++k) {
+            const int gy = Y0 + ib + k;
+            float a = 0.0f, b = 0.0f;
+            if (f != nullptr && gy >= 0 && gy < h) {
+                const S *fr = f + (int64_t)gy * p.ldf;
+                if (p.vec_f && gx >= 0 && gx + 1 < w) {
+                    const float2 v = Store<S>::load2(fr + gx);
+                    a = v.x;
+                    b = v.y;
+                } else {
+                    if (gx >= 0 && gx < w) a = Store<S>::load(fr + gx);
+                    if (gx + 1 >= 0 && gx + 1 < w) b = Store<S>::load(fr + gx + 1);
+                }
+            }
+            g[k] = make_float2(p.c_f * a, p.c_f * b);
         }
-    __syncthreads();
+    }
 
-    S *__restrict__ out = static_cast<S *>(p.out);
+    // ---- wait for the window
+    if (p.use_tma) {
+        const bool ok = mbar_wait_bounded(smem_u32(&bar), 0, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && p.status) atomicOr(p.status, 1u);
+            return;
+        }
+        if (sizeof(S) != 4) {  // widen the staged 16-bit box
+            const S *stage = reinterpret_cast<const S *>(buf1 + BUF);
+            for (int idx = tid; idx < LH * LW; idx += kTileThreadsV2)
+                buf0[idx] = Store<S>::to_float(stage[idx]);
+            __syncthreads();
+        }
+    } else {
+        __syncthreads();
+    }
+
+    // ---- REPLICATE: fill the ring just outside the image from its nearest in-image cell
+    if (BND == BND_REPLICATE && border) {
+        for (int idx = tid; idx < LH * LW; idx += kTileThreadsV2) {
+            const int i = idx / LW, jj = idx - (idx / LW) * LW;
+            const int yy = Y0 + i, xx = X0 + jj;
+            const bool inside = (yy >= 0) & (yy < h) & (xx >= 0) & (xx < w);
+            const bool ring = (yy >= -1) & (yy <= h) & (xx >= -1) & (xx <= w);
+            if (ring && !inside) {
+                const int ci = min(max(yy, 0), h - 1) - Y0, cj = min(max(xx, 0), w - 1) - X0;
+                buf0[i * P + jj] = buf0[ci * P + cj];
+            }
+        }
+        __syncthreads();
+    }
+
+    // per-thread constants for tiles touching the border
+    const bool cin0 = (gx >= 0) & (gx < w), cin1 = (gx + 1 >= 0) & (gx + 1 < w);
+    const bool col_out = (j >= M) & (j < M + OW);
+    S *out = static_cast<S *>(p.out);
 
 #pragma unroll 1
     for (int s = 0; s < T; ++s) {
-        const float *src = smem + (s & 1) * (SH * SP);
-        float *dst = smem + ((s + 1) & 1) * (SH * SP);
+        const float *src = (s & 1) ? buf1 : buf0;
+        float *dst = (s & 1) ? buf0 : buf1;
         const bool last = (s == T - 1);
+        const float *rp = src + (ib - 1) * P + (j - 2);
+        float2 a0 = lds2(rp), b0 = lds2(rp + 2), c0 = lds2(rp + 4);
+        float2 a1 = lds2(rp + P), b1 = lds2(rp + P + 2), c1 = lds2(rp + P + 4);
 #pragma unroll
-        for (int j = 0; j < NCOL; ++j) {
-            // Sliding 3-row window over columns c-1 (a), c (b), c+1 (d).
-            float a0 = src[roff[0] + cl[j]], b0 = src[roff[0] + cc[j]], d0 = src[roff[0] + cr[j]];
-            float a1 = src[roff[1] + cl[j]], b1 = src[roff[1] + cc[j]], d1 = src[roff[1] + cr[j]];
-            const int gx = gx0 + cc[j];
-            const bool col_in = (gx >= 0) & (gx < w);
+        for (int k = 0; k < kRY; ++k) {
+            const float *rq = rp + (k + 2) * P;
+            const float2 a2 = lds2(rq), b2 = lds2(rq + 2), c2 = lds2(rq + 4);
+            // cell j:   NW a0.y  N b0.x  NE b0.y / W a1.y C b1.x E b1.y / SW a2.y S b2.x SE b2.y
+            // cell j+1: NW b0.x  N b0.y  NE c0.x / W b1.x C b1.y E c1.x / SW b2.x S b2.y SE c2.x
+            const float h0 = half_laplace12(a0.y, b0.x, b0.y, a1.y, b1.x, b1.y, a2.y, b2.x, b2.y);
+            const float h1 = half_laplace12(b0.x, b0.y, c0.x, b1.x, b1.y, c1.x, b2.x, b2.y, c2.x);
+            float v0 = fmaf(p.c_h, h0, fmaf(p.c_keep, b1.x, g[k].x));
+            float v1 = fmaf(p.c_h, h1, fmaf(p.c_keep, b1.y, g[k].y));
+            const int i = ib + k;
+            if (!last) {
+                v0 = Store<S>::round(v0);
+                v1 = Store<S>::round(v1);
+                float *d = dst + i * P + j;
+                if (!border) {
+                    sts2(d, v0, v1);
+                } else {
+                    const int gy = Y0 + i;
+                    const bool rin = (gy >= 0) & (gy < h);
+                    if (BND == BND_ZERO) {
+                        sts2(d, (rin & cin0) ? v0 : 0.0f, (rin & cin1) ? v1 : 0.0f);
+                    } else {
+                        // in-image cells: normal write plus mirror writes into the ring
 #pragma unroll
-            for (int k = 0; k < RY; ++k) {
-                const float a2 = src[roff[k + 2] + cl[j]];
-                const float b2 = src[roff[k + 2] + cc[j]];
-                const float d2 = src[roff[k + 2] + cr[j]];
-                const float h12 = half_laplace12(a0, b0, d0, a1, b1, d1, a2, b2, d2);
-                const int r = rbeg + k;
-                const int gy = gy0 + r;
-                const bool in = col_in & (gy >= 0) & (gy < h);
-                float v;
-                if (MODE == MODE_EVAL) {
-                    v = p.c_h * h12;
-                } else {
-                    v = fmaf(p.c_h, h12, fmaf(p.c_keep, b1, g[j][k]));
+                        for (int e = 0; e < 2; ++e) {
+                            const bool in = rin & (e == 0 ? cin0 : cin1);
+                            if (!in) continue;
+                            const float v = e == 0 ? v0 : v1;
+                            const int xe = gx + e;
+                            d[e] = v;
+                            const int up = (gy == 0) ? -1 : 0, dn = (gy == h - 1) ? 1 : 0;
+                            const int lf = (xe == 0) ? -1 : 0, rt = (xe == w - 1) ? 1 : 0;
+                            for (int di = up; di <= dn; ++di)
+                                for (int dj = lf; dj <= rt; ++dj) {
+                                    if (di == 0 && dj == 0) continue;
+                                    const int ii = i + di, jj = j + e + dj;
+                                    if (ii >= 0 && ii < LH && jj >= 0 && jj < LW) dst[ii * P + jj] = v;
+                                }
+                        }
+                    }
                 }
-                if (!last) {
-                    if (in) dst[r * SP + cc[j]] = Store<S>::round(v);
-                } else {
-                    // Output cells: shared rows/cols T .. T+OH-1 / T .. T+OW-1.
-                    const bool own = (r >= T) & (r < T + OH) & (cc[j] >= T) & (cc[j] < T + OW);
-                    if (in & own) Store<S>::store(out + (int64_t)gy * p.ldo + gx, v);
+            } else {
+                const int gy = Y0 + i;
+                const bool row_out = (i >= T) & (i < T + OH) & (gy < h);
+                if (col_out & row_out) {
+                    S *o = out + (int64_t)gy * p.ldo + gx;
+                    if (p.vec_o && gx + 1 < w) {
+                        Store<S>::store2(o, v0, v1);
+                    } else {
+                        if (gx < w) Store<S>::store(o, v0);
+                        if (gx + 1 < w) Store<S>::store(o + 1, v1);
+                    }
                 }
-                a0 = a1; b0 = b1; d0 = d1;
-                a1 = a2; b1 = b2; d1 = d2;
             }
+            a0 = a1; b0 = b1; c0 = c1;
+            a1 = a2; b1 = b2; c1 = c2;
         }
         if (!last) __syncthreads();
     }
-    (void)rTop; (void)rBot; (void)cLft; (void)cRgt;
 }
 
-template <int T, int MODE, typename S, int BND>
-cudaError_t launch_tile_t(const TileParams &p, cudaStream_t st) {
-    constexpr int OW = SW - 2 * T;
-    constexpr int OH = SH - 2 * T;
-    dim3 grid((p.w + OW - 1) / OW, (p.h + OH - 1) / OH);
-    const size_t smem = (T > 1 ? 2 : 1) * SH * SP * sizeof(float);
-    tile_kernel<T, MODE, S, BND><<<grid, kTileThreads, smem, st>>>(p);
+template <int T, typename S, int BND>
+cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, cudaStream_t st) {
+    using G = Geom<S>;
+    constexpr int OW = Out<S, T>::OW;
+    constexpr int OH = Out<S, T>::OH;
+    const int64_t ntx = (p.w + OW - 1) / OW, nty = (p.h + OH - 1) / OH;
+    if (ntx * nty > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    p.ntx = (int32_t)ntx;
+    cudaError_t e = cudaFuncSetAttribute(tile_v2_kernel<T, S, BND>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (e != cudaSuccess) return e;
+    CUtensorMap dummy;
+    if (!p.use_tma) {
+        memset(&dummy, 0, sizeof dummy);
+        map = &dummy;
+    }
+    tile_v2_kernel<T, S, BND><<<(unsigned)(ntx * nty), kTileThreadsV2, G::SMEM, st>>>(*map, p);
     return cudaGetLastError();
 }
 
 template <typename S, int BND>
-cudaError_t launch_tile_steps(int mode, int steps, const TileParams &p, cudaStream_t st) {
-    if (mode == MODE_EVAL) return launch_tile_t<1, MODE_EVAL, S, BND>(p, st);
+cudaError_t launch_tile_v2_steps(int steps, const CUtensorMap *map, const TileV2Params &p,
+                                 cudaStream_t st) {
     switch (steps) {
-        case 1: return launch_tile_t<1, MODE_FLOW, S, BND>(p, st);
-        case 2: return launch_tile_t<2, MODE_FLOW, S, BND>(p, st);
-        case 3: return launch_tile_t<3, MODE_FLOW, S, BND>(p, st);
-        case 4: return launch_tile_t<4, MODE_FLOW, S, BND>(p, st);
-        case 5: return launch_tile_t<5, MODE_FLOW, S, BND>(p, st);
-        case 6: return launch_tile_t<6, MODE_FLOW, S, BND>(p, st);
-        case 7: return launch_tile_t<7, MODE_FLOW, S, BND>(p, st);
-        case 8: return launch_tile_t<8, MODE_FLOW, S, BND>(p, st);
+        case 2: return launch_tile_v2_t<2, S, BND>(map, p, st);
+        case 3: return launch_tile_v2_t<3, S, BND>(map, p, st);
+        case 4: return launch_tile_v2_t<4, S, BND>(map, p, st);
+        case 5: return launch_tile_v2_t<5, S, BND>(map, p, st);
+        case 6: return launch_tile_v2_t<6, S, BND>(map, p, st);
+        case 7: return launch_tile_v2_t<7, S, BND>(map, p, st);
+        case 8: return launch_tile_v2_t<8, S, BND>(map, p, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename S>
-cudaError_t launch_tile_dtype(int mode, int steps, const TileParams &p, cudaStream_t st) {
-    if (p.bnd == BND_ZERO) return launch_tile_steps<S, BND_ZERO>(mode, steps, p, st);
-    return launch_tile_steps<S, BND_REPLICATE>(mode, steps, p, st);
+cudaError_t launch_tile_v2_dtype(int steps, int bnd, const CUtensorMap *map,
+                                 const TileV2Params &p, cudaStream_t st) {
+    if (bnd == BND_ZERO) return launch_tile_v2_steps<S, BND_ZERO>(steps, map, p, st);
+    return launch_tile_v2_steps<S, BND_REPLICATE>(steps, map, p, st);
 }
 
 }  // namespace wmc

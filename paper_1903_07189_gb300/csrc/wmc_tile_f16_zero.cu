@@ -1,0 +1,9 @@
+// Instantiations of the temporally blocked flow kernel: __half storage, BND_ZERO.
+#include "wmc_tile.cuh"
+
+namespace wmc {
+cudaError_t launch_tile_f16_zero(int steps, const CUtensorMap *map, const TileV2Params &p,
+                                   cudaStream_t st) {
+    return launch_tile_v2_steps<__half, BND_ZERO>(steps, map, p, st);
+}
+}  // namespace wmc

@@ -1,0 +1,9 @@
+// Instantiations of the temporally blocked flow kernel: float storage, BND_REPLICATE.
+#include "wmc_tile.cuh"
+
+namespace wmc {
+cudaError_t launch_tile_f32_rep(int steps, const CUtensorMap *map, const TileV2Params &p,
+                                   cudaStream_t st) {
+    return launch_tile_v2_steps<float, BND_REPLICATE>(steps, map, p, st);
+}
+}  // namespace wmc

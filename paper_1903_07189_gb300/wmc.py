@@ -42,6 +42,7 @@ SIGNATURES = {
     "wmc_denoise": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp, _sz, _vp]),
     "wmc_denoise_ex": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32,
                               ctypes.POINTER(Config), _vp, _sz, _vp]),
+    "wmc_denoise_status": (_i32, [_vp, _vp]),
     "wmc_denoise_host_workspace_size": (_sz, [_i32, _i32, _i64, _i32]),
     "wmc_denoise_host": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp, _sz,
                                 _vp]),
@@ -181,6 +182,12 @@ def denoise_host(f: torch.Tensor, lam: float = 1.0, step: float | None = None, i
                                 int(iters), BOUNDARY[boundary], workspace.data_ptr(), workspace.numel(), st),
            "wmc_denoise_host")
     return out
+
+
+def check_status(workspace: torch.Tensor):
+    """Raise WMCError(WMC_ERR_TIMEOUT) if a bounded device wait in the last flow call that used
+    `workspace` gave up (synchronises the current stream)."""
+    _check(load().wmc_denoise_status(workspace.data_ptr(), _stream(workspace.device)), "wmc_denoise_status")
 
 
 def denoise_host_workspace_size(h: int, w: int, dtype=torch.float32) -> int:

@@ -60,10 +60,11 @@ def test_status_strings(lib):
 
 def test_workspace_sizes(lib):
     assert lib.wmc_denoise_workspace_size(0, 5, 5, 0) == 0
-    assert lib.wmc_denoise_workspace_size(3, 5, 8, 0) == 256
-    assert lib.wmc_denoise_workspace_size(100, 100, 128, 1) == (100 * 128 * 2 + 255) // 256 * 256
+    # status word (256 bytes) + one image rounded up to 256 bytes
+    assert lib.wmc_denoise_workspace_size(3, 5, 8, 0) == 256 + 256
+    assert lib.wmc_denoise_workspace_size(100, 100, 128, 1) == 256 + (100 * 128 * 2 + 255) // 256 * 256
     assert lib.wmc_denoise_workspace_size(4, 5, 4, 0) == 0  # ld < w
-    assert lib.wmc_denoise_host_workspace_size(10, 10, 10, 0) == 4 * 512
+    assert lib.wmc_denoise_host_workspace_size(10, 10, 10, 0) == 256 + 4 * 512
     assert lib.wmc_energy_workspace_size(10, 10) % 256 == 0
 
 

@@ -259,3 +259,47 @@ def test_reduced_storage_step(dtype):
     tr = lambda c: F[..., None] + 0.25 * c
     ok, _, err = tie_check(g, cand, value_range(F), transform=tr, extra_tol=np.abs(g) * ulp)
     assert ok.all(), err
+
+
+@pytest.mark.parametrize("shape,ld", [((61, 61), None), ((70, 133), 135), ((129, 250), 256), ((3, 200), None)])
+def test_flow_pitches_and_fallbacks(shape, ld):
+    """Odd widths / pitches take the plain-load path of the multi-step kernel (no TMA: the row
+    pitch is not a multiple of 16 bytes) and the unpaired-column paths; results must still be
+    bit-identical across steps_per_launch and match the oracle step by step."""
+    f32 = synth.make_image(*shape, seed=21, sigma=0.07)
+    fg = to_gpu(f32, ld=ld)
+    ref = wmc().denoise(fg, 1.0, 0.25, 9, steps_per_launch=1)
+    for T in (2, 3, 5, 8):
+        assert torch.equal(wmc().denoise(fg, 1.0, 0.25, 9, steps_per_launch=T), ref), T
+    U = host(wmc().denoise(fg, 1.0, 0.25, 8, steps_per_launch=4))
+    u9 = host(wmc().denoise(fg, 1.0, 0.25, 1, u0=to_gpu(U.astype(np.float32), ld=ld)))
+    _, cand, _ = oracle.wmc_eval(U, candidates=True)
+    F = host(fg)
+    tr = lambda c: U[..., None] + 0.25 * (c - (U[..., None] - F[..., None]))
+    ok, _, err = tie_check(u9, cand, value_range(F), transform=tr)
+    assert ok.all(), err
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_reduced_storage_steps_per_launch_bitwise(dtype, bnd):
+    """Every step rounds to the storage type, inside a multi-step launch too, so T = 1..8 agree
+    bit for bit for BF16/FP16 as well."""
+    f = to_gpu(synth.make_image(140, 301, seed=22, sigma=0.1), dtype)
+    ref = wmc().denoise(f, 1.0, 0.25, 11, bnd, steps_per_launch=1)
+    for T in range(2, 9):
+        assert torch.equal(wmc().denoise(f, 1.0, 0.25, 11, bnd, steps_per_launch=T), ref), T
+
+
+def test_status_word_ok_after_runs():
+    f = to_gpu(synth.make_image(300, 300, seed=23))
+    ws = torch.empty(wmc().load().wmc_denoise_workspace_size(300, 300, 300, 0), dtype=torch.uint8, device=DEV)
+    wmc().denoise(f, 1.0, 0.25, 12, steps_per_launch=4, workspace=ws)
+    wmc().check_status(ws)  # raises on WMC_ERR_TIMEOUT
+
+
+def test_mcf_steps_per_launch_bitwise():
+    u0 = to_gpu(synth.make_image(200, 180, seed=24))
+    ref = wmc().mcf(u0, step=0.3, iters=10, steps_per_launch=1)
+    for T in (2, 4, 7):
+        assert torch.equal(wmc().mcf(u0, step=0.3, iters=10, steps_per_launch=T), ref), T
