@@ -231,7 +231,7 @@ def run_gpu(args):
     peak, peak_kind = peaks()
     achieved = BYTES_PER_PX_LAUNCH * H * W / (launch_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"wmc::tile_kernel<T={T}> (flow)", "peak_kind": peak_kind,
+                "traffic": None, "kernel": f"wmc::tile_v2_kernel<T={T}> (flow)" if T > 1 else "wmc::stream_kernel (flow step)", "peak_kind": peak_kind,
                 "launch_ms": launch_ms,
                 "effective_gbs_per_iter": BYTES_PER_PX_LAUNCH * H * W * T / (launch_ms * 1e-3) / 1e9}
 

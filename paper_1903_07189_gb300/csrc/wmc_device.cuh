@@ -27,6 +27,25 @@
 
 namespace wmc {
 
+// Selection of Eq. act from the ×12 Laplacian L and odd parts a_j (j = 1, 2, 5, 6): the t_j =
+// |L| - |a_j| of least magnitude, with the sign of L.  Ties between the t_j keep the first in
+// the order 1, 2, 5, 6.  When L is exactly 0 the two candidates of every pair are an
+// opposite-sign tie and RNE arithmetic gives L = +0 for U and for -U alike; taking the sign of
+// L + 2^-40 a_1 instead makes the choice odd in U (H^w(-U) = -H^w(U) bit for bit) and changes
+// nothing outside that tie band.
+__device__ __forceinline__ float select12(float L, float a1, float a2, float a5, float a6) {
+    const float aL = fabsf(L);
+    float t = aL - fabsf(a1);
+    const float t2 = aL - fabsf(a2);
+    const float t5 = aL - fabsf(a5);
+    const float t6 = aL - fabsf(a6);
+    t = fabsf(t2) < fabsf(t) ? t2 : t;
+    t = fabsf(t5) < fabsf(t) ? t5 : t;
+    t = fabsf(t6) < fabsf(t) ? t6 : t;
+    const float Ls = fmaf(0x1p-40f, a1, L);
+    return __int_as_float(__float_as_int(t) ^ (__float_as_int(Ls) & 0x80000000));
+}
+
 // 12 * H^w at the centre of a 3x3 neighbourhood (rows: n* above, s* below).
 __device__ __forceinline__ float half_laplace12(float nw, float n, float ne, float w, float c,
                                                 float e, float sw, float s, float se) {
@@ -41,20 +60,34 @@ __device__ __forceinline__ float half_laplace12(float nw, float n, float ne, flo
     const float a2 = fmaf(2.0f, p, A + B);
     const float a5 = fmaf(2.0f, p + q, A);
     const float a6 = fmaf(2.0f, p - q, B);
-    const float aL = fabsf(L);
-    float t = aL - fabsf(a1);
-    const float t2 = aL - fabsf(a2);
-    const float t5 = aL - fabsf(a5);
-    const float t6 = aL - fabsf(a6);
-    t = fabsf(t2) < fabsf(t) ? t2 : t;
-    t = fabsf(t5) < fabsf(t) ? t5 : t;
-    t = fabsf(t6) < fabsf(t) ? t6 : t;
-    // sign(L) * t: flip t's sign bit when L is negative (one LOP3).  When L is exactly 0 the
-    // two candidates of every pair are an opposite-sign tie and RNE arithmetic gives L = +0
-    // for U and for -U alike; taking the sign of L + 2^-40 a_1 instead makes the choice odd in
-    // U (H^w(-U) = -H^w(U) bit for bit) and changes nothing outside that tie band.
-    const float Ls = fmaf(0x1p-40f, a1, L);
-    return __int_as_float(__float_as_int(t) ^ (__float_as_int(Ls) & 0x80000000));
+    return select12(L, a1, a2, a5, a6);
+}
+
+// The same for two cells at once (lane .x = one cell, .y = the other): the twenty linear
+// operations run as packed FP32x2 instructions (sm_100+), each lane rounding exactly as the
+// scalar operation above (a - b is computed as fma(b, -1, a), which is exact in the product),
+// so both forms give bit-identical results.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 half_laplace12_x2(float2 nw, float2 n, float2 ne, float2 w,
+                                                    float2 c, float2 e, float2 sw, float2 s,
+                                                    float2 se) {
+    const float2 two = make_float2(2.0f, 2.0f);
+    const float2 m12 = make_float2(-12.0f, -12.0f);
+    const float2 p = sub2(n, s);
+    const float2 q = sub2(w, e);
+    const float2 A = sub2(nw, se);
+    const float2 B = sub2(ne, sw);
+    const float2 corners = __fadd2_rn(__fadd2_rn(nw, se), __fadd2_rn(ne, sw));
+    const float2 edges = __fadd2_rn(__fadd2_rn(n, s), __fadd2_rn(w, e));
+    const float2 L = __ffma2_rn(m12, c, __ffma2_rn(two, edges, corners));
+    const float2 a1 = __ffma2_rn(two, q, sub2(A, B));
+    const float2 a2 = __ffma2_rn(two, p, __fadd2_rn(A, B));
+    const float2 a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
+    const float2 a6 = __ffma2_rn(two, sub2(p, q), B);
+    return make_float2(select12(L.x, a1.x, a2.x, a5.x, a6.x),
+                       select12(L.y, a1.y, a2.y, a5.y, a6.y));
 }
 
 // ---------------------------------------------------------------- storage types

@@ -18,7 +18,7 @@
 namespace wmc {
 
 constexpr int kStreamWarps = 8;
-constexpr int kStreamRY = 16;
+constexpr int kStreamRY = 8;
 
 struct StreamParams {
     const void *u;
@@ -51,29 +51,18 @@ __device__ __forceinline__ float load_one(const S *__restrict__ row, int x, int 
     return Store<S>::load(row + min(max(x, 0), w - 1));
 }
 
-// Columns x-1 .. x+2 of one row: .x = x-1, .y = x, .z = x+1, .w = x+2.
-template <typename S, int BND, bool VEC>
-__device__ __forceinline__ float4 load_row(const S *__restrict__ base, int64_t ld, int y, int h,
-                                           int x, int w, int lane) {
-    bool row_ok = true;
-    if (BND == BND_ZERO) {
-        row_ok = (y >= 0) & (y < h);
-        y = min(max(y, 0), h - 1);  // keep the address valid; values are zeroed
-    } else {
-        y = min(max(y, 0), h - 1);
-    }
-    const S *row = base + (int64_t)y * ld;
-    const float2 v = load_pair<S, BND, VEC>(row, x, w, row_ok);
-    float left = __shfl_up_sync(0xffffffffu, v.y, 1);
-    float right = __shfl_down_sync(0xffffffffu, v.x, 1);
-    if (lane == 0) left = load_one<S, BND>(row, x - 1, w, row_ok);
-    if (lane == 31) right = load_one<S, BND>(row, x + 2, w, row_ok);
-    return make_float4(left, v.x, v.y, right);
+// Row index of strip row y under the boundary rule (REPLICATE: clamped; ZERO: clamped for a
+// valid address, with *ok = false marking a row of zeros).
+template <int BND>
+__device__ __forceinline__ int row_index(int y, int h, bool *ok) {
+    *ok = (BND == BND_REPLICATE) | ((y >= 0) & (y < h));
+    return min(max(y, 0), h - 1);
 }
 
 template <typename S, int BND, int MODE, bool VEC>
-__global__ void __launch_bounds__(kStreamWarps * 32)
+__global__ void __launch_bounds__(kStreamWarps * 32, 3)
     stream_kernel(const StreamParams p) {
+    constexpr int R = kStreamRY;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int w = p.w, h = p.h;
@@ -82,41 +71,65 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
     const int by = (int)(blockIdx.x / nbx), bx = (int)(blockIdx.x - (unsigned)by * nbx);
     const int x = ((bx * kStreamWarps + warp) * 32 + lane) * 2;
     if ((x & ~63) >= w) return;  // whole warp right of the image (warp-uniform)
-    const int y0 = by * kStreamRY;
+    const int y0 = by * R;
     const S *__restrict__ u = static_cast<const S *>(p.u);
     const S *__restrict__ f = static_cast<const S *>(p.f);
     S *__restrict__ out = static_cast<S *>(p.out);
 
-    float4 r0 = load_row<S, BND, VEC>(u, p.ldu, y0 - 1, h, x, w, lane);
-    float4 r1 = load_row<S, BND, VEC>(u, p.ldu, y0, h, x, w, lane);
+    // ---- issue every load of the strip first: R + 2 rows of pairs, the two outer columns
+    // (lanes 0 and 31 only) and the R rows of f
+    float2 v[R + 2];
+    float el[R + 2], er[R + 2];
 #pragma unroll
-    for (int k = 0; k < kStreamRY; ++k) {
+    for (int k = 0; k < R + 2; ++k) {
+        bool ok;
+        const int y = row_index<BND>(y0 - 1 + k, h, &ok);
+        const S *row = u + (int64_t)y * p.ldu;
+        v[k] = load_pair<S, BND, VEC>(row, x, w, ok);
+        el[k] = (lane == 0) ? load_one<S, BND>(row, x - 1, w, ok) : 0.0f;
+        er[k] = (lane == 31) ? load_one<S, BND>(row, x + 2, w, ok) : 0.0f;
+    }
+    float2 g[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        g[k] = make_float2(0.0f, 0.0f);
+        if (MODE == MODE_FLOW && f != nullptr && y0 + k < h)
+            g[k] = load_pair<S, BND_ZERO, VEC>(f + (int64_t)(y0 + k) * p.ldf, x, w, true);
+    }
+
+    // ---- neighbours across lanes, then the strip's R rows
+    float lf[R + 2], rt[R + 2];
+#pragma unroll
+    for (int k = 0; k < R + 2; ++k) {
+        lf[k] = __shfl_up_sync(0xffffffffu, v[k].y, 1);
+        rt[k] = __shfl_down_sync(0xffffffffu, v[k].x, 1);
+        if (lane == 0) lf[k] = el[k];
+        if (lane == 31) rt[k] = er[k];
+    }
+    const float2 ch = make_float2(p.c_h, p.c_h), ck = make_float2(p.c_keep, p.c_keep);
+    const float2 cf = make_float2(p.c_f, p.c_f);
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
         const int y = y0 + k;
-        const float4 r2 = load_row<S, BND, VEC>(u, p.ldu, y + 1, h, x, w, lane);
-        float2 g = make_float2(0.0f, 0.0f);
-        if (MODE == MODE_FLOW && f != nullptr && y < h)
-            g = load_pair<S, BND_ZERO, VEC>(f + (int64_t)y * p.ldf, x, w, true);
-        const float h0 = half_laplace12(r0.x, r0.y, r0.z, r1.x, r1.y, r1.z, r2.x, r2.y, r2.z);
-        const float h1 = half_laplace12(r0.y, r0.z, r0.w, r1.y, r1.z, r1.w, r2.y, r2.z, r2.w);
-        float v0, v1;
-        if (MODE == MODE_EVAL) {
-            v0 = p.c_h * h0;
-            v1 = p.c_h * h1;
-        } else {
-            v0 = fmaf(p.c_h, h0, fmaf(p.c_keep, r1.y, p.c_f * g.x));
-            v1 = fmaf(p.c_h, h1, fmaf(p.c_keep, r1.z, p.c_f * g.y));
-        }
+        // lanes: (cell x, cell x+1); row r columns x-1 .. x+2 are (lf, v.x, v.y, rt)
+        const float2 hw = half_laplace12_x2(
+            make_float2(lf[k], v[k].x), v[k], make_float2(v[k].y, rt[k]),
+            make_float2(lf[k + 1], v[k + 1].x), v[k + 1], make_float2(v[k + 1].y, rt[k + 1]),
+            make_float2(lf[k + 2], v[k + 2].x), v[k + 2], make_float2(v[k + 2].y, rt[k + 2]));
+        float2 o2;
+        if (MODE == MODE_EVAL)
+            o2 = __fmul2_rn(ch, hw);
+        else
+            o2 = __ffma2_rn(ch, hw, __ffma2_rn(ck, v[k + 1], __fmul2_rn(cf, g[k])));
         if (y < h) {
             S *o = out + (int64_t)y * p.ldo;
             if (VEC && x + 1 < w) {
-                Store<S>::store2(o + x, v0, v1);
+                Store<S>::store2(o + x, o2.x, o2.y);
             } else {
-                if (x < w) Store<S>::store(o + x, v0);
-                if (x + 1 < w) Store<S>::store(o + x + 1, v1);
+                if (x < w) Store<S>::store(o + x, o2.x);
+                if (x + 1 < w) Store<S>::store(o + x + 1, o2.y);
             }
         }
-        r0 = r1;
-        r1 = r2;
     }
 }
 

@@ -132,6 +132,87 @@ __device__ __forceinline__ void sts2(float *p, float a, float b) {
 }
 
 // ------------------------------------------------------------------------------- kernel
+// Per-thread constants of one tile.
+struct TileCtx {
+    int j, ib;         // shared column of the thread's first cell, shared row of its first row
+    int X0, Y0, gx;    // window origin, image column of the first cell
+    int h, w;
+    bool cin0, cin1;   // the two cells' columns lie inside the image
+};
+
+enum StepWrite { WRITE_INTERIOR = 0, WRITE_BORDER = 1, WRITE_GLOBAL = 2 };
+
+// One Jacobi step over the thread's kRY rows x 2 columns, reading `src`, writing `dst` (shared)
+// or the output image (last step).  The two cells run as the lanes of packed FP32x2 operations.
+template <int WMODE, int T, typename S, int BND>
+__device__ __forceinline__ void tile_step(const float *__restrict__ src, float *__restrict__ dst,
+                                          const TileCtx &c, const float2 (&g)[kRY],
+                                          const TileV2Params &p) {
+    using G = Geom<S>;
+    constexpr int P = G::P, LH = G::LH, LW = G::LW;
+    constexpr int M = Out<S, T>::M, OW = Out<S, T>::OW, OH = Out<S, T>::OH;
+    const float2 ch = make_float2(p.c_h, p.c_h), ck = make_float2(p.c_keep, p.c_keep);
+    const float *rp = src + (c.ib - 1) * P + (c.j - 2);
+    float2 a0 = lds2(rp), b0 = lds2(rp + 2), c0 = lds2(rp + 4);
+    float2 a1 = lds2(rp + P), b1 = lds2(rp + P + 2), c1 = lds2(rp + P + 4);
+    const bool col_out = (c.j >= M) & (c.j < M + OW);
+#pragma unroll
+    for (int k = 0; k < kRY; ++k) {
+        const float *rq = rp + (k + 2) * P;
+        const float2 a2 = lds2(rq), b2 = lds2(rq + 2), c2 = lds2(rq + 4);
+        // lanes: (cell j, cell j+1); shared columns j-2 .. j+3 are (a.x a.y b.x b.y c.x c.y)
+        const float2 hw = half_laplace12_x2(
+            make_float2(a0.y, b0.x), b0, make_float2(b0.y, c0.x),
+            make_float2(a1.y, b1.x), b1, make_float2(b1.y, c1.x),
+            make_float2(a2.y, b2.x), b2, make_float2(b2.y, c2.x));
+        float2 v = __ffma2_rn(ch, hw, __ffma2_rn(ck, b1, g[k]));
+        const int i = c.ib + k;
+        if (WMODE == WRITE_INTERIOR) {
+            sts2(dst + i * P + c.j, Store<S>::round(v.x), Store<S>::round(v.y));
+        } else if (WMODE == WRITE_BORDER) {
+            v.x = Store<S>::round(v.x);
+            v.y = Store<S>::round(v.y);
+            const int gy = c.Y0 + i;
+            const bool rin = (gy >= 0) & (gy < c.h);
+            if (BND == BND_ZERO) {
+                sts2(dst + i * P + c.j, (rin & c.cin0) ? v.x : 0.0f, (rin & c.cin1) ? v.y : 0.0f);
+            } else {
+                // in-image cells: normal write plus mirror writes into the ring outside the image
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const bool in = rin & (e == 0 ? c.cin0 : c.cin1);
+                    if (!in) continue;
+                    const float ve = e == 0 ? v.x : v.y;
+                    const int xe = c.gx + e;
+                    dst[i * P + c.j + e] = ve;
+                    const int up = (gy == 0) ? -1 : 0, dn = (gy == c.h - 1) ? 1 : 0;
+                    const int lf = (xe == 0) ? -1 : 0, rt = (xe == c.w - 1) ? 1 : 0;
+                    for (int di = up; di <= dn; ++di)
+                        for (int dj = lf; dj <= rt; ++dj) {
+                            if (di == 0 && dj == 0) continue;
+                            const int ii = i + di, jj = c.j + e + dj;
+                            if (ii >= 0 && ii < LH && jj >= 0 && jj < LW) dst[ii * P + jj] = ve;
+                        }
+                }
+            }
+        } else {
+            const int gy = c.Y0 + i;
+            const bool row_out = (i >= T) & (i < T + OH) & (gy < c.h);
+            if (col_out & row_out) {
+                S *o = static_cast<S *>(p.out) + (int64_t)gy * p.ldo + c.gx;
+                if (p.vec_o && c.gx + 1 < c.w) {
+                    Store<S>::store2(o, v.x, v.y);
+                } else {
+                    if (c.gx < c.w) Store<S>::store(o, v.x);
+                    if (c.gx + 1 < c.w) Store<S>::store(o + 1, v.y);
+                }
+            }
+        }
+        a0 = a1; b0 = b1; c0 = c1;
+        a1 = a2; b1 = b2; c1 = c2;
+    }
+}
+
 template <int T, typename S, int BND>
 __global__ void __launch_bounds__(kTileThreadsV2, 2)
     tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const TileV2Params p) {
@@ -178,16 +259,23 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
 
     // ---- per-thread geometry and f (overlaps the load)
     const int lane = tid & 31, warp = tid >> 5;
-    const int wx = warp & 1, wy = warp >> 1;
-    const int j = 2 + 64 * wx + 2 * lane;   // shared column of this thread's first cell
-    const int ib = 1 + kRY * wy;            // shared row of its first cell
-    const int gx = X0 + j;                  // image column of the first cell (even)
+    TileCtx c;
+    c.j = 2 + 64 * (warp & 1) + 2 * lane;
+    c.ib = 1 + kRY * (warp >> 1);
+    c.X0 = X0;
+    c.Y0 = Y0;
+    c.gx = X0 + c.j;
+    c.h = h;
+    c.w = w;
+    c.cin0 = (c.gx >= 0) & (c.gx < w);
+    c.cin1 = (c.gx + 1 >= 0) & (c.gx + 1 < w);
     float2 g[kRY];
     {
         const S *f = static_cast<const S *>(p.f);
+        const int gx = c.gx;
 #pragma unroll
         for (int k = 0; k < kRY; ++k) {
-            const int gy = Y0 + ib + k;
+            const int gy = Y0 + c.ib + k;
             float a = 0.0f, b = 0.0f;
             if (f != nullptr && gy >= 0 && gy < h) {
                 const S *fr = f + (int64_t)gy * p.ldf;
@@ -200,7 +288,7 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
                     if (gx + 1 >= 0 && gx + 1 < w) b = Store<S>::load(fr + gx + 1);
                 }
             }
-            g[k] = make_float2(p.c_f * a, p.c_f * b);
+            g[k] = __fmul2_rn(make_float2(p.c_f, p.c_f), make_float2(a, b));
         }
     }
 
@@ -236,79 +324,18 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
         __syncthreads();
     }
 
-    // per-thread constants for tiles touching the border
-    const bool cin0 = (gx >= 0) & (gx < w), cin1 = (gx + 1 >= 0) & (gx + 1 < w);
-    const bool col_out = (j >= M) & (j < M + OW);
-    S *out = static_cast<S *>(p.out);
-
+    // ---- T steps: ping-pong buf0 -> buf1 -> buf0 ...; the last one writes the output tile
 #pragma unroll 1
-    for (int s = 0; s < T; ++s) {
+    for (int s = 0; s < T - 1; ++s) {
         const float *src = (s & 1) ? buf1 : buf0;
         float *dst = (s & 1) ? buf0 : buf1;
-        const bool last = (s == T - 1);
-        const float *rp = src + (ib - 1) * P + (j - 2);
-        float2 a0 = lds2(rp), b0 = lds2(rp + 2), c0 = lds2(rp + 4);
-        float2 a1 = lds2(rp + P), b1 = lds2(rp + P + 2), c1 = lds2(rp + P + 4);
-#pragma unroll
-        for (int k = 0; k < kRY; ++k) {
-            const float *rq = rp + (k + 2) * P;
-            const float2 a2 = lds2(rq), b2 = lds2(rq + 2), c2 = lds2(rq + 4);
-            // cell j:   NW a0.y  N b0.x  NE b0.y / W a1.y C b1.x E b1.y / SW a2.y S b2.x SE b2.y
-            // cell j+1: NW b0.x  N b0.y  NE c0.x / W b1.x C b1.y E c1.x / SW b2.x S b2.y SE c2.x
-            const float h0 = half_laplace12(a0.y, b0.x, b0.y, a1.y, b1.x, b1.y, a2.y, b2.x, b2.y);
-            const float h1 = half_laplace12(b0.x, b0.y, c0.x, b1.x, b1.y, c1.x, b2.x, b2.y, c2.x);
-            float v0 = fmaf(p.c_h, h0, fmaf(p.c_keep, b1.x, g[k].x));
-            float v1 = fmaf(p.c_h, h1, fmaf(p.c_keep, b1.y, g[k].y));
-            const int i = ib + k;
-            if (!last) {
-                v0 = Store<S>::round(v0);
-                v1 = Store<S>::round(v1);
-                float *d = dst + i * P + j;
-                if (!border) {
-                    sts2(d, v0, v1);
-                } else {
-                    const int gy = Y0 + i;
-                    const bool rin = (gy >= 0) & (gy < h);
-                    if (BND == BND_ZERO) {
-                        sts2(d, (rin & cin0) ? v0 : 0.0f, (rin & cin1) ? v1 : 0.0f);
-                    } else {
-                        // in-image cells: normal write plus mirror writes into the ring
-#pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const bool in = rin & (e == 0 ? cin0 : cin1);
-                            if (!in) continue;
-                            const float v = e == 0 ? v0 : v1;
-                            const int xe = gx + e;
-                            d[e] = v;
-                            const int up = (gy == 0) ? -1 : 0, dn = (gy == h - 1) ? 1 : 0;
-                            const int lf = (xe == 0) ? -1 : 0, rt = (xe == w - 1) ? 1 : 0;
-                            for (int di = up; di <= dn; ++di)
-                                for (int dj = lf; dj <= rt; ++dj) {
-                                    if (di == 0 && dj == 0) continue;
-                                    const int ii = i + di, jj = j + e + dj;
-                                    if (ii >= 0 && ii < LH && jj >= 0 && jj < LW) dst[ii * P + jj] = v;
-                                }
-                        }
-                    }
-                }
-            } else {
-                const int gy = Y0 + i;
-                const bool row_out = (i >= T) & (i < T + OH) & (gy < h);
-                if (col_out & row_out) {
-                    S *o = out + (int64_t)gy * p.ldo + gx;
-                    if (p.vec_o && gx + 1 < w) {
-                        Store<S>::store2(o, v0, v1);
-                    } else {
-                        if (gx < w) Store<S>::store(o, v0);
-                        if (gx + 1 < w) Store<S>::store(o + 1, v1);
-                    }
-                }
-            }
-            a0 = a1; b0 = b1; c0 = c1;
-            a1 = a2; b1 = b2; c1 = c2;
-        }
-        if (!last) __syncthreads();
+        if (!border)
+            tile_step<WRITE_INTERIOR, T, S, BND>(src, dst, c, g, p);
+        else
+            tile_step<WRITE_BORDER, T, S, BND>(src, dst, c, g, p);
+        __syncthreads();
     }
+    tile_step<WRITE_GLOBAL, T, S, BND>(((T - 1) & 1) ? buf1 : buf0, nullptr, c, g, p);
 }
 
 template <int T, typename S, int BND>
