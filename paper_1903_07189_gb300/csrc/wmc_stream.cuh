@@ -111,16 +111,19 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 3)
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int y = y0 + k;
-        // lanes: (cell x, cell x+1); row r columns x-1 .. x+2 are (lf, v.x, v.y, rt)
-        const float2 hw = half_laplace12_x2(
-            make_float2(lf[k], v[k].x), v[k], make_float2(v[k].y, rt[k]),
-            make_float2(lf[k + 1], v[k + 1].x), v[k + 1], make_float2(v[k + 1].y, rt[k + 1]),
-            make_float2(lf[k + 2], v[k + 2].x), v[k + 2], make_float2(v[k + 2].y, rt[k + 2]));
+        // row r columns x-1 .. x+2 are (lf, v.x, v.y, rt); scalar arithmetic, since pairs of
+        // adjacent columns would need register shuffling for packed operands
+        const float h0 = half_laplace12(lf[k], v[k].x, v[k].y, lf[k + 1], v[k + 1].x,
+                                        v[k + 1].y, lf[k + 2], v[k + 2].x, v[k + 2].y);
+        const float h1 = half_laplace12(v[k].x, v[k].y, rt[k], v[k + 1].x, v[k + 1].y,
+                                        rt[k + 1], v[k + 2].x, v[k + 2].y, rt[k + 2]);
         float2 o2;
-        if (MODE == MODE_EVAL)
-            o2 = __fmul2_rn(ch, hw);
-        else
-            o2 = __ffma2_rn(ch, hw, __ffma2_rn(ck, v[k + 1], __fmul2_rn(cf, g[k])));
+        if (MODE == MODE_EVAL) {
+            o2 = make_float2(ch.x * h0, ch.x * h1);
+        } else {
+            o2.x = fmaf(ch.x, h0, fmaf(ck.x, v[k + 1].x, cf.x * g[k].x));
+            o2.y = fmaf(ch.x, h1, fmaf(ck.x, v[k + 1].y, cf.x * g[k].y));
+        }
         if (y < h) {
             S *o = out + (int64_t)y * p.ldo;
             if (VEC && x + 1 < w) {

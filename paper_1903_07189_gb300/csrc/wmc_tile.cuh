@@ -15,9 +15,12 @@
 // x-coordinate is aligned and every thread's column pair (even, odd) is either wholly inside or
 // wholly outside the output tile.
 //
-// Threads: 8 warps as 2 (x) x 4 (y); lane l of warp (wx, wy) updates the column pair
-// j = 2 + 64 wx + 2 l, j + 1 for rows i = 1 + 16 wy .. 16 + 16 wy.  Per row it reads three aligned
-// 8-byte pairs (columns j-2 .. j+3) with constant offsets, so the inner loop has no index
+// Threads: 8 warps as 2 (x) x 4 (y); lane l of warp (wx, wy) updates columns j = 2 + 64 wx + l
+// and j + 32 for rows i = 1 + 16 wy .. 16 + 16 wy.  The two columns are the two lanes of packed
+// FP32x2 arithmetic: every operand pair (west, centre, east neighbours of both cells) is read
+// by two conflict-free 4-byte shared loads straight into an aligned register pair, so no
+// register shuffling is needed (pairing the adjacent columns j, j+1 instead would make six of
+// the nine operands straddle register pairs).  Offsets are constants: the inner loop has no index
 // arithmetic and no per-cell predicates in tiles that lie inside the image.
 //
 // Image boundary.  ZERO: the TMA fill supplies the zeros; in tiles touching the border, cells
@@ -134,7 +137,7 @@ __device__ __forceinline__ void sts2(float *p, float a, float b) {
 // ------------------------------------------------------------------------------- kernel
 // Per-thread constants of one tile.
 struct TileCtx {
-    int j, ib;         // shared column of the thread's first cell, shared row of its first row
+    int j, ib;         // shared column of the thread's first cell (second: j + 32), first row
     int X0, Y0, gx;    // window origin, image column of the first cell
     int h, w;
     bool cin0, cin1;   // the two cells' columns lie inside the image
@@ -142,8 +145,20 @@ struct TileCtx {
 
 enum StepWrite { WRITE_INTERIOR = 0, WRITE_BORDER = 1, WRITE_GLOBAL = 2 };
 
+// Columns j-1, j, j+1 of one shared row for both lanes (j and j+32) as aligned pairs.
+struct Row3 {
+    float2 w, c, e;
+};
+__device__ __forceinline__ Row3 load_row3(const float *r) {
+    Row3 o;
+    o.w = make_float2(r[-1], r[31]);
+    o.c = make_float2(r[0], r[32]);
+    o.e = make_float2(r[1], r[33]);
+    return o;
+}
+
 // One Jacobi step over the thread's kRY rows x 2 columns, reading `src`, writing `dst` (shared)
-// or the output image (last step).  The two cells run as the lanes of packed FP32x2 operations.
+// or the output image (last step).
 template <int WMODE, int T, typename S, int BND>
 __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *__restrict__ dst,
                                           const TileCtx &c, const float2 (&g)[kRY],
@@ -152,64 +167,58 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
     constexpr int P = G::P, LH = G::LH, LW = G::LW;
     constexpr int M = Out<S, T>::M, OW = Out<S, T>::OW, OH = Out<S, T>::OH;
     const float2 ch = make_float2(p.c_h, p.c_h), ck = make_float2(p.c_keep, p.c_keep);
-    const float *rp = src + (c.ib - 1) * P + (c.j - 2);
-    float2 a0 = lds2(rp), b0 = lds2(rp + 2), c0 = lds2(rp + 4);
-    float2 a1 = lds2(rp + P), b1 = lds2(rp + P + 2), c1 = lds2(rp + P + 4);
-    const bool col_out = (c.j >= M) & (c.j < M + OW);
+    const float *rp = src + (c.ib - 1) * P + c.j;
+    Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
+    const bool col_out0 = (c.j >= M) & (c.j < M + OW);
+    const bool col_out1 = (c.j + 32 >= M) & (c.j + 32 < M + OW);
 #pragma unroll
     for (int k = 0; k < kRY; ++k) {
-        const float *rq = rp + (k + 2) * P;
-        const float2 a2 = lds2(rq), b2 = lds2(rq + 2), c2 = lds2(rq + 4);
-        // lanes: (cell j, cell j+1); shared columns j-2 .. j+3 are (a.x a.y b.x b.y c.x c.y)
-        const float2 hw = half_laplace12_x2(
-            make_float2(a0.y, b0.x), b0, make_float2(b0.y, c0.x),
-            make_float2(a1.y, b1.x), b1, make_float2(b1.y, c1.x),
-            make_float2(a2.y, b2.x), b2, make_float2(b2.y, c2.x));
-        float2 v = __ffma2_rn(ch, hw, __ffma2_rn(ck, b1, g[k]));
+        const Row3 r2 = load_row3(rp + (k + 2) * P);
+        const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+        float2 v = __ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k]));
         const int i = c.ib + k;
         if (WMODE == WRITE_INTERIOR) {
-            sts2(dst + i * P + c.j, Store<S>::round(v.x), Store<S>::round(v.y));
+            float *d = dst + i * P + c.j;
+            d[0] = Store<S>::round(v.x);
+            d[32] = Store<S>::round(v.y);
         } else if (WMODE == WRITE_BORDER) {
             v.x = Store<S>::round(v.x);
             v.y = Store<S>::round(v.y);
             const int gy = c.Y0 + i;
             const bool rin = (gy >= 0) & (gy < c.h);
-            if (BND == BND_ZERO) {
-                sts2(dst + i * P + c.j, (rin & c.cin0) ? v.x : 0.0f, (rin & c.cin1) ? v.y : 0.0f);
-            } else {
-                // in-image cells: normal write plus mirror writes into the ring outside the image
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const bool in = rin & (e == 0 ? c.cin0 : c.cin1);
+            for (int e = 0; e < 2; ++e) {
+                const bool in = rin & (e == 0 ? c.cin0 : c.cin1);
+                const float ve = e == 0 ? v.x : v.y;
+                const int jc = c.j + 32 * e;
+                if (BND == BND_ZERO) {
+                    dst[i * P + jc] = in ? ve : 0.0f;
+                } else {
+                    // in-image cells: normal write plus mirror writes into the ring outside
+                    // the image
                     if (!in) continue;
-                    const float ve = e == 0 ? v.x : v.y;
-                    const int xe = c.gx + e;
-                    dst[i * P + c.j + e] = ve;
+                    const int xe = c.gx + 32 * e;
+                    dst[i * P + jc] = ve;
                     const int up = (gy == 0) ? -1 : 0, dn = (gy == c.h - 1) ? 1 : 0;
                     const int lf = (xe == 0) ? -1 : 0, rt = (xe == c.w - 1) ? 1 : 0;
                     for (int di = up; di <= dn; ++di)
                         for (int dj = lf; dj <= rt; ++dj) {
                             if (di == 0 && dj == 0) continue;
-                            const int ii = i + di, jj = c.j + e + dj;
+                            const int ii = i + di, jj = jc + dj;
                             if (ii >= 0 && ii < LH && jj >= 0 && jj < LW) dst[ii * P + jj] = ve;
                         }
                 }
             }
         } else {
             const int gy = c.Y0 + i;
-            const bool row_out = (i >= T) & (i < T + OH) & (gy < c.h);
-            if (col_out & row_out) {
+            if ((i >= T) & (i < T + OH) & (gy < c.h)) {
                 S *o = static_cast<S *>(p.out) + (int64_t)gy * p.ldo + c.gx;
-                if (p.vec_o && c.gx + 1 < c.w) {
-                    Store<S>::store2(o, v.x, v.y);
-                } else {
-                    if (c.gx < c.w) Store<S>::store(o, v.x);
-                    if (c.gx + 1 < c.w) Store<S>::store(o + 1, v.y);
-                }
+                if (col_out0 & (c.gx < c.w)) Store<S>::store(o, v.x);
+                if (col_out1 & (c.gx + 32 < c.w)) Store<S>::store(o + 32, v.y);
             }
         }
-        a0 = a1; b0 = b1; c0 = c1;
-        a1 = a2; b1 = b2; c1 = c2;
+        r0 = r1;
+        r1 = r2;
     }
 }
 
@@ -260,7 +269,7 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
     // ---- per-thread geometry and f (overlaps the load)
     const int lane = tid & 31, warp = tid >> 5;
     TileCtx c;
-    c.j = 2 + 64 * (warp & 1) + 2 * lane;
+    c.j = 2 + 64 * (warp & 1) + lane;
     c.ib = 1 + kRY * (warp >> 1);
     c.X0 = X0;
     c.Y0 = Y0;
@@ -268,7 +277,7 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
     c.h = h;
     c.w = w;
     c.cin0 = (c.gx >= 0) & (c.gx < w);
-    c.cin1 = (c.gx + 1 >= 0) & (c.gx + 1 < w);
+    c.cin1 = (c.gx + 32 >= 0) & (c.gx + 32 < w);
     float2 g[kRY];
     {
         const S *f = static_cast<const S *>(p.f);
@@ -279,14 +288,8 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
             float a = 0.0f, b = 0.0f;
             if (f != nullptr && gy >= 0 && gy < h) {
                 const S *fr = f + (int64_t)gy * p.ldf;
-                if (p.vec_f && gx >= 0 && gx + 1 < w) {
-                    const float2 v = Store<S>::load2(fr + gx);
-                    a = v.x;
-                    b = v.y;
-                } else {
-                    if (gx >= 0 && gx < w) a = Store<S>::load(fr + gx);
-                    if (gx + 1 >= 0 && gx + 1 < w) b = Store<S>::load(fr + gx + 1);
-                }
+                if (c.cin0) a = Store<S>::load(fr + gx);
+                if (c.cin1) b = Store<S>::load(fr + gx + 32);
             }
             g[k] = __fmul2_rn(make_float2(p.c_f, p.c_f), make_float2(a, b));
         }
