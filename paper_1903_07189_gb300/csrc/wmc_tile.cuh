@@ -15,8 +15,8 @@
 // x-coordinate is aligned and every thread's column pair (even, odd) is either wholly inside or
 // wholly outside the output tile.
 //
-// Threads: 8 warps as 2 (x) x 4 (y); lane l of warp (wx, wy) updates columns j = 2 + 64 wx + l
-// and j + 32 for rows i = 1 + 16 wy .. 16 + 16 wy.  The two columns are the two lanes of packed
+// Threads: 16 warps as 2 (x) x 8 (y); lane l of warp (wx, wy) updates columns j = 2 + 64 wx + l
+// and j + 32 for rows i = 1 + 8 wy .. 8 + 8 wy.  The two columns are the two lanes of packed
 // FP32x2 arithmetic: every operand pair (west, centre, east neighbours of both cells) is read
 // by two conflict-free 4-byte shared loads straight into an aligned register pair, so no
 // register shuffling is needed (pairing the adjacent columns j, j+1 instead would make six of
@@ -44,8 +44,10 @@ namespace wmc {
 
 constexpr int kCW = 128;   // updated columns per step
 constexpr int kCH = 64;    // updated rows per step
-constexpr int kRY = 16;    // rows per thread
-constexpr int kTileThreadsV2 = 256;
+constexpr int kRY = 8;     // rows per thread
+constexpr int kTileWX = 2; // warps across (64 columns each)
+constexpr int kTileWY = kCH / kRY;  // warps down
+constexpr int kTileThreadsV2 = 32 * kTileWX * kTileWY;  // 512
 
 template <typename S> struct Geom {
     static constexpr int A = 16 / (int)sizeof(S);                 // TMA x alignment (elements)
@@ -194,19 +196,21 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
                 if (BND == BND_ZERO) {
                     dst[i * P + jc] = in ? ve : 0.0f;
                 } else {
-                    // in-image cells: normal write plus mirror writes into the ring outside
-                    // the image
+                    // in-image cells: normal write; cells on the image edge also refresh the
+                    // ring cells outside the image that copy them
                     if (!in) continue;
                     const int xe = c.gx + 32 * e;
                     dst[i * P + jc] = ve;
-                    const int up = (gy == 0) ? -1 : 0, dn = (gy == c.h - 1) ? 1 : 0;
-                    const int lf = (xe == 0) ? -1 : 0, rt = (xe == c.w - 1) ? 1 : 0;
-                    for (int di = up; di <= dn; ++di)
-                        for (int dj = lf; dj <= rt; ++dj) {
-                            if (di == 0 && dj == 0) continue;
-                            const int ii = i + di, jj = jc + dj;
-                            if (ii >= 0 && ii < LH && jj >= 0 && jj < LW) dst[ii * P + jj] = ve;
-                        }
+                    if ((gy == 0) | (gy == c.h - 1) | (xe == 0) | (xe == c.w - 1)) {
+                        const int up = (gy == 0) ? -1 : 0, dn = (gy == c.h - 1) ? 1 : 0;
+                        const int lf = (xe == 0) ? -1 : 0, rt = (xe == c.w - 1) ? 1 : 0;
+                        for (int di = up; di <= dn; ++di)
+                            for (int dj = lf; dj <= rt; ++dj) {
+                                if (di == 0 && dj == 0) continue;
+                                const int ii = i + di, jj = jc + dj;
+                                if (ii >= 0 && ii < LH && jj >= 0 && jj < LW) dst[ii * P + jj] = ve;
+                            }
+                    }
                 }
             }
         } else {
@@ -312,17 +316,29 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
         __syncthreads();
     }
 
-    // ---- REPLICATE: fill the ring just outside the image from its nearest in-image cell
+    // ---- REPLICATE: fill the ring just outside the image from its nearest in-image cell.
+    // The ring is at most four segments (image rows -1 and h, image columns -1 and w) crossing
+    // the window; corner cells belong to two segments and get the same value from both.
     if (BND == BND_REPLICATE && border) {
-        for (int idx = tid; idx < LH * LW; idx += kTileThreadsV2) {
-            const int i = idx / LW, jj = idx - (idx / LW) * LW;
-            const int yy = Y0 + i, xx = X0 + jj;
-            const bool inside = (yy >= 0) & (yy < h) & (xx >= 0) & (xx < w);
-            const bool ring = (yy >= -1) & (yy <= h) & (xx >= -1) & (xx <= w);
-            if (ring && !inside) {
-                const int ci = min(max(yy, 0), h - 1) - Y0, cj = min(max(xx, 0), w - 1) - X0;
-                buf0[i * P + jj] = buf0[ci * P + cj];
+        const int ir0 = -1 - Y0, ir1 = h - Y0;  // shared rows of image rows -1 and h
+        const int jc0 = -1 - X0, jc1 = w - X0;  // shared columns of image columns -1 and w
+        const int jlo = max(jc0, 0), jhi = min(jc1, LW - 1);
+        const int ilo = max(ir0, 0), ihi = min(ir1, LH - 1);
+        for (int t = tid; t < 2 * (LW + LH); t += kTileThreadsV2) {
+            int i, j2;
+            if (t < 2 * LW) {
+                i = (t < LW) ? ir0 : ir1;
+                j2 = (t < LW) ? t : t - LW;
+                if (i < 0 || i >= LH || j2 < jlo || j2 > jhi) continue;
+            } else {
+                const int u = t - 2 * LW;
+                j2 = (u < LH) ? jc0 : jc1;
+                i = (u < LH) ? u : u - LH;
+                if (j2 < 0 || j2 >= LW || i < ilo || i > ihi) continue;
             }
+            const int yy = Y0 + i, xx = X0 + j2;
+            const int ci = min(max(yy, 0), h - 1) - Y0, cj = min(max(xx, 0), w - 1) - X0;
+            buf0[i * P + j2] = buf0[ci * P + cj];
         }
         __syncthreads();
     }
