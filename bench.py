@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--steps-per-launch", type=int, default=0)
     ap.add_argument("--iters", type=int, default=ITERS, help="override (profiling runs only)")
+    ap.add_argument("--workload", default="scale", choices=["scale", "precision", "batch"],
+                    help="scale: the headline 4096^2 run; precision / batch: the reduced-storage "
+                         "and uneven-batch measurements (one JSON line each, not the headline)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -298,10 +301,153 @@ def run_gpu(args):
     return 0
 
 
+def run_precision(args):
+    """16384 x 16384 image (64 bumps, 32 shapes, sigma 0.05, seed 3) stored as FP32, BF16 and FP16,
+    200 iterations each; throughput per storage type and error against the FP64 oracle on the
+    top-left 2048 x 2048 crop (the oracle runs on a 2248 x 2248 crop: 200 px of light cone)."""
+    import torch
+    import oracle
+    from paper_1903_07189_gb300 import synth, wmc
+    dev = torch.device("cuda", 0)
+    n, iters, crop, margin = 16384, 200, 2048, 200
+    img = synth.make_image(n, n, seed=3, n_bumps=64, n_shapes=32, sigma=0.05)
+    oracle.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    ref = oracle.denoise(img[:crop + margin, :crop + margin].astype(np.float64), LAM, STEP, iters)[:crop, :crop]
+    oracle_s = time.perf_counter() - t0
+    ref_bf = {}
+    for st in ("bf16", "f16"):
+        sub = img[:crop + margin, :crop + margin].astype(np.float64)
+        ref_bf[st] = oracle.denoise(sub, LAM, STEP, iters, storage=st)[:crop, :crop]
+    results = {}
+    for name, dt in [("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)]:
+        f = torch.from_numpy(img).to(dev).to(dt)
+        out = torch.empty_like(f)
+        ws = torch.empty(wmc.load().wmc_denoise_workspace_size(n, n, n, wmc.DTYPES[dt]), dtype=torch.uint8,
+                         device=dev)
+        T = args.steps_per_launch or DEFAULT_T
+        wmc.denoise(f, LAM, STEP, iters, out=out, steps_per_launch=T, workspace=ws)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(max(1, min(args.steps, 3))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            wmc.denoise(f, LAM, STEP, iters, out=out, steps_per_launch=T, workspace=ws)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        got = out[:crop, :crop].float().cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref)
+        mse = float((err ** 2).mean())
+        r = {"gpix_iter_s": n * n * iters / (min(times) * 1e-3) / 1e9, "ms": min(times),
+             "max_abs_err_vs_fp64": float(err.max()),
+             "psnr_vs_fp64_db": 10 * np.log10(1.0 / mse) if mse > 0 else float("inf")}
+        if name in ref_bf:
+            e2 = np.abs(got - ref_bf[name])
+            r["max_abs_err_vs_emulated_storage"] = float(e2.max())
+            r["frac_beyond_1ulp_vs_emulated"] = float((e2 > np.abs(ref_bf[name]) * (2.0 ** -7 if name == "bf16" else 2.0 ** -10)).mean())
+        results[name] = r
+        del f, out, ws
+        torch.cuda.empty_cache()
+    line = {"workload": "precision", "metric": METRIC, "unit": UNIT, "config": {
+        "image": f"{n}x{n} synthetic (64 bumps + 32 shapes, sigma 0.05, seed 3)", "iters": iters,
+        "lambda": LAM, "step": STEP, "boundary": "replicate",
+        "error_crop": f"top-left {crop}x{crop} (oracle on {crop + margin}x{crop + margin}, FP64, "
+                      f"{oracle.get_threads()} threads, {oracle_s:.1f} s)",
+        "arithmetic": "FP32 for every storage type; every step rounds to the storage type"},
+        "results": results}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """512 images, sides uniform in [64, 1536] (seeded), image i: seed 1000+i, 8 bumps + 4 shapes,
+    sigma_i ~ U[0.01, 0.15], lambda_i ~ U[0.5, 2], step_i = 0.5/(1+lambda_i); 300 iterations.
+    Aggregate pixel-iterations/s of (a) one batch plan run captured in a CUDA graph and replayed,
+    (b) the same run launched directly, (c) looping the single-image path over the images."""
+    import torch
+    from paper_1903_07189_gb300 import synth, wmc
+    dev = torch.device("cuda", 0)
+    n, iters = 512, 300
+    sizes = synth.batch_sizes(n)
+    params = synth.batch_params(n)
+    fs = [torch.from_numpy(synth.make_image(h, w, seed=1000 + i, n_bumps=8, n_shapes=4, sigma=sg)).to(dev)
+          for i, ((h, w), (sg, _)) in enumerate(zip(sizes, params))]
+    lams = [l for _, l in params]
+    steps = [0.5 / (1 + l) for l in lams]
+    px = sum(h * w for h, w in sizes)
+    Ts = [args.steps_per_launch] if args.steps_per_launch else [2, 3, 4, 6]
+    # steps-per-launch chosen by timing a short run of each candidate on this batch
+    tune = {}
+    for T in Ts:
+        b = wmc.Batch(fs, lams, steps, steps_per_launch=T)
+        b.run(2 * T)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        b.run(12 * T)
+        e.record()
+        torch.cuda.synchronize()
+        tune[T] = a.elapsed_time(e) / (12 * T)
+        del b
+    T = min(tune, key=tune.get)
+    b = wmc.Batch(fs, lams, steps, steps_per_launch=T)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(iters)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.run(iters)
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(e))
+        return min(ts)
+
+    graph.replay()
+    t_graph = timed(graph.replay, max(1, min(args.steps, 5)))
+    t_direct = timed(lambda: b.run(iters), max(1, min(args.steps, 3)))
+    b.check_status()
+    outs = [torch.empty_like(f) for f in fs]
+    ws = torch.empty(max(wmc.load().wmc_denoise_workspace_size(h, w, w, 0) for h, w in sizes),
+                     dtype=torch.uint8, device=dev)
+
+    def loop():
+        for f, l, st, o in zip(fs, lams, steps, outs):
+            wmc.denoise(f, l, st, iters, out=o, steps_per_launch=T, workspace=ws)
+
+    loop()
+    t_loop = timed(loop, 1)
+    same = all(torch.equal(a, c) for a, c in zip(b.outs, outs))
+    line = {"workload": "batch", "metric": METRIC, "unit": UNIT, "config": {
+        "images": n, "pixels": px, "sides": "uniform [64, 1536] (seed 999)", "iters": iters,
+        "sigma": "U[0.01, 0.15]", "lambda": "U[0.5, 2]", "step": "0.5/(1+lambda)", "dtype": "f32",
+        "steps_per_launch": T, "autotune_ms_per_iter": tune},
+        "results": {"batched_graph": px * iters / (t_graph * 1e-3) / 1e9,
+                    "batched_direct": px * iters / (t_direct * 1e-3) / 1e9,
+                    "single_image_loop": px * iters / (t_loop * 1e-3) / 1e9,
+                    "ms": {"graph": t_graph, "direct": t_direct, "loop": t_loop},
+                    "batched_equals_loop_bitwise": same}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "precision":
+        return run_precision(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

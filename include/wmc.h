@@ -51,7 +51,7 @@ typedef enum {
     WMC_ERR_ALIAS = 2,       /* an output overlaps an input it must not overlap */
     WMC_ERR_UNSUPPORTED = 3, /* valid request this build cannot serve (e.g. no sm_103a GPU) */
     WMC_ERR_CUDA = 4,        /* a CUDA runtime call failed; see wmc_last_error() */
-    WMC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (batched path) */
+    WMC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (see wmc_denoise_status) */
     WMC_ERR_WORKSPACE = 6    /* workspace missing, too small or misaligned */
 } wmc_status_t;
 
@@ -147,7 +147,8 @@ wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_h
  *   (out[1] = 0 when f is NULL, out[2] = 0 when clean is NULL).
  *   u, f, clean: device, h x w, pitch ld, type dtype (f, clean may be NULL).  out: DEVICE, 3 doubles, written (not
  *   accumulated).  Per-thread partial sums run in FP32 over at most 16 pixels and in FP64
- *   beyond; the summation order is fixed, so repeated calls give identical results.
+ *   beyond; the summation order is fixed, so repeated calls give identical results.  The
+ *   workspace size depends on h and w (one FP64 triple per CTA).
  *   workspace: device, >= wmc_energy_workspace_size() bytes, aligned as above.
  */
 size_t wmc_energy_workspace_size(int32_t h, int32_t w);
@@ -155,6 +156,54 @@ size_t wmc_energy_workspace_size(int32_t h, int32_t w);
 wmc_status_t wmc_energy(const void *u, const void *f, const void *clean, int32_t h, int32_t w,
                         int64_t ld, wmc_dtype_t dtype, wmc_boundary_t bnd, double *out,
                         void *workspace, size_t workspace_bytes, wmc_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Batched denoising: many images of different sizes, each with its own lambda and step, advanced
+ * together -- every kernel launch takes T Jacobi steps (wmc_config_t.steps_per_launch, default 3)
+ * on the tiles of all images (Sec. V-B flow with A = I; colour channels are images too, as the
+ * paper treats them separately, Sec. V-D).
+ *
+ *   wmc_image_t: f (device, U^0 = f), u (device output), h x w, pitch ld (elements, shared by f
+ *   and u), lambda (finite, >= 0), step (finite, > 0).  Images may share f; u must not overlap
+ *   any f or any other u.  h or w may be 0 (the image is skipped).
+ *
+ *   wmc_batch_workspace_size: device bytes for the plan below (status word, per-image
+ *   descriptors and tensor maps, the tile table, and one ping-pong image per input).
+ *   wmc_batch_plan: validates the images, writes descriptors and the tile table into
+ *   `workspace` (device, WMC_WORKSPACE_ALIGN-aligned) and fills `plan` (caller-owned host
+ *   memory, opaque).  It synchronises `stream` once, so the `imgs` array may be freed on return.
+ *   wmc_batch_run: `iters` Jacobi steps of every image; only kernel launches and one 4-byte
+ *   memset are enqueued on `stream`, so the call can be captured into a CUDA graph and replayed.
+ *   The plan (and its workspace) stays valid until the caller frees them.  wmc_denoise_status()
+ *   on the workspace reports a timed-out tile load, as for single images.
+ *   wmc_denoise_batched: plan + run in one call.
+ * Errors: WMC_ERR_INVALID_ARG (a bad image, count or config; the detail names the image),
+ *         WMC_ERR_ALIAS, WMC_ERR_WORKSPACE, WMC_ERR_CUDA.
+ */
+typedef struct {
+    const void *f;
+    void *u;
+    int32_t h, w;
+    int64_t ld;
+    float lambda, step;
+} wmc_image_t;
+
+typedef struct {
+    int64_t opaque[16];
+} wmc_batch_t;
+
+size_t wmc_batch_workspace_size(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                                const wmc_config_t *config);
+
+wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                            wmc_boundary_t bnd, const wmc_config_t *config, void *workspace,
+                            size_t workspace_bytes, wmc_batch_t *plan, wmc_stream_t stream);
+
+wmc_status_t wmc_batch_run(const wmc_batch_t *plan, int32_t iters, wmc_stream_t stream);
+
+wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                                 int32_t iters, wmc_boundary_t bnd, void *workspace,
+                                 size_t workspace_bytes, wmc_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------ */
 const char *wmc_status_string(wmc_status_t status); /* static string, never NULL */

@@ -32,11 +32,15 @@ _i8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def build(force: bool = False) -> str:
-    """Compile wmc_oracle.c into _build/liboracle.so (gcc, -O2, no vendor code)."""
+    """Compile wmc_oracle.c into _build/liboracle.so (gcc, -O2, OpenMP if available)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -47,6 +51,8 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             i32, i64, d = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_get_threads.restype = ctypes.c_int
             lib.oracle_kernel.argtypes = [ctypes.c_int, _dp]
             lib.oracle_canonical_order.argtypes = [_ip]
             lib.oracle_round_storage.argtypes = [d, ctypes.c_int]
@@ -77,6 +83,15 @@ def _bnd(boundary) -> int:
     if isinstance(boundary, str):
         return {"replicate": REPLICATE, "zero": ZERO}[boundary]
     return int(boundary)
+
+
+def set_threads(n: int) -> None:
+    """Split whole-image passes over n OpenMP threads (results do not depend on n)."""
+    _load().oracle_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().oracle_get_threads())
 
 
 def kernel(i: int) -> np.ndarray:

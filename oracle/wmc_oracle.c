@@ -39,6 +39,13 @@
 #define ORACLE_BND_REPLICATE 0
 #define ORACLE_BND_ZERO 1
 
+/* Rows of a whole-image pass may be split across OpenMP threads (every pixel is computed on
+ * its own, so the result does not depend on the thread count).  Default: 1 thread. */
+static int g_threads = 1;
+
+void oracle_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+int oracle_get_threads(void) { return g_threads; }
+
 /* 12 * h_i, i = 1..8, exactly as printed in Sec. IV-B (row r = 0 is the top row). */
 static const int H12[8][3][3] = {
     /* h1 */ {{2, 2, 0}, {4, -12, 0}, {2, 2, 0}},
@@ -114,6 +121,7 @@ static int check_dims(int32_t h, int32_t w, int64_t ld) {
 int oracle_wmc_eval(const double *u, double *hw, int32_t h, int32_t w, int64_t ld_u,
                     int64_t ld_hw, int bnd, double *cand, uint8_t *index) {
     if (check_dims(h, w, ld_u) || (h > 0 && w > 0 && ld_hw < w)) return 1;
+#pragma omp parallel for schedule(static) num_threads(g_threads)
     for (int32_t y = 0; y < h; ++y)
         for (int32_t x = 0; x < w; ++x) {
             double d[8];
@@ -198,6 +206,7 @@ int oracle_wmc_flow(const double *f, const double *u0, double *u_out, int32_t h,
         }
     for (int32_t t = 0; t < iters; ++t) {
         oracle_wmc_eval(U, Hw, h, w, w, w, bnd, NULL, NULL);
+#pragma omp parallel for schedule(static) num_threads(g_threads)
         for (size_t p = 0; p < n; ++p) {
             double next = U[p] + step * (lambda * Hw[p] - mu * (U[p] - F[p]));
             V[p] = oracle_round_storage(next, storage);

@@ -5,7 +5,10 @@
 #include <cstdio>
 #include <cstring>
 
+#include <algorithm>
+#include <atomic>
 #include <mutex>
+#include <vector>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -132,16 +135,18 @@ bool pair_aligned(const void *p, int64_t ld, size_t es) {
     return p == nullptr || (((uintptr_t)p % (2 * es)) == 0 && (ld % 2) == 0);
 }
 
+// batch_tiles < 0: single-image launch (tiles from the grid); >= 0: batch launch over that
+// many tiles of the plan's table.
 cudaError_t launch_tile(wmc_dtype_t dtype, wmc_boundary_t bnd, int steps, const CUtensorMap *map,
-                        const wmc::TileV2Params &p, cudaStream_t st) {
+                        const wmc::TileV2Params &p, int64_t batch_tiles, cudaStream_t st) {
     const bool z = bnd == WMC_BOUNDARY_ZERO;
     switch (dtype) {
-        case WMC_F32: return z ? wmc::launch_tile_f32_zero(steps, map, p, st)
-                               : wmc::launch_tile_f32_rep(steps, map, p, st);
-        case WMC_BF16: return z ? wmc::launch_tile_bf16_zero(steps, map, p, st)
-                                : wmc::launch_tile_bf16_rep(steps, map, p, st);
-        case WMC_F16: return z ? wmc::launch_tile_f16_zero(steps, map, p, st)
-                               : wmc::launch_tile_f16_rep(steps, map, p, st);
+        case WMC_F32: return z ? wmc::launch_tile_f32_zero(steps, map, p, batch_tiles, st)
+                               : wmc::launch_tile_f32_rep(steps, map, p, batch_tiles, st);
+        case WMC_BF16: return z ? wmc::launch_tile_bf16_zero(steps, map, p, batch_tiles, st)
+                                : wmc::launch_tile_bf16_rep(steps, map, p, batch_tiles, st);
+        case WMC_F16: return z ? wmc::launch_tile_f16_zero(steps, map, p, batch_tiles, st)
+                               : wmc::launch_tile_f16_rep(steps, map, p, batch_tiles, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -226,17 +231,15 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
             tp.u = src;
             tp.f = f;
             tp.out = dst;
-            tp.ldu = tp.ldf = tp.ldo = ld;
+            tp.ld = ld;
             tp.h = h;
             tp.w = w;
             tp.use_tma = tma[src_id] ? 1 : 0;
-            tp.vec_f = pair_aligned(f, ld, es) ? 1 : 0;
-            tp.vec_o = pair_aligned(dst, ld, es) ? 1 : 0;
             tp.c_keep = c_keep;
             tp.c_f = c_f;
             tp.c_h = c_h;
             tp.status = status;
-            e = launch_tile(dtype, bnd, s, &maps[src_id], tp, st);
+            e = launch_tile(dtype, bnd, s, &maps[src_id], tp, -1, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "flow kernel launch");
         src = dst;
@@ -279,6 +282,139 @@ wmc_status_t check_flow_args(const void *f, const void *u0, void *u, int32_t h, 
         if (u0 && u0 != u && overlap(u, n, u0, n)) return fail(WMC_ERR_ALIAS, "u overlaps u0");
     }
     return WMC_OK;
+}
+
+// ------------------------------------------------------------------ batches
+constexpr uint32_t kBatchMagic = 0x57424348u;  // "WBCH"
+
+struct BatchPlan {
+    void *ws;
+    int64_t ntiles;
+    int64_t off_images, off_tiles;
+    int32_t n, dtype, bnd, steps;
+    int32_t owt, oht;
+    uint32_t magic;
+};
+static_assert(sizeof(BatchPlan) <= sizeof(wmc_batch_t), "plan does not fit wmc_batch_t");
+
+void out_tile(wmc_dtype_t dtype, int T, int *owt, int *oht) {
+    // Out<S, T> for the storage type; computed like the device-side struct.
+    const int A = dtype == WMC_F32 ? 4 : 8;
+    const int M = A * ((T + 1 + A - 1) / A);
+    *owt = A * ((wmc::kCW + 3 - T - M) / A);
+    *oht = wmc::kCH + 2 - 2 * T;
+}
+
+struct BatchLayout {
+    size_t off_images, off_tiles, off_bufs, total;
+    int64_t ntiles;
+    std::vector<size_t> buf_off;
+};
+
+BatchLayout batch_layout(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype, int T) {
+    BatchLayout L{};
+    int owt, oht;
+    out_tile(dtype, T, &owt, &oht);
+    L.off_images = kStatusBytes;
+    L.off_tiles = round_up(L.off_images + (size_t)n * sizeof(wmc::BatchImage), WMC_WORKSPACE_ALIGN);
+    L.ntiles = 0;
+    for (int32_t i = 0; i < n; ++i)
+        if (imgs[i].h > 0 && imgs[i].w > 0)
+            L.ntiles += (int64_t)((imgs[i].w + owt - 1) / owt) * ((imgs[i].h + oht - 1) / oht);
+    L.off_bufs = round_up(L.off_tiles + (size_t)L.ntiles * sizeof(int4), WMC_WORKSPACE_ALIGN);
+    size_t off = L.off_bufs;
+    L.buf_off.resize(n);
+    for (int32_t i = 0; i < n; ++i) {
+        L.buf_off[i] = off;
+        if (imgs[i].h > 0 && imgs[i].w > 0) off += image_bytes(imgs[i].h, imgs[i].ld, dtype);
+    }
+    L.total = off;
+    return L;
+}
+
+int batch_steps(const wmc_config_t *cfg) {
+    return (cfg && cfg->steps_per_launch > 0) ? cfg->steps_per_launch : kDefaultSteps;
+}
+
+wmc_status_t check_batch(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype, wmc_boundary_t bnd,
+                         const wmc_config_t *cfg) {
+    wmc_status_t s;
+    if ((s = check_enums(dtype, bnd)) != WMC_OK) return s;
+    if (n < 0) return fail(WMC_ERR_INVALID_ARG, "negative image count %d", n);
+    if (n > 0 && !imgs) return fail(WMC_ERR_INVALID_ARG, "imgs is NULL");
+    if (cfg) {
+        if (cfg->steps_per_launch < 0 || cfg->steps_per_launch > wmc::kMaxSteps)
+            return fail(WMC_ERR_INVALID_ARG, "steps_per_launch must be 0..%d (got %d)",
+                        wmc::kMaxSteps, cfg->steps_per_launch);
+        if (cfg->tile != 0) return fail(WMC_ERR_INVALID_ARG, "unknown tile %d", cfg->tile);
+    }
+    const size_t es = elem_size(dtype);
+    // every u must be disjoint from every other buffer; f buffers may overlap each other
+    struct Iv { uintptr_t a, b; bool is_u; int32_t img; };
+    std::vector<Iv> iv;
+    iv.reserve(2 * (size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        const wmc_image_t &m = imgs[i];
+        if (m.h < 0 || m.w < 0)
+            return fail(WMC_ERR_INVALID_ARG, "image %d: negative size %d x %d", i, m.h, m.w);
+        if (m.h > kMaxSide || m.w > kMaxSide)
+            return fail(WMC_ERR_INVALID_ARG, "image %d: side longer than %d", i, kMaxSide);
+        if (m.h == 0 || m.w == 0) continue;
+        if (m.ld < m.w)
+            return fail(WMC_ERR_INVALID_ARG, "image %d: leading dimension %lld < width %d", i,
+                        (long long)m.ld, m.w);
+        if (!m.f || !m.u) return fail(WMC_ERR_INVALID_ARG, "image %d: NULL f or u", i);
+        if (!std::isfinite(m.lambda) || m.lambda < 0.0f)
+            return fail(WMC_ERR_INVALID_ARG, "image %d: lambda must be finite and >= 0", i);
+        if (!std::isfinite(m.step) || m.step <= 0.0f)
+            return fail(WMC_ERR_INVALID_ARG, "image %d: step must be finite and > 0", i);
+        const size_t nb = span_bytes(m.h, m.w, m.ld, es);
+        iv.push_back({(uintptr_t)m.f, (uintptr_t)m.f + nb, false, i});
+        iv.push_back({(uintptr_t)m.u, (uintptr_t)m.u + nb, true, i});
+    }
+    std::sort(iv.begin(), iv.end(), [](const Iv &x, const Iv &y) {
+        return x.a < y.a || (x.a == y.a && x.b < y.b);
+    });
+    uintptr_t maxend = 0;
+    const Iv *holder = nullptr;
+    for (const Iv &x : iv) {
+        if (holder && x.a < maxend && (x.is_u || holder->is_u))
+            return fail(WMC_ERR_ALIAS, "image %d: output overlaps image %d", x.is_u ? x.img : holder->img,
+                        x.is_u ? holder->img : x.img);
+        if (x.b > maxend) {
+            maxend = x.b;
+            holder = &x;
+        }
+    }
+    return WMC_OK;
+}
+
+// U = f for every output tile of a batch (a run with zero iterations).
+template <typename E>
+__global__ void batch_copy_kernel(const wmc::BatchImage *images, const int4 *tiles, int owt, int oht) {
+    const int4 t = tiles[blockIdx.x];
+    const wmc::BatchImage &im = images[t.x];
+    const E *f = static_cast<const E *>(im.buf[0]);
+    E *u = static_cast<E *>(const_cast<void *>(im.buf[1]));
+    for (int idx = threadIdx.x; idx < owt * oht; idx += blockDim.x) {
+        const int y = t.z + idx / owt, x = t.y + idx % owt;
+        if (y < im.h && x < im.w) u[(int64_t)y * im.ld + x] = f[(int64_t)y * im.ld + x];
+    }
+}
+
+template <typename F>
+void for_each_launch(int iters, int T, F &&fn) {
+    // launch k takes min(T, remaining) steps; the roles alternate so that the last launch writes
+    // u (role 1): f (role 0) is read by the first launch only
+    const int nl = (iters + T - 1) / T;
+    int src = 0, done = 0;
+    for (int k = 0; k < nl; ++k) {
+        const int s = (iters - done) < T ? (iters - done) : T;
+        const int dst = ((nl - 1 - k) % 2 == 0) ? 1 : 2;
+        fn(s, src, dst);
+        src = dst;
+        done += s;
+    }
 }
 
 }  // namespace
@@ -428,10 +564,9 @@ wmc_status_t wmc_denoise_status(const void *workspace, wmc_stream_t stream) {
 }
 
 size_t wmc_energy_workspace_size(int32_t h, int32_t w) {
-    (void)h;
-    (void)w;
-    return round_up(3 * sizeof(double) * (size_t)wmc::energy_grid_blocks() + sizeof(unsigned int),
-                    WMC_WORKSPACE_ALIGN);
+    if (h <= 0 || w <= 0) return WMC_WORKSPACE_ALIGN;
+    return WMC_WORKSPACE_ALIGN +
+           round_up(3 * sizeof(double) * (size_t)wmc::energy_blocks(h, w), WMC_WORKSPACE_ALIGN);
 }
 
 wmc_status_t wmc_energy(const void *u, const void *f, const void *clean, int32_t h, int32_t w,
@@ -456,6 +591,139 @@ wmc_status_t wmc_energy(const void *u, const void *f, const void *clean, int32_t
     cudaError_t e = wmc::launch_energy((int)dtype, u, f, clean, h, w, ld, (int)bnd, out, workspace, st);
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
     return WMC_OK;
+}
+
+size_t wmc_batch_workspace_size(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                                const wmc_config_t *config) {
+    if (n < 0 || (n > 0 && !imgs) || elem_size(dtype) == 0) return 0;
+    const int T = batch_steps(config);
+    if (T < 1 || T > wmc::kMaxSteps) return 0;
+    for (int32_t i = 0; i < n; ++i)
+        if (imgs[i].h < 0 || imgs[i].w < 0 || (imgs[i].h > 0 && imgs[i].w > 0 && imgs[i].ld < imgs[i].w))
+            return 0;
+    return batch_layout(imgs, n, dtype, T).total;
+}
+
+wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                            wmc_boundary_t bnd, const wmc_config_t *config, void *workspace,
+                            size_t workspace_bytes, wmc_batch_t *plan, wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    if (!plan) return fail(WMC_ERR_INVALID_ARG, "plan is NULL");
+    memset(plan, 0, sizeof *plan);
+    wmc_status_t s = check_batch(imgs, n, dtype, bnd, config);
+    if (s != WMC_OK) return s;
+    const int T = batch_steps(config);
+    const BatchLayout L = batch_layout(imgs, n, dtype, T);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", L.total,
+                    workspace ? workspace_bytes : (size_t)0);
+    if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
+        return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    const size_t es = elem_size(dtype);
+    for (int32_t i = 0; i < n; ++i) {
+        if (imgs[i].h == 0 || imgs[i].w == 0) continue;
+        const size_t nb = span_bytes(imgs[i].h, imgs[i].w, imgs[i].ld, es);
+        if (overlap(workspace, L.total, imgs[i].f, nb) || overlap(workspace, L.total, imgs[i].u, nb))
+            return fail(WMC_ERR_ALIAS, "workspace overlaps image %d", i);
+    }
+    int owt, oht;
+    out_tile(dtype, T, &owt, &oht);
+    char *base = static_cast<char *>(workspace);
+    std::vector<wmc::BatchImage> desc((size_t)n);
+    std::vector<int4> tiles;
+    tiles.reserve((size_t)L.ntiles);
+    for (int32_t i = 0; i < n; ++i) {
+        const wmc_image_t &m = imgs[i];
+        wmc::BatchImage &d = desc[i];
+        memset(&d, 0, sizeof d);
+        if (m.h == 0 || m.w == 0) continue;
+        d.buf[0] = m.f;
+        d.buf[1] = m.u;
+        d.buf[2] = base + L.buf_off[i];
+        d.ld = m.ld;
+        d.h = m.h;
+        d.w = m.w;
+        d.c_keep = 1.0f - m.step;
+        d.c_f = m.step;
+        d.c_h = m.step * m.lambda / 12.0f;
+        for (int r = 0; r < 3; ++r)
+            d.use_tma[r] = encode_window_map(&d.map[r], d.buf[r], dtype, m.h, m.w, m.ld) ? 1 : 0;
+        for (int y0 = 0; y0 < m.h; y0 += oht)
+            for (int x0 = 0; x0 < m.w; x0 += owt) tiles.push_back(make_int4(i, x0, y0, 0));
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (n > 0)
+        e = cudaMemcpyAsync(base + L.off_images, desc.data(), desc.size() * sizeof(wmc::BatchImage),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !tiles.empty())
+        e = cudaMemcpyAsync(base + L.off_tiles, tiles.data(), tiles.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload batch plan");
+    BatchPlan bp{};
+    bp.ws = workspace;
+    bp.ntiles = L.ntiles;
+    bp.off_images = (int64_t)L.off_images;
+    bp.off_tiles = (int64_t)L.off_tiles;
+    bp.n = n;
+    bp.dtype = (int32_t)dtype;
+    bp.bnd = (int32_t)bnd;
+    bp.steps = T;
+    bp.owt = owt;
+    bp.oht = oht;
+    bp.magic = kBatchMagic;
+    memcpy(plan, &bp, sizeof bp);
+    return WMC_OK;
+}
+
+wmc_status_t wmc_batch_run(const wmc_batch_t *plan, int32_t iters, wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    if (!plan) return fail(WMC_ERR_INVALID_ARG, "plan is NULL");
+    BatchPlan bp;
+    memcpy(&bp, plan, sizeof bp);
+    if (bp.magic != kBatchMagic) return fail(WMC_ERR_INVALID_ARG, "plan was not made by wmc_batch_plan");
+    if (iters < 0) return fail(WMC_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
+    if (bp.ntiles == 0) return WMC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *base = static_cast<char *>(bp.ws);
+    unsigned int *status = reinterpret_cast<unsigned int *>(base);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "clear status");
+    wmc::TileV2Params p{};
+    p.images = reinterpret_cast<const wmc::BatchImage *>(base + bp.off_images);
+    p.tiles = reinterpret_cast<const int4 *>(base + bp.off_tiles);
+    p.owt = bp.owt;
+    p.oht = bp.oht;
+    p.status = status;
+    if (iters == 0) {  // U^0 = f: copy every output tile
+        const int es = (int)elem_size((wmc_dtype_t)bp.dtype);
+        if (bp.ntiles > 0x7fffffffLL) return fail(WMC_ERR_INVALID_ARG, "too many tiles");
+        if (es == 4)
+            batch_copy_kernel<uint32_t><<<(unsigned)bp.ntiles, 256, 0, st>>>(p.images, p.tiles, bp.owt, bp.oht);
+        else
+            batch_copy_kernel<uint16_t><<<(unsigned)bp.ntiles, 256, 0, st>>>(p.images, p.tiles, bp.owt, bp.oht);
+        e = cudaGetLastError();
+        return e == cudaSuccess ? WMC_OK : cuda_fail(e, "batch copy launch");
+    }
+    for_each_launch(iters, bp.steps, [&](int s, int src, int dst) {
+        if (e != cudaSuccess) return;
+        p.src_role = src;
+        p.dst_role = dst;
+        e = launch_tile((wmc_dtype_t)bp.dtype, (wmc_boundary_t)bp.bnd, s, nullptr, p, bp.ntiles, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+    return WMC_OK;
+}
+
+wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                                 int32_t iters, wmc_boundary_t bnd, void *workspace,
+                                 size_t workspace_bytes, wmc_stream_t stream) {
+    wmc_batch_t plan;
+    wmc_status_t s =
+        wmc_batch_plan(imgs, n, dtype, bnd, nullptr, workspace, workspace_bytes, &plan, stream);
+    if (s != WMC_OK) return s;
+    return wmc_batch_run(&plan, iters, stream);
 }
 
 }  // extern "C"

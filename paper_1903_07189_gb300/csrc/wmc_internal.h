@@ -20,18 +20,18 @@ cudaError_t launch_stream(int dtype, int mode, int bnd, const StreamParams &p, b
                           cudaStream_t st);
 
 // Temporally blocked flow kernels, steps = 2..kMaxSteps.
-cudaError_t launch_tile_f32_rep(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
-cudaError_t launch_tile_f32_zero(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
-cudaError_t launch_tile_bf16_rep(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
-cudaError_t launch_tile_bf16_zero(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
-cudaError_t launch_tile_f16_rep(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
-cudaError_t launch_tile_f16_zero(int steps, const CUtensorMap *map, const TileV2Params &p, cudaStream_t st);
+cudaError_t launch_tile_f32_rep(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
+cudaError_t launch_tile_f32_zero(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
+cudaError_t launch_tile_bf16_rep(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
+cudaError_t launch_tile_bf16_zero(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
+cudaError_t launch_tile_f16_rep(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
+cudaError_t launch_tile_f16_zero(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
 
 // Shape of the TMA box the tile kernel loads, in elements of the storage type.
 void tile_box(int dtype, int *box_w, int *box_h);
 
-// FP64 energies; workspace: 3 * energy_grid_blocks() doubles + a ticket word.
-int energy_grid_blocks();
+// FP64 energies; workspace: a 256-byte ticket block followed by 3 doubles per CTA.
+int64_t energy_blocks(int32_t h, int32_t w);
 cudaError_t launch_energy(int dtype, const void *u, const void *f, const void *clean, int32_t h,
                           int32_t w, int64_t ld, int bnd, double *out, void *workspace,
                           cudaStream_t st);

@@ -3,31 +3,22 @@
 //   E_data = 1/2 sum_p (U - f)^2        (the L2 data term of Eq. 1, A = I)
 //   SSE    = sum_p (U - clean)^2        (for PSNR against a known clean image)
 //
-// A fixed grid walks the image in 16-pixel row segments.  Each thread sums a segment in FP32
-// and adds the segment total to FP64 accumulators; CTAs reduce in FP64 with warp shuffles and
-// write one partial each; the last CTA to finish (ticket counter) adds the partials in CTA
-// order.  The grid and the assignment of segments never change, so the result is
+// The image is streamed like the single-pass kernels (a warp owns 64 columns, lanes hold column
+// pairs, neighbours by warp shuffle, each thread a strip of kStreamRY rows with every load issued
+// up front).  Each thread sums its 16 cells in FP32; everything after that is FP64: a fixed
+// shuffle tree inside the CTA, one partial per CTA, and the last CTA to finish (ticket counter)
+// adds the partials in CTA order.  The assignment and the order never change, so the result is
 // bitwise reproducible.
 #include "wmc_device.cuh"
 #include "wmc_internal.h"
+#include "wmc_stream.cuh"
 
 namespace wmc {
 
-constexpr int kEnergyBlocks = 608;  // 4 x 152 SMs
-constexpr int kEnergyThreads = 256;
-constexpr int kSeg = 16;
-
-int energy_grid_blocks() { return kEnergyBlocks; }
-
-template <typename S, int BND>
-__device__ __forceinline__ float at(const S *u, int64_t ld, int h, int w, int y, int x) {
-    if (BND == BND_ZERO) {
-        if (y < 0 || y >= h || x < 0 || x >= w) return 0.0f;
-    } else {
-        y = min(max(y, 0), h - 1);
-        x = min(max(x, 0), w - 1);
-    }
-    return Store<S>::load(u + (int64_t)y * ld + x);
+int64_t energy_blocks(int32_t h, int32_t w) {
+    const int64_t nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
+    const int64_t nby = (h + kStreamRY - 1) / kStreamRY;
+    return nbx * nby;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -37,64 +28,87 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 template <typename S, int BND>
-__global__ void __launch_bounds__(kEnergyThreads)
+__global__ void __launch_bounds__(kStreamWarps * 32)
     energy_kernel(const S *__restrict__ u, const S *__restrict__ f, const S *__restrict__ clean,
                   int h, int w, int64_t ld, double *__restrict__ out,
                   double *__restrict__ partials, unsigned int *__restrict__ ticket) {
-    const int64_t segs_per_row = (w + kSeg - 1) / kSeg;
-    const int64_t nseg = (int64_t)h * segs_per_row;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t t = blockIdx.x * (int64_t)kEnergyThreads + threadIdx.x; t < nseg;
-         t += (int64_t)kEnergyBlocks * kEnergyThreads) {
-        const int y = (int)(t / segs_per_row);
-        const int xb = (int)(t - (int64_t)y * segs_per_row) * kSeg;
-        const int xe = min(xb + kSeg, w);
-        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
-        for (int x = xb; x < xe; ++x) {
-            const float c = at<S, BND>(u, ld, h, w, y, x);
-            const float h12 = half_laplace12(
-                at<S, BND>(u, ld, h, w, y - 1, x - 1), at<S, BND>(u, ld, h, w, y - 1, x),
-                at<S, BND>(u, ld, h, w, y - 1, x + 1), at<S, BND>(u, ld, h, w, y, x - 1), c,
-                at<S, BND>(u, ld, h, w, y, x + 1), at<S, BND>(u, ld, h, w, y + 1, x - 1),
-                at<S, BND>(u, ld, h, w, y + 1, x), at<S, BND>(u, ld, h, w, y + 1, x + 1));
-            s0 += fabsf(h12) * (1.0f / 12.0f);
+    constexpr int R = kStreamRY;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
+    const int by = (int)(blockIdx.x / nbx), bx = (int)(blockIdx.x - (unsigned)by * nbx);
+    const int x = ((bx * kStreamWarps + warp) * 32 + lane) * 2;
+    const int y0 = by * R;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    if ((x & ~63) < w) {  // warp-uniform
+        float2 v[R + 2];
+        float el[R + 2], er[R + 2];
+#pragma unroll
+        for (int k = 0; k < R + 2; ++k) {
+            bool ok;
+            const int y = row_index<BND>(y0 - 1 + k, h, &ok);
+            const S *row = u + (int64_t)y * ld;
+            v[k] = load_pair<S, BND, false>(row, x, w, ok);
+            el[k] = (lane == 0) ? load_one<S, BND>(row, x - 1, w, ok) : 0.0f;
+            er[k] = (lane == 31) ? load_one<S, BND>(row, x + 2, w, ok) : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            float lf = __shfl_up_sync(0xffffffffu, v[k].y, 1);
+            float rt = __shfl_down_sync(0xffffffffu, v[k].x, 1);
+            float lf1 = __shfl_up_sync(0xffffffffu, v[k + 1].y, 1);
+            float rt1 = __shfl_down_sync(0xffffffffu, v[k + 1].x, 1);
+            float lf2 = __shfl_up_sync(0xffffffffu, v[k + 2].y, 1);
+            float rt2 = __shfl_down_sync(0xffffffffu, v[k + 2].x, 1);
+            if (lane == 0) { lf = el[k]; lf1 = el[k + 1]; lf2 = el[k + 2]; }
+            if (lane == 31) { rt = er[k]; rt1 = er[k + 1]; rt2 = er[k + 2]; }
+            const int y = y0 + k;
+            if (y >= h) continue;
+            const float h0 = half_laplace12(lf, v[k].x, v[k].y, lf1, v[k + 1].x, v[k + 1].y, lf2,
+                                            v[k + 2].x, v[k + 2].y);
+            const float h1 = half_laplace12(v[k].x, v[k].y, rt, v[k + 1].x, v[k + 1].y, rt1,
+                                            v[k + 2].x, v[k + 2].y, rt2);
+            const bool in0 = x < w, in1 = x + 1 < w;
+            if (in0) s0 += fabsf(h0) * (1.0f / 12.0f);
+            if (in1) s0 += fabsf(h1) * (1.0f / 12.0f);
             if (f) {
-                const float d = c - Store<S>::load(f + (int64_t)y * ld + x);
-                s1 = fmaf(d, d, s1);
+                const float2 fv = load_pair<S, BND_ZERO, false>(f + (int64_t)y * ld, x, w, true);
+                const float d0 = v[k + 1].x - fv.x, d1 = v[k + 1].y - fv.y;
+                if (in0) s1 = fmaf(d0, d0, s1);
+                if (in1) s1 = fmaf(d1, d1, s1);
             }
             if (clean) {
-                const float d = c - Store<S>::load(clean + (int64_t)y * ld + x);
-                s2 = fmaf(d, d, s2);
+                const float2 cv = load_pair<S, BND_ZERO, false>(clean + (int64_t)y * ld, x, w, true);
+                const float d0 = v[k + 1].x - cv.x, d1 = v[k + 1].y - cv.y;
+                if (in0) s2 = fmaf(d0, d0, s2);
+                if (in1) s2 = fmaf(d1, d1, s2);
             }
         }
-        acc[0] += (double)s0;
-        acc[1] += 0.5 * (double)s1;
-        acc[2] += (double)s2;
     }
-    __shared__ double red[3][kEnergyThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double acc[3] = {(double)s0, 0.5 * (double)s1, (double)s2};
+    __shared__ double red[3][kStreamWarps];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double v = warp_sum(acc[k]);
-        if (lane == 0) red[k][wid] = v;
+        const double t = warp_sum(acc[k]);
+        if (lane == 0) red[k][warp] = t;
     }
     __syncthreads();
     __shared__ bool is_last;
     if (threadIdx.x < 3) {
-        double v = 0.0;
-        for (int i = 0; i < kEnergyThreads / 32; ++i) v += red[threadIdx.x][i];
-        partials[blockIdx.x * 3 + threadIdx.x] = v;
+        double t = 0.0;
+        for (int i = 0; i < kStreamWarps; ++i) t += red[threadIdx.x][i];
+        partials[(int64_t)blockIdx.x * 3 + threadIdx.x] = t;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == kEnergyBlocks - 1);
+    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     __syncthreads();
     if (is_last && threadIdx.x < 3) {
         __threadfence();
-        double v = 0.0;
-        for (int b = 0; b < kEnergyBlocks; ++b)
-            v += *((volatile double *)partials + b * 3 + threadIdx.x);
-        out[threadIdx.x] = v;
+        double t = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b)
+            t += *((volatile double *)partials + (int64_t)b * 3 + threadIdx.x);
+        out[threadIdx.x] = t;
     }
 }
 
@@ -102,16 +116,18 @@ template <typename S>
 static cudaError_t launch_energy_t(const void *u, const void *f, const void *clean, int32_t h,
                                    int32_t w, int64_t ld, int bnd, double *out, void *ws,
                                    cudaStream_t st) {
-    double *partials = static_cast<double *>(ws);
-    unsigned int *ticket = reinterpret_cast<unsigned int *>(partials + 3 * kEnergyBlocks);
+    const int64_t nb = energy_blocks(h, w);
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    unsigned int *ticket = static_cast<unsigned int *>(ws);
+    double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + 256);
     cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     if (bnd == BND_ZERO)
-        energy_kernel<S, BND_ZERO><<<kEnergyBlocks, kEnergyThreads, 0, st>>>(
+        energy_kernel<S, BND_ZERO><<<(unsigned)nb, kStreamWarps * 32, 0, st>>>(
             static_cast<const S *>(u), static_cast<const S *>(f), static_cast<const S *>(clean), h,
             w, ld, out, partials, ticket);
     else
-        energy_kernel<S, BND_REPLICATE><<<kEnergyBlocks, kEnergyThreads, 0, st>>>(
+        energy_kernel<S, BND_REPLICATE><<<(unsigned)nb, kStreamWarps * 32, 0, st>>>(
             static_cast<const S *>(u), static_cast<const S *>(f), static_cast<const S *>(clean), h,
             w, ld, out, partials, ticket);
     return cudaGetLastError();

@@ -1,5 +1,5 @@
-// wmc_tile.cuh -- temporally blocked WMC flow kernel: T >= 2 Jacobi steps per launch in shared
-// memory.
+// wmc_tile.cuh -- temporally blocked WMC flow kernel: T Jacobi steps per launch in shared memory,
+// for one image or for a batch of images of different sizes in the same launch.
 //
 // The update U^{t+1} = U^t + step (lambda H^w(U^t) - mu (U^t - f)) (Sec. V-B, Eq. MCF) is
 // Jacobi-ordered: every pixel of step t+1 reads only U^t.  So a CTA can load a window of U^t,
@@ -10,10 +10,13 @@
 //   loaded window  [X0, X0+LW) x [Y0, Y0+LH)       one 2-D TMA box, zero-filled outside the image
 //   updated cells  [X0+2, X0+2+CW) x [Y0+1, Y0+1+CH)    every step (CW = 128, CH = 64)
 //   exact after T  [X0+1+T, X0+3+CW-T) x [Y0+T, Y0+2+CH-T)
-//   written back   [x0, x0+OW) x [y0, y0+OH),  x0 = X0 + M, y0 = Y0 + T
-// M (>= T+1) and OW are multiples of the TMA alignment (16 bytes of elements), so every TMA
-// x-coordinate is aligned and every thread's column pair (even, odd) is either wholly inside or
-// wholly outside the output tile.
+//   written back   [x0, x0+OWt) x [y0, y0+OHt),  x0 = X0 + M, y0 = Y0 + T
+// M (>= T+1) is a multiple of the TMA alignment (16 bytes of elements).  The output tile size
+// (OWt, OHt) is a launch parameter: a single-image launch uses the largest exact tile of its T
+// (Out<S,T>); a batch uses the tile of its deepest T for every launch, which any shallower
+// launch also covers exactly (its exact region is larger), so one tile table serves them all.
+// Output tile origins are multiples of the TMA alignment, which keeps every TMA x-coordinate
+// aligned.
 //
 // Threads: 16 warps as 2 (x) x 8 (y); lane l of warp (wx, wy) updates columns j = 2 + 64 wx + l
 // and j + 32 for rows i = 1 + 8 wy .. 8 + 8 wy.  The two columns are the two lanes of packed
@@ -32,10 +35,17 @@
 // Shared memory always holds FP32; for BF16/FP16 storage the TMA box lands in a staging area
 // and is widened once, and every step rounds its result to the storage type, so the arithmetic
 // is identical to the single-step streaming kernel.
+//
+// Batches: a tile table lists (image, x0, y0) for every tile of every image; each image has a
+// descriptor with its buffers (f, u, workspace), pitch, size, update coefficients (its own
+// lambda and step) and one tensor map per buffer.  A launch reads every image from the buffer of
+// one role and writes the buffer of another, so all images advance T steps together.
 #pragma once
 
 #include <cuda.h>
 #include <string.h>
+
+#include <atomic>
 
 #include "wmc_device.cuh"
 #include "wmc_internal.h"
@@ -59,7 +69,7 @@ template <typename S> struct Geom {
     static constexpr int SMEM = 2 * BUF * 4 + STAGE_BYTES + 128;  // + alignment slack
 };
 
-// Output tile of a T-step launch: margin M (>= T+1, TMA-aligned), width OW, height OH.
+// Output tile of a T-step single-image launch: margin M (>= T+1, TMA-aligned), width OW, height OH.
 template <typename S, int T> struct Out {
     static constexpr int A = Geom<S>::A;
     static constexpr int M = A * ((T + 1 + A - 1) / A);
@@ -67,18 +77,33 @@ template <typename S, int T> struct Out {
     static constexpr int OH = kCH + 2 - 2 * T;
 };
 
+// One image of a batch (device memory; 64-byte aligned for the tensor maps).
+struct alignas(64) BatchImage {
+    CUtensorMap map[3];   // tensor maps over buf[0..2]
+    const void *buf[3];   // 0: f (read only), 1: u (output), 2: workspace image
+    int64_t ld;
+    int32_t h, w;
+    float c_keep, c_f, c_h;
+    int32_t use_tma[3];
+};
+
 struct TileV2Params {
+    // single image (tiles from blockIdx)
     const void *u;    // U^t (device); read through the tensor map when use_tma
     const void *f;    // f or nullptr (mean-curvature flow)
     void *out;        // U^{t+T}
-    int64_t ldu, ldf, ldo;
+    int64_t ld;       // pitch of u, f and out
     int32_t h, w;
     int32_t ntx;      // tiles per row of tiles
     int32_t use_tma;
-    int32_t vec_f;    // f rows allow 2-element loads (aligned base, even pitch)
-    int32_t vec_o;    // same for the output
     float c_keep, c_f, c_h;
-    unsigned int *status;  // device status word (bit 0: a bounded wait gave up) or nullptr
+    // batch (tiles from the table)
+    const BatchImage *images;
+    const int4 *tiles;    // (image, x0, y0, 0) per tile
+    int32_t src_role, dst_role;
+    // both
+    int32_t owt, oht;     // output tile size
+    unsigned int *status; // device status word (bit 0: a bounded wait gave up) or nullptr
 };
 
 // ------------------------------------------------------------------ TMA / mbarrier helpers
@@ -129,13 +154,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, 
 
 constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s
 
-__device__ __forceinline__ float2 lds2(const float *p) {
-    return *reinterpret_cast<const float2 *>(p);
-}
-__device__ __forceinline__ void sts2(float *p, float a, float b) {
-    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
-}
-
 // ------------------------------------------------------------------------------- kernel
 // Per-thread constants of one tile.
 struct TileCtx {
@@ -143,6 +161,11 @@ struct TileCtx {
     int X0, Y0, gx;    // window origin, image column of the first cell
     int h, w;
     bool cin0, cin1;   // the two cells' columns lie inside the image
+    bool out0, out1;   // ... and inside the output tile
+    unsigned out_rows; // bit k: row ib + k is an output row inside the image
+    void *out;         // output image
+    int64_t ld;
+    float c_keep, c_h;
 };
 
 enum StepWrite { WRITE_INTERIOR = 0, WRITE_BORDER = 1, WRITE_GLOBAL = 2 };
@@ -161,18 +184,14 @@ __device__ __forceinline__ Row3 load_row3(const float *r) {
 
 // One Jacobi step over the thread's kRY rows x 2 columns, reading `src`, writing `dst` (shared)
 // or the output image (last step).
-template <int WMODE, int T, typename S, int BND>
+template <int WMODE, typename S, int BND>
 __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *__restrict__ dst,
-                                          const TileCtx &c, const float2 (&g)[kRY],
-                                          const TileV2Params &p) {
+                                          const TileCtx &c, const float2 (&g)[kRY]) {
     using G = Geom<S>;
     constexpr int P = G::P, LH = G::LH, LW = G::LW;
-    constexpr int M = Out<S, T>::M, OW = Out<S, T>::OW, OH = Out<S, T>::OH;
-    const float2 ch = make_float2(p.c_h, p.c_h), ck = make_float2(p.c_keep, p.c_keep);
+    const float2 ch = make_float2(c.c_h, c.c_h), ck = make_float2(c.c_keep, c.c_keep);
     const float *rp = src + (c.ib - 1) * P + c.j;
     Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
-    const bool col_out0 = (c.j >= M) & (c.j < M + OW);
-    const bool col_out1 = (c.j + 32 >= M) & (c.j + 32 < M + OW);
 #pragma unroll
     for (int k = 0; k < kRY; ++k) {
         const Row3 r2 = load_row3(rp + (k + 2) * P);
@@ -214,11 +233,10 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
                 }
             }
         } else {
-            const int gy = c.Y0 + i;
-            if ((i >= T) & (i < T + OH) & (gy < c.h)) {
-                S *o = static_cast<S *>(p.out) + (int64_t)gy * p.ldo + c.gx;
-                if (col_out0 & (c.gx < c.w)) Store<S>::store(o, v.x);
-                if (col_out1 & (c.gx + 32 < c.w)) Store<S>::store(o + 32, v.y);
+            if ((c.out_rows >> k) & 1u) {
+                S *o = static_cast<S *>(c.out) + (int64_t)(c.Y0 + i) * c.ld + c.gx;
+                if (c.out0) Store<S>::store(o, v.x);
+                if (c.out1) Store<S>::store(o + 32, v.y);
             }
         }
         r0 = r1;
@@ -226,15 +244,12 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
     }
 }
 
-template <int T, typename S, int BND>
+template <int T, typename S, int BND, bool BATCH>
 __global__ void __launch_bounds__(kTileThreadsV2, 2)
     tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const TileV2Params p) {
     using G = Geom<S>;
     constexpr int LW = G::LW, LH = G::LH, P = G::P, BUF = G::BUF;
     constexpr int M = Out<S, T>::M;
-    constexpr int OW = Out<S, T>::OW;
-    constexpr int OH = Out<S, T>::OH;
-    static_assert(OW > 0 && OH > 0, "tile too small for T");
 
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -242,65 +257,109 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *buf1 = buf0 + BUF;
 
-    const int h = p.h, w = p.w;
-    const int ty = blockIdx.x / p.ntx, tx = blockIdx.x - ty * p.ntx;
-    const int x0 = tx * OW, y0 = ty * OH;
+    // ---- this CTA's job: image, buffers, coefficients and output tile
+    const S *u;
+    const S *f;
+    TileCtx c;
+    const CUtensorMap *map;
+    bool use_tma;
+    int x0, y0;
+    float c_f;
+    if (BATCH) {
+        const int4 t = p.tiles[blockIdx.x];
+        const BatchImage &im = p.images[t.x];
+        u = static_cast<const S *>(im.buf[p.src_role]);
+        f = static_cast<const S *>(im.buf[0]);
+        c.out = const_cast<void *>(im.buf[p.dst_role]);
+        c.ld = im.ld;
+        c.h = im.h;
+        c.w = im.w;
+        c.c_keep = im.c_keep;
+        c.c_h = im.c_h;
+        c_f = im.c_f;
+        map = &im.map[p.src_role];
+        use_tma = im.use_tma[p.src_role] != 0;
+        x0 = t.y;
+        y0 = t.z;
+    } else {
+        u = static_cast<const S *>(p.u);
+        f = static_cast<const S *>(p.f);
+        c.out = p.out;
+        c.ld = p.ld;
+        c.h = p.h;
+        c.w = p.w;
+        c.c_keep = p.c_keep;
+        c.c_h = p.c_h;
+        c_f = p.c_f;
+        map = &tmap;
+        use_tma = p.use_tma != 0;
+        const int ty = blockIdx.x / p.ntx, tx = blockIdx.x - ty * p.ntx;
+        x0 = tx * p.owt;
+        y0 = ty * p.oht;
+    }
+    const int h = c.h, w = c.w;
     const int X0 = x0 - M, Y0 = y0 - T;
     const int tid = threadIdx.x;
     const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
 
     // ---- issue the load of the window of U^t
-    if (p.use_tma) {
+    if (use_tma) {
         if (tid == 0) mbar_init(smem_u32(&bar), 1);
         __syncthreads();
         if (tid == 0) {
             void *dst = (sizeof(S) == 4) ? static_cast<void *>(buf0)
                                          : static_cast<void *>(buf1 + BUF);  // staging
             mbar_expect_tx(smem_u32(&bar), (uint32_t)(LW * LH * sizeof(S)));
-            tma_load_2d(smem_u32(dst), &tmap, X0, Y0, smem_u32(&bar));
+            tma_load_2d(smem_u32(dst), map, X0, Y0, smem_u32(&bar));
         }
     } else {
-        const S *u = static_cast<const S *>(p.u);
         for (int idx = tid; idx < LH * LW; idx += kTileThreadsV2) {
             const int i = idx / LW, j = idx - (idx / LW) * LW;
             const int gy = Y0 + i, gx = X0 + j;
             float v = 0.0f;
-            if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = Store<S>::load(u + (int64_t)gy * p.ldu + gx);
+            if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = Store<S>::load(u + (int64_t)gy * c.ld + gx);
             buf0[i * P + j] = v;
         }
     }
 
     // ---- per-thread geometry and f (overlaps the load)
     const int lane = tid & 31, warp = tid >> 5;
-    TileCtx c;
     c.j = 2 + 64 * (warp & 1) + lane;
     c.ib = 1 + kRY * (warp >> 1);
     c.X0 = X0;
     c.Y0 = Y0;
     c.gx = X0 + c.j;
-    c.h = h;
-    c.w = w;
     c.cin0 = (c.gx >= 0) & (c.gx < w);
     c.cin1 = (c.gx + 32 >= 0) & (c.gx + 32 < w);
+    c.out0 = c.cin0 & (c.gx >= x0) & (c.gx < x0 + p.owt);
+    c.out1 = c.cin1 & (c.gx + 32 >= x0) & (c.gx + 32 < x0 + p.owt);
+    unsigned in_rows = 0;  // bit k: image row Y0 + ib + k exists
+    c.out_rows = 0;
+#pragma unroll
+    for (int k = 0; k < kRY; ++k) {
+        const int gy = Y0 + c.ib + k;
+        const bool rin = (gy >= 0) & (gy < h);
+        in_rows |= (rin ? 1u : 0u) << k;
+        c.out_rows |= ((rin & (gy >= y0) & (gy < y0 + p.oht)) ? 1u : 0u) << k;
+    }
     float2 g[kRY];
     {
-        const S *f = static_cast<const S *>(p.f);
-        const int gx = c.gx;
+        const float2 cf = make_float2(c_f, c_f);
+        const S *fr = f + (int64_t)(Y0 + c.ib) * c.ld + c.gx;
 #pragma unroll
         for (int k = 0; k < kRY; ++k) {
-            const int gy = Y0 + c.ib + k;
             float a = 0.0f, b = 0.0f;
-            if (f != nullptr && gy >= 0 && gy < h) {
-                const S *fr = f + (int64_t)gy * p.ldf;
-                if (c.cin0) a = Store<S>::load(fr + gx);
-                if (c.cin1) b = Store<S>::load(fr + gx + 32);
+            if (f != nullptr && ((in_rows >> k) & 1u)) {
+                const S *fk = fr + (int64_t)k * c.ld;
+                if (c.cin0) a = Store<S>::load(fk);
+                if (c.cin1) b = Store<S>::load(fk + 32);
             }
-            g[k] = __fmul2_rn(make_float2(p.c_f, p.c_f), make_float2(a, b));
+            g[k] = __fmul2_rn(cf, make_float2(a, b));
         }
     }
 
     // ---- wait for the window
-    if (p.use_tma) {
+    if (use_tma) {
         const bool ok = mbar_wait_bounded(smem_u32(&bar), 0, kWaitLimitNs);
         if (__syncthreads_or(!ok)) {
             if (tid == 0 && p.status) atomicOr(p.status, 1u);
@@ -331,9 +390,9 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
                 j2 = (t < LW) ? t : t - LW;
                 if (i < 0 || i >= LH || j2 < jlo || j2 > jhi) continue;
             } else {
-                const int u = t - 2 * LW;
-                j2 = (u < LH) ? jc0 : jc1;
-                i = (u < LH) ? u : u - LH;
+                const int q = t - 2 * LW;
+                j2 = (q < LH) ? jc0 : jc1;
+                i = (q < LH) ? q : q - LH;
                 if (j2 < 0 || j2 >= LW || i < ilo || i > ihi) continue;
             }
             const int yy = Y0 + i, xx = X0 + j2;
@@ -349,54 +408,69 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
         const float *src = (s & 1) ? buf1 : buf0;
         float *dst = (s & 1) ? buf0 : buf1;
         if (!border)
-            tile_step<WRITE_INTERIOR, T, S, BND>(src, dst, c, g, p);
+            tile_step<WRITE_INTERIOR, S, BND>(src, dst, c, g);
         else
-            tile_step<WRITE_BORDER, T, S, BND>(src, dst, c, g, p);
+            tile_step<WRITE_BORDER, S, BND>(src, dst, c, g);
         __syncthreads();
     }
-    tile_step<WRITE_GLOBAL, T, S, BND>(((T - 1) & 1) ? buf1 : buf0, nullptr, c, g, p);
+    tile_step<WRITE_GLOBAL, S, BND>(((T - 1) & 1) ? buf1 : buf0, nullptr, c, g);
 }
 
-template <int T, typename S, int BND>
-cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, cudaStream_t st) {
+template <int T, typename S, int BND, bool BATCH>
+cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, int64_t nblocks,
+                             cudaStream_t st) {
     using G = Geom<S>;
-    constexpr int OW = Out<S, T>::OW;
-    constexpr int OH = Out<S, T>::OH;
-    const int64_t ntx = (p.w + OW - 1) / OW, nty = (p.h + OH - 1) / OH;
-    if (ntx * nty > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    p.ntx = (int32_t)ntx;
-    cudaError_t e = cudaFuncSetAttribute(tile_v2_kernel<T, S, BND>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (!BATCH) {
+        p.owt = Out<S, T>::OW;
+        p.oht = Out<S, T>::OH;
+        const int64_t ntx = (p.w + p.owt - 1) / p.owt, nty = (p.h + p.oht - 1) / p.oht;
+        nblocks = ntx * nty;
+        p.ntx = (int32_t)ntx;
+    }
+    if (nblocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (nblocks == 0) return cudaSuccess;
+    // The shared-memory opt-in is per device; set it once per device so that launches made
+    // while a stream is being captured into a graph issue no attribute calls.
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(attr_set.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(tile_v2_kernel<T, S, BND, BATCH>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set.fetch_or(bit, std::memory_order_release);
+    }
     CUtensorMap dummy;
-    if (!p.use_tma) {
+    if (BATCH || !p.use_tma) {
         memset(&dummy, 0, sizeof dummy);
         map = &dummy;
     }
-    tile_v2_kernel<T, S, BND><<<(unsigned)(ntx * nty), kTileThreadsV2, G::SMEM, st>>>(*map, p);
+    tile_v2_kernel<T, S, BND, BATCH><<<(unsigned)nblocks, kTileThreadsV2, G::SMEM, st>>>(*map, p);
     return cudaGetLastError();
 }
 
 template <typename S, int BND>
 cudaError_t launch_tile_v2_steps(int steps, const CUtensorMap *map, const TileV2Params &p,
-                                 cudaStream_t st) {
+                                 int64_t batch_tiles, cudaStream_t st) {
+    const bool b = batch_tiles >= 0;
+#define WMC_TILE_CASE(T)                                                                        \
+    case T:                                                                                     \
+        return b ? launch_tile_v2_t<T, S, BND, true>(map, p, batch_tiles, st)                   \
+                 : launch_tile_v2_t<T, S, BND, false>(map, p, 0, st);
     switch (steps) {
-        case 2: return launch_tile_v2_t<2, S, BND>(map, p, st);
-        case 3: return launch_tile_v2_t<3, S, BND>(map, p, st);
-        case 4: return launch_tile_v2_t<4, S, BND>(map, p, st);
-        case 5: return launch_tile_v2_t<5, S, BND>(map, p, st);
-        case 6: return launch_tile_v2_t<6, S, BND>(map, p, st);
-        case 7: return launch_tile_v2_t<7, S, BND>(map, p, st);
-        case 8: return launch_tile_v2_t<8, S, BND>(map, p, st);
+        WMC_TILE_CASE(1)
+        WMC_TILE_CASE(2)
+        WMC_TILE_CASE(3)
+        WMC_TILE_CASE(4)
+        WMC_TILE_CASE(5)
+        WMC_TILE_CASE(6)
+        WMC_TILE_CASE(7)
+        WMC_TILE_CASE(8)
         default: return cudaErrorInvalidValue;
     }
-}
-
-template <typename S>
-cudaError_t launch_tile_v2_dtype(int steps, int bnd, const CUtensorMap *map,
-                                 const TileV2Params &p, cudaStream_t st) {
-    if (bnd == BND_ZERO) return launch_tile_v2_steps<S, BND_ZERO>(steps, map, p, st);
-    return launch_tile_v2_steps<S, BND_REPLICATE>(steps, map, p, st);
+#undef WMC_TILE_CASE
 }
 
 }  // namespace wmc

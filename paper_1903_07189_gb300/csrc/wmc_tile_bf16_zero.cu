@@ -3,7 +3,7 @@
 
 namespace wmc {
 cudaError_t launch_tile_bf16_zero(int steps, const CUtensorMap *map, const TileV2Params &p,
-                                   cudaStream_t st) {
-    return launch_tile_v2_steps<__nv_bfloat16, BND_ZERO>(steps, map, p, st);
+                                   int64_t batch_tiles, cudaStream_t st) {
+    return launch_tile_v2_steps<__nv_bfloat16, BND_ZERO>(steps, map, p, batch_tiles, st);
 }
 }  // namespace wmc

@@ -32,6 +32,17 @@ class Config(ctypes.Structure):
     _fields_ = [("steps_per_launch", ctypes.c_int32), ("tile", ctypes.c_int32)]
 
 
+class Image(ctypes.Structure):
+    """wmc_image_t"""
+    _fields_ = [("f", ctypes.c_void_p), ("u", ctypes.c_void_p), ("h", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("ld", ctypes.c_int64), ("lam", ctypes.c_float), ("step", ctypes.c_float)]
+
+
+class BatchPlan(ctypes.Structure):
+    """wmc_batch_t (opaque, caller-owned)"""
+    _fields_ = [("opaque", ctypes.c_int64 * 16)]
+
+
 _lib = None
 
 # name -> (restype, argtypes) for every symbol declared in include/wmc.h
@@ -48,6 +59,11 @@ SIGNATURES = {
                                 _vp]),
     "wmc_energy_workspace_size": (_sz, [_i32, _i32]),
     "wmc_energy": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _i32, _vp, _vp, _sz, _vp]),
+    "wmc_batch_workspace_size": (_sz, [ctypes.POINTER(Image), _i32, _i32, ctypes.POINTER(Config)]),
+    "wmc_batch_plan": (_i32, [ctypes.POINTER(Image), _i32, _i32, _i32, ctypes.POINTER(Config), _vp, _sz,
+                              ctypes.POINTER(BatchPlan), _vp]),
+    "wmc_batch_run": (_i32, [ctypes.POINTER(BatchPlan), _i32, _vp]),
+    "wmc_denoise_batched": (_i32, [ctypes.POINTER(Image), _i32, _i32, _i32, _i32, _vp, _sz, _vp]),
     "wmc_status_string": (ctypes.c_char_p, [_i32]),
     "wmc_last_error": (ctypes.c_char_p, []),
     "wmc_version": (_i32, []),
@@ -214,6 +230,62 @@ def energy(u: torch.Tensor, f: torch.Tensor | None = None, clean: torch.Tensor |
                           BOUNDARY[boundary], out.data_ptr(), workspace.data_ptr(), workspace.numel(),
                           _stream(u.device)), "wmc_energy")
     return out
+
+
+class Batch:
+    """A planned batch of images of any sizes, each with its own lambda and step (wmc_batch_plan).
+
+    fs: 2-D CUDA tensors of one dtype (U^0 = f); outs: optional output tensors (same shapes and
+    pitches).  run(iters) enqueues wmc_batch_run on the current stream: kernel launches only, so
+    it can be captured into a CUDA graph.  The plan keeps references to fs, outs and its
+    workspace, which must outlive every run.
+    """
+
+    def __init__(self, fs, lams, steps=None, outs=None, boundary: str = "replicate",
+                 steps_per_launch: int = 0):
+        if not fs:
+            raise ValueError("empty batch")
+        dt = fs[0].dtype
+        if steps is None:
+            steps = [default_step(l) for l in lams]
+        if outs is None:
+            outs = [torch.empty_strided(f.shape, f.stride(), dtype=f.dtype, device=f.device) for f in fs]
+        if not (len(fs) == len(lams) == len(steps) == len(outs)):
+            raise ValueError("fs, lams, steps and outs must have the same length")
+        n = len(fs)
+        imgs = (Image * n)()
+        for i, (f, u, l, st) in enumerate(zip(fs, outs, lams, steps)):
+            pf, h, w, ld = _img(f, f"fs[{i}]")
+            pu, h2, w2, ld2 = _img(u, f"outs[{i}]")
+            if (h2, w2, ld2) != (h, w, ld) or f.dtype != dt or u.dtype != dt:
+                raise ValueError(f"image {i}: f and out must share shape, pitch and dtype")
+            imgs[i] = Image(pf, pu, h, w, ld, float(l), float(st))
+        lib = load()
+        self.cfg = Config(int(steps_per_launch), 0)
+        self.dtype = DTYPES[dt]
+        size = lib.wmc_batch_workspace_size(imgs, n, self.dtype, ctypes.byref(self.cfg))
+        if size == 0:
+            raise WMCError(1, "wmc_batch_workspace_size", "invalid batch")
+        self.device = fs[0].device
+        self.workspace = _workspace(size, self.device)
+        self.plan = BatchPlan()
+        _check(lib.wmc_batch_plan(imgs, n, self.dtype, BOUNDARY[boundary], ctypes.byref(self.cfg),
+                                  self.workspace.data_ptr(), self.workspace.numel(), ctypes.byref(self.plan),
+                                  _stream(self.device)), "wmc_batch_plan")
+        self.fs, self.outs, self.imgs, self.n = list(fs), outs, imgs, n
+
+    def run(self, iters: int):
+        _check(load().wmc_batch_run(ctypes.byref(self.plan), int(iters), _stream(self.device)), "wmc_batch_run")
+        return self.outs
+
+    def check_status(self):
+        check_status(self.workspace)
+
+
+def denoise_batched(fs, lams, steps=None, iters: int = 100, boundary: str = "replicate", outs=None,
+                    steps_per_launch: int = 0):
+    """Plan and run one batch; returns the output tensors."""
+    return Batch(fs, lams, steps, outs, boundary, steps_per_launch).run(iters)
 
 
 def psnr(sse: float, n: int, peak: float = 1.0) -> float:

@@ -119,3 +119,32 @@ def test_energy_validation(lib):
     assert lib.wmc_energy(A, None, None, 4, 4, 4, 0, 0, None, None, 0, None) == INVALID
     assert lib.wmc_energy(None, None, None, 4, 4, 4, 0, 0, B, 0x30000000, 1 << 20, None) == INVALID
     assert lib.wmc_energy(A, None, None, 4, 4, 4, 0, 0, B, None, 0, None) == WORKSPACE
+
+
+def _images(specs):
+    arr = (wmc.Image * len(specs))()
+    for i, (f, u, h, w, ld, lam, st) in enumerate(specs):
+        arr[i] = wmc.Image(f, u, h, w, ld, lam, st)
+    return arr
+
+
+def test_batch_validation(lib):
+    plan = wmc.BatchPlan()
+    ok = (A, B, 8, 8, 8, 1.0, 0.25)
+    cfg = wmc.Config(3, 0)
+    imgs = _images([ok])
+    assert lib.wmc_batch_plan(imgs, -1, 0, 0, None, 0x30000000, 1 << 20, ctypes.byref(plan), None) == INVALID
+    assert lib.wmc_batch_plan(_images([(A, B, 8, 8, 8, float("nan"), 0.25)]), 1, 0, 0, None, 0x30000000,
+                              1 << 20, ctypes.byref(plan), None) == INVALID and "image 0" in _err(lib)
+    assert lib.wmc_batch_plan(_images([ok, (A + 4096, B + 64, 8, 8, 8, 1.0, 0.25)]), 2, 0, 0, None,
+                              0x30000000, 1 << 20, ctypes.byref(plan), None) == ALIAS
+    assert lib.wmc_batch_plan(_images([ok, (A, B + 4096, 8, 8, 8, 1.0, 0.25)]), 2, 0, 0, None,
+                              0x30000000, 16, ctypes.byref(plan), None) == WORKSPACE  # shared f is fine
+    assert lib.wmc_batch_plan(imgs, 1, 0, 0, ctypes.byref(wmc.Config(9, 0)), 0x30000000, 1 << 20,
+                              ctypes.byref(plan), None) == INVALID
+    assert lib.wmc_batch_plan(_images([(A, B, 8, 8, 7, 1.0, 0.25)]), 1, 0, 0, None, 0x30000000, 1 << 20,
+                              ctypes.byref(plan), None) == INVALID
+    need = lib.wmc_batch_workspace_size(imgs, 1, 0, ctypes.byref(cfg))
+    assert need > 0 and need % 256 == 0
+    assert lib.wmc_batch_workspace_size(_images([(A, B, 8, 8, 7, 1.0, 0.25)]), 1, 0, None) == 0
+    assert lib.wmc_batch_run(ctypes.byref(wmc.BatchPlan()), 5, None) == INVALID  # not planned
