@@ -28,8 +28,8 @@
 //
 // Image boundary.  ZERO: the TMA fill supplies the zeros; in tiles touching the border, cells
 // outside the image are rewritten as 0 every step.  REPLICATE: the ring of cells just outside
-// the image is kept equal to its nearest in-image cell (filled after the load, then rewritten
-// by the in-image edge cells every step), so in-image cells read their neighbours without any
+// the image is kept equal to its nearest in-image cell (refreshed after the load and after every
+// step, in tiles touching the border only), so in-image cells read their neighbours without any
 // clamping and produce exactly what clamped reads would.
 //
 // Shared memory always holds FP32; for BF16/FP16 storage the TMA box lands in a staging area
@@ -163,8 +163,6 @@ struct TileCtx {
     bool cin0, cin1;   // the two cells' columns lie inside the image
     bool out0, out1;   // ... and inside the output tile
     unsigned out_rows; // bit k: row ib + k is an output row inside the image
-    void *out;         // output image
-    int64_t ld;
     float c_keep, c_h;
 };
 
@@ -186,7 +184,8 @@ __device__ __forceinline__ Row3 load_row3(const float *r) {
 // or the output image (last step).
 template <int WMODE, typename S, int BND>
 __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *__restrict__ dst,
-                                          const TileCtx &c, const float2 (&g)[kRY]) {
+                                          const TileCtx &c, const float2 (&g)[kRY],
+                                          S *__restrict__ orow = nullptr, int64_t ld = 0) {
     using G = Geom<S>;
     constexpr int P = G::P, LH = G::LH, LW = G::LW;
     const float2 ch = make_float2(c.c_h, c.c_h), ck = make_float2(c.c_keep, c.c_keep);
@@ -203,44 +202,58 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
             d[0] = Store<S>::round(v.x);
             d[32] = Store<S>::round(v.y);
         } else if (WMODE == WRITE_BORDER) {
-            v.x = Store<S>::round(v.x);
-            v.y = Store<S>::round(v.y);
+            // tiles touching the border: cells outside the image keep 0 (ZERO) or are left
+            // for the ring refresh after the step (REPLICATE)
             const int gy = c.Y0 + i;
             const bool rin = (gy >= 0) & (gy < c.h);
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const bool in = rin & (e == 0 ? c.cin0 : c.cin1);
-                const float ve = e == 0 ? v.x : v.y;
-                const int jc = c.j + 32 * e;
-                if (BND == BND_ZERO) {
-                    dst[i * P + jc] = in ? ve : 0.0f;
-                } else {
-                    // in-image cells: normal write; cells on the image edge also refresh the
-                    // ring cells outside the image that copy them
-                    if (!in) continue;
-                    const int xe = c.gx + 32 * e;
-                    dst[i * P + jc] = ve;
-                    if ((gy == 0) | (gy == c.h - 1) | (xe == 0) | (xe == c.w - 1)) {
-                        const int up = (gy == 0) ? -1 : 0, dn = (gy == c.h - 1) ? 1 : 0;
-                        const int lf = (xe == 0) ? -1 : 0, rt = (xe == c.w - 1) ? 1 : 0;
-                        for (int di = up; di <= dn; ++di)
-                            for (int dj = lf; dj <= rt; ++dj) {
-                                if (di == 0 && dj == 0) continue;
-                                const int ii = i + di, jj = jc + dj;
-                                if (ii >= 0 && ii < LH && jj >= 0 && jj < LW) dst[ii * P + jj] = ve;
-                            }
-                    }
-                }
+            const bool in0 = rin & c.cin0, in1 = rin & c.cin1;
+            float *d = dst + i * P + c.j;
+            if (BND == BND_ZERO) {
+                d[0] = in0 ? Store<S>::round(v.x) : 0.0f;
+                d[32] = in1 ? Store<S>::round(v.y) : 0.0f;
+            } else {
+                if (in0) d[0] = Store<S>::round(v.x);
+                if (in1) d[32] = Store<S>::round(v.y);
             }
         } else {
             if ((c.out_rows >> k) & 1u) {
-                S *o = static_cast<S *>(c.out) + (int64_t)(c.Y0 + i) * c.ld + c.gx;
+                S *o = orow + (int64_t)k * ld;  // row Y0 + ib + k, column gx
                 if (c.out0) Store<S>::store(o, v.x);
                 if (c.out1) Store<S>::store(o + 32, v.y);
             }
         }
         r0 = r1;
         r1 = r2;
+    }
+}
+
+// REPLICATE: set the ring of cells just outside the image (image rows -1 and h, image columns -1
+// and w, where they cross the window) to the value of the nearest in-image cell, so that in-image
+// cells can read their neighbours without clamping.  Corner cells belong to two segments and get
+// the same value from both.
+template <typename S>
+__device__ __forceinline__ void refresh_ring(float *buf, int X0, int Y0, int h, int w, int tid) {
+    using G = Geom<S>;
+    constexpr int LW = G::LW, LH = G::LH, P = G::P;
+    const int ir0 = -1 - Y0, ir1 = h - Y0;  // shared rows of image rows -1 and h
+    const int jc0 = -1 - X0, jc1 = w - X0;  // shared columns of image columns -1 and w
+    const int jlo = max(jc0, 0), jhi = min(jc1, LW - 1);
+    const int ilo = max(ir0, 0), ihi = min(ir1, LH - 1);
+    for (int t = tid; t < 2 * (LW + LH); t += kTileThreadsV2) {
+        int i, j2;
+        if (t < 2 * LW) {
+            i = (t < LW) ? ir0 : ir1;
+            j2 = (t < LW) ? t : t - LW;
+            if (i < 0 || i >= LH || j2 < jlo || j2 > jhi) continue;
+        } else {
+            const int q = t - 2 * LW;
+            j2 = (q < LH) ? jc0 : jc1;
+            i = (q < LH) ? q : q - LH;
+            if (j2 < 0 || j2 >= LW || i < ilo || i > ihi) continue;
+        }
+        const int yy = Y0 + i, xx = X0 + j2;
+        const int ci = min(max(yy, 0), h - 1) - Y0, cj = min(max(xx, 0), w - 1) - X0;
+        buf[i * P + j2] = buf[ci * P + cj];
     }
 }
 
@@ -265,13 +278,13 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
     bool use_tma;
     int x0, y0;
     float c_f;
+    int64_t ld;
     if (BATCH) {
         const int4 t = p.tiles[blockIdx.x];
         const BatchImage &im = p.images[t.x];
         u = static_cast<const S *>(im.buf[p.src_role]);
         f = static_cast<const S *>(im.buf[0]);
-        c.out = const_cast<void *>(im.buf[p.dst_role]);
-        c.ld = im.ld;
+        ld = im.ld;
         c.h = im.h;
         c.w = im.w;
         c.c_keep = im.c_keep;
@@ -284,8 +297,7 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
     } else {
         u = static_cast<const S *>(p.u);
         f = static_cast<const S *>(p.f);
-        c.out = p.out;
-        c.ld = p.ld;
+        ld = p.ld;
         c.h = p.h;
         c.w = p.w;
         c.c_keep = p.c_keep;
@@ -317,7 +329,7 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
             const int i = idx / LW, j = idx - (idx / LW) * LW;
             const int gy = Y0 + i, gx = X0 + j;
             float v = 0.0f;
-            if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = Store<S>::load(u + (int64_t)gy * c.ld + gx);
+            if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = Store<S>::load(u + (int64_t)gy * ld + gx);
             buf0[i * P + j] = v;
         }
     }
@@ -345,12 +357,12 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
     float2 g[kRY];
     {
         const float2 cf = make_float2(c_f, c_f);
-        const S *fr = f + (int64_t)(Y0 + c.ib) * c.ld + c.gx;
+        const S *fr = f + (int64_t)(Y0 + c.ib) * ld + c.gx;
 #pragma unroll
         for (int k = 0; k < kRY; ++k) {
             float a = 0.0f, b = 0.0f;
             if (f != nullptr && ((in_rows >> k) & 1u)) {
-                const S *fk = fr + (int64_t)k * c.ld;
+                const S *fk = fr + (int64_t)k * ld;
                 if (c.cin0) a = Store<S>::load(fk);
                 if (c.cin1) b = Store<S>::load(fk + 32);
             }
@@ -376,29 +388,8 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
     }
 
     // ---- REPLICATE: fill the ring just outside the image from its nearest in-image cell.
-    // The ring is at most four segments (image rows -1 and h, image columns -1 and w) crossing
-    // the window; corner cells belong to two segments and get the same value from both.
     if (BND == BND_REPLICATE && border) {
-        const int ir0 = -1 - Y0, ir1 = h - Y0;  // shared rows of image rows -1 and h
-        const int jc0 = -1 - X0, jc1 = w - X0;  // shared columns of image columns -1 and w
-        const int jlo = max(jc0, 0), jhi = min(jc1, LW - 1);
-        const int ilo = max(ir0, 0), ihi = min(ir1, LH - 1);
-        for (int t = tid; t < 2 * (LW + LH); t += kTileThreadsV2) {
-            int i, j2;
-            if (t < 2 * LW) {
-                i = (t < LW) ? ir0 : ir1;
-                j2 = (t < LW) ? t : t - LW;
-                if (i < 0 || i >= LH || j2 < jlo || j2 > jhi) continue;
-            } else {
-                const int q = t - 2 * LW;
-                j2 = (q < LH) ? jc0 : jc1;
-                i = (q < LH) ? q : q - LH;
-                if (j2 < 0 || j2 >= LW || i < ilo || i > ihi) continue;
-            }
-            const int yy = Y0 + i, xx = X0 + j2;
-            const int ci = min(max(yy, 0), h - 1) - Y0, cj = min(max(xx, 0), w - 1) - X0;
-            buf0[i * P + j2] = buf0[ci * P + cj];
-        }
+        refresh_ring<S>(buf0, X0, Y0, h, w, tid);
         __syncthreads();
     }
 
@@ -407,13 +398,32 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
     for (int s = 0; s < T - 1; ++s) {
         const float *src = (s & 1) ? buf1 : buf0;
         float *dst = (s & 1) ? buf0 : buf1;
-        if (!border)
+        if (!border) {
             tile_step<WRITE_INTERIOR, S, BND>(src, dst, c, g);
-        else
+            __syncthreads();
+        } else {
             tile_step<WRITE_BORDER, S, BND>(src, dst, c, g);
-        __syncthreads();
+            __syncthreads();
+            if (BND == BND_REPLICATE) {
+                refresh_ring<S>(dst, X0, Y0, h, w, tid);
+                __syncthreads();
+            }
+        }
     }
-    tile_step<WRITE_GLOBAL, S, BND>(((T - 1) & 1) ? buf1 : buf0, nullptr, c, g);
+    // the output pointer is looked up again here (kernel parameters, or the image descriptor in
+    // L1) rather than kept in registers through the steps
+    S *out;
+    int64_t ldo;
+    if (BATCH) {
+        const BatchImage &im = p.images[p.tiles[blockIdx.x].x];
+        out = static_cast<S *>(const_cast<void *>(im.buf[p.dst_role]));
+        ldo = im.ld;
+    } else {
+        out = static_cast<S *>(p.out);
+        ldo = p.ld;
+    }
+    tile_step<WRITE_GLOBAL, S, BND>(((T - 1) & 1) ? buf1 : buf0, nullptr, c, g,
+                                    out + (int64_t)(Y0 + c.ib) * ldo + c.gx, ldo);
 }
 
 template <int T, typename S, int BND, bool BATCH>
