@@ -47,7 +47,7 @@ BYTES_PER_PX_LAUNCH = 12  # read U, read f, write U (FP32): algorithmic bytes of
 # compare/select/sign logic (7 more) runs on the separate ALU pipe and is not counted.
 FMA_OPS_PER_PX_ITER = 27
 SMS, FP32_LANES_PER_SM = 152, 128
-DEFAULT_T = 3
+DEFAULT_T = 4
 
 
 def parse():

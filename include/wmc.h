@@ -159,7 +159,7 @@ wmc_status_t wmc_energy(const void *u, const void *f, const void *clean, int32_t
 
 /* ------------------------------------------------------------------------------------------
  * Batched denoising: many images of different sizes, each with its own lambda and step, advanced
- * together -- every kernel launch takes T Jacobi steps (wmc_config_t.steps_per_launch, default 3)
+ * together -- every kernel launch takes T Jacobi steps (wmc_config_t.steps_per_launch, default 4)
  * on the tiles of all images (Sec. V-B flow with A = I; colour channels are images too, as the
  * paper treats them separately, Sec. V-D).
  *

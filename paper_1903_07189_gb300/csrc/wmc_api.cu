@@ -151,7 +151,7 @@ cudaError_t launch_tile(wmc_dtype_t dtype, wmc_boundary_t bnd, int steps, const 
     }
 }
 
-constexpr int kDefaultSteps = 3;
+constexpr int kDefaultSteps = 4;
 constexpr size_t kStatusBytes = WMC_WORKSPACE_ALIGN;
 
 size_t image_bytes(int32_t h, int64_t ld, wmc_dtype_t dtype) {
