@@ -125,6 +125,31 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
 wmc_status_t wmc_denoise_status(const void *workspace, wmc_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
+ * wmc_denoise_noalloc: wmc_denoise without a workspace argument and without allocating.  It is
+ * for callers that cannot obtain device memory for scratch space: code running where a memory
+ * pool is owned by someone else and may not be grown, real-time or embedded hosts that forbid
+ * allocation after start-up, or bindings that can pass existing image pointers but have no
+ * CUDA allocator of their own.  (The paper has no counterpart: this is an interface choice.)
+ *   Scratch comes from one fixed device array of wmc_denoise_noalloc_max_bytes() bytes
+ *   (32 MiB) inside the library; every GPU that loads the library holds it until the process
+ *   exits.  Images whose wmc_denoise_workspace_size() exceeds that are rejected with
+ *   WMC_ERR_INVALID_ARG (FP32 up to about 8.3 M pixels, e.g. 2880 x 2880; BF16/FP16 up to about
+ *   16.7 M, e.g. 4064 x 4064) -- use wmc_denoise for larger ones.
+ *   The first call on each device looks up the array's device address with that device
+ *   current; make that first call before capturing any stream into a CUDA graph.
+ *   All calls on a device share the one array and the array keeps the last call's contents:
+ *   calls whose work overlaps on the GPU (different streams, or threads enqueueing at the same
+ *   time) race and corrupt each other; serialise them (one stream, or events).  The status
+ *   word at the start of the array is cleared by every call.  Other arguments, results and
+ *   errors: as wmc_denoise.
+ */
+size_t wmc_denoise_noalloc_max_bytes(void);
+
+wmc_status_t wmc_denoise_noalloc(const void *f, const void *u0, void *u, int32_t h, int32_t w,
+                                 int64_t ld, wmc_dtype_t dtype, float lambda, float step,
+                                 int32_t iters, wmc_boundary_t bnd, wmc_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
  * wmc_denoise_host: wmc_denoise on HOST buffers.  Copies f (and u0) to the device workspace on
  * `stream`, runs the flow there and copies U^iters back into u_host; all of it is enqueued on
  * `stream` and the call returns without waiting (synchronise the stream before reading

@@ -419,6 +419,41 @@ void for_each_launch(int iters, int T, F &&fn) {
 
 }  // namespace
 
+// ------------------------------------------------------------------ fixed device scratch
+// Scratch for wmc_denoise_noalloc: one status word and one ping-pong image, in a statically
+// sized device array that every GPU loading this library holds until the process exits.  Host
+// code must not pass `wmc_noalloc_scratch` itself to a kernel (on the host that name is only a
+// stand-in); it looks up the device address once per device below.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char wmc_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (resolved on the first call per
+// device, with that device current).
+wmc_status_t noalloc_scratch(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(WMC_ERR_UNSUPPORTED, "device ordinal %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, wmc_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(wmc_noalloc_scratch)");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return WMC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *wmc_status_string(wmc_status_t s) {
@@ -724,6 +759,31 @@ wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t
         wmc_batch_plan(imgs, n, dtype, bnd, nullptr, workspace, workspace_bytes, &plan, stream);
     if (s != WMC_OK) return s;
     return wmc_batch_run(&plan, iters, stream);
+}
+
+size_t wmc_denoise_noalloc_max_bytes(void) { return kNoAllocScratchBytes; }
+
+wmc_status_t wmc_denoise_noalloc(const void *f, const void *u0, void *u, int32_t h, int32_t w,
+                                 int64_t ld, wmc_dtype_t dtype, float lambda, float step,
+                                 int32_t iters, wmc_boundary_t bnd, wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    int T = 0;
+    wmc_status_t s =
+        check_flow_args(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, nullptr, &T);
+    if (s != WMC_OK) return s;
+    if (h == 0 || w == 0) return WMC_OK;
+    const size_t need = wmc_denoise_workspace_size(h, w, ld, dtype);
+    if (need > kNoAllocScratchBytes)
+        return fail(WMC_ERR_INVALID_ARG,
+                    "image needs %zu bytes of scratch; the fixed device scratch of "
+                    "wmc_denoise_noalloc holds %zu bytes (use wmc_denoise with a workspace)",
+                    need, kNoAllocScratchBytes);
+    void *scratch = nullptr;
+    if ((s = noalloc_scratch(&scratch)) != WMC_OK) return s;
+    // run_flow clears the status word at the start of every call; nothing else in the scratch
+    // needs a defined value (the ping-pong image is always written before it is read)
+    return run_flow(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, T, scratch,
+                    (cudaStream_t)stream);
 }
 
 }  // extern "C"

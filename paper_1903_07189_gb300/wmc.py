@@ -54,6 +54,8 @@ SIGNATURES = {
     "wmc_denoise_ex": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32,
                               ctypes.POINTER(Config), _vp, _sz, _vp]),
     "wmc_denoise_status": (_i32, [_vp, _vp]),
+    "wmc_denoise_noalloc_max_bytes": (_sz, []),
+    "wmc_denoise_noalloc": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp]),
     "wmc_denoise_host_workspace_size": (_sz, [_i32, _i32, _i64, _i32]),
     "wmc_denoise_host": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp, _sz,
                                 _vp]),
