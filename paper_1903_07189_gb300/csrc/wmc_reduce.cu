@@ -27,7 +27,7 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <typename S, int BND>
+template <typename S, int BND, bool VEC>
 __global__ void __launch_bounds__(kStreamWarps * 32)
     energy_kernel(const S *__restrict__ u, const S *__restrict__ f, const S *__restrict__ clean,
                   int h, int w, int64_t ld, double *__restrict__ out,
@@ -48,9 +48,17 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
             bool ok;
             const int y = row_index<BND>(y0 - 1 + k, h, &ok);
             const S *row = u + (int64_t)y * ld;
-            v[k] = load_pair<S, BND, false>(row, x, w, ok);
+            v[k] = load_pair<S, BND, VEC>(row, x, w, ok);
             el[k] = (lane == 0) ? load_one<S, BND>(row, x - 1, w, ok) : 0.0f;
             er[k] = (lane == 31) ? load_one<S, BND>(row, x + 2, w, ok) : 0.0f;
+        }
+        float2 fv[R], cv[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int y = min(y0 + k, h - 1);
+            fv[k] = f ? load_pair<S, BND_ZERO, VEC>(f + (int64_t)y * ld, x, w, true) : make_float2(0.f, 0.f);
+            cv[k] = clean ? load_pair<S, BND_ZERO, VEC>(clean + (int64_t)y * ld, x, w, true)
+                          : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -72,14 +80,12 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
             if (in0) s0 += fabsf(h0) * (1.0f / 12.0f);
             if (in1) s0 += fabsf(h1) * (1.0f / 12.0f);
             if (f) {
-                const float2 fv = load_pair<S, BND_ZERO, false>(f + (int64_t)y * ld, x, w, true);
-                const float d0 = v[k + 1].x - fv.x, d1 = v[k + 1].y - fv.y;
+                const float d0 = v[k + 1].x - fv[k].x, d1 = v[k + 1].y - fv[k].y;
                 if (in0) s1 = fmaf(d0, d0, s1);
                 if (in1) s1 = fmaf(d1, d1, s1);
             }
             if (clean) {
-                const float2 cv = load_pair<S, BND_ZERO, false>(clean + (int64_t)y * ld, x, w, true);
-                const float d0 = v[k + 1].x - cv.x, d1 = v[k + 1].y - cv.y;
+                const float d0 = v[k + 1].x - cv[k].x, d1 = v[k + 1].y - cv[k].y;
                 if (in0) s2 = fmaf(d0, d0, s2);
                 if (in1) s2 = fmaf(d1, d1, s2);
             }
@@ -122,14 +128,21 @@ static cudaError_t launch_energy_t(const void *u, const void *f, const void *cle
     double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + 256);
     cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    if (bnd == BND_ZERO)
-        energy_kernel<S, BND_ZERO><<<(unsigned)nb, kStreamWarps * 32, 0, st>>>(
-            static_cast<const S *>(u), static_cast<const S *>(f), static_cast<const S *>(clean), h,
-            w, ld, out, partials, ticket);
-    else
-        energy_kernel<S, BND_REPLICATE><<<(unsigned)nb, kStreamWarps * 32, 0, st>>>(
-            static_cast<const S *>(u), static_cast<const S *>(f), static_cast<const S *>(clean), h,
-            w, ld, out, partials, ticket);
+    // 2-element loads when every row start of u, f and clean is aligned to two elements
+    auto al = [&](const void *q) {
+        return q == nullptr || ((uintptr_t)q % (2 * sizeof(S)) == 0 && ld % 2 == 0);
+    };
+    const bool vec = al(u) && al(f) && al(clean);
+    const S *U = static_cast<const S *>(u), *F = static_cast<const S *>(f),
+            *C = static_cast<const S *>(clean);
+    const unsigned g = (unsigned)nb, b = kStreamWarps * 32;
+    if (bnd == BND_ZERO) {
+        if (vec) energy_kernel<S, BND_ZERO, true><<<g, b, 0, st>>>(U, F, C, h, w, ld, out, partials, ticket);
+        else energy_kernel<S, BND_ZERO, false><<<g, b, 0, st>>>(U, F, C, h, w, ld, out, partials, ticket);
+    } else {
+        if (vec) energy_kernel<S, BND_REPLICATE, true><<<g, b, 0, st>>>(U, F, C, h, w, ld, out, partials, ticket);
+        else energy_kernel<S, BND_REPLICATE, false><<<g, b, 0, st>>>(U, F, C, h, w, ld, out, partials, ticket);
+    }
     return cudaGetLastError();
 }
 

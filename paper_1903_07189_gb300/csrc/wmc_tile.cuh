@@ -136,16 +136,17 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// Poll the barrier's phase; give up after `limit_ns` (returns false).
+// Wait for the barrier's phase; give up after `limit_ns` (returns false).  Each try_wait may
+// suspend the thread in hardware for up to 1 ms, so the loop spins very little.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, uint64_t limit_ns) {
     const uint64_t t0 = global_timer_ns();
     for (;;) {
         uint32_t done;
         asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;"
             " selp.u32 %0, 1, 0, p; }"
             : "=r"(done)
-            : "r"(bar), "r"(phase)
+            : "r"(bar), "r"(phase), "r"(1000000u)
             : "memory");
         if (done) return true;
         if (global_timer_ns() - t0 > limit_ns) return false;
@@ -314,11 +315,11 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
     const int tid = threadIdx.x;
     const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
 
-    // ---- issue the load of the window of U^t
+    // ---- issue the load of the window of U^t (thread 0 alone owns the barrier: it initialises
+    // it, issues the copy and later waits for it, so the other threads never poll it)
     if (use_tma) {
-        if (tid == 0) mbar_init(smem_u32(&bar), 1);
-        __syncthreads();
         if (tid == 0) {
+            mbar_init(smem_u32(&bar), 1);
             void *dst = (sizeof(S) == 4) ? static_cast<void *>(buf0)
                                          : static_cast<void *>(buf1 + BUF);  // staging
             mbar_expect_tx(smem_u32(&bar), (uint32_t)(LW * LH * sizeof(S)));
@@ -370,9 +371,10 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
         }
     }
 
-    // ---- wait for the window
+    // ---- wait for the window: thread 0 waits on the barrier (its completion makes the copied
+    // data visible to it), then the CTA barrier orders everyone else's reads after that
     if (use_tma) {
-        const bool ok = mbar_wait_bounded(smem_u32(&bar), 0, kWaitLimitNs);
+        const bool ok = (tid != 0) || mbar_wait_bounded(smem_u32(&bar), 0, kWaitLimitNs);
         if (__syncthreads_or(!ok)) {
             if (tid == 0 && p.status) atomicOr(p.status, 1u);
             return;
