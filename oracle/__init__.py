@@ -63,6 +63,7 @@ def _load():
             lib.oracle_energies.argtypes = [_dp, _dp, _dp, i32, i32, i64, ctypes.c_int, _dp]
             lib.oracle_wmc_l1_primal_dual.argtypes = [_dp, _dp, _dp, _dp, i32, i32, i64, d, d, d, i32,
                                                       ctypes.c_int]
+            lib.oracle_unrolled_grad.argtypes = [_dp, _dp, i32, i32, d, d, i32, ctypes.c_int, _dp, _dp, _dp]
             lib.oracle_wmc_eval_points.argtypes = [_dp, i32, i32, i64, ctypes.c_int, _ip, _ip, i64, _dp,
                                                    _dp]
             lib.oracle_wmc_step_points.argtypes = [_dp, _dp, i32, i32, i64, d, d, d, ctypes.c_int, _ip,
@@ -225,3 +226,25 @@ def step_points(u, f, lam: float, step: float, ys, xs, boundary="replicate", mu:
     if rc:
         raise ValueError(f"oracle_wmc_step_points failed ({rc})")
     return (out, cand) if candidates else out
+
+
+def unrolled_grad(f, clean, lam: float, step: float, K: int, boundary="replicate"):
+    """Loss = mean((U^K - clean)^2) of K unrolled denoising steps from U^0 = f, and its gradient
+    (dloss/dlambda, dloss/df) with each step's selection held fixed.  Returns (loss, dlam, df)."""
+    f = _f64(f)
+    clean = _f64(clean)
+    h, w = f.shape
+    loss = ctypes.c_double()
+    dl = ctypes.c_double()
+    df = np.zeros((h, w))
+    rc = _load().oracle_unrolled_grad(_ptr(f), _ptr(clean), h, w, float(lam), float(step), int(K),
+                                      _bnd(boundary), ctypes.byref(loss), ctypes.byref(dl), _ptr(df))
+    if rc:
+        raise ValueError(f"oracle_unrolled_grad failed ({rc})")
+    return loss.value, dl.value, df
+
+
+def unrolled_loss(f, clean, lam: float, step: float, K: int, boundary="replicate") -> float:
+    """Forward only: mean((U^K - clean)^2)."""
+    u = denoise(f, lam, step, K, boundary)
+    return float(np.mean((u - _f64(clean)) ** 2))

@@ -321,3 +321,86 @@ int oracle_wmc_step_points(const double *f, const double *u, int32_t h, int32_t 
     }
     return 0;
 }
+
+/*
+ * Unrolled L2 denoising and its gradient.  U^0 = f and, for t < K (Sec. V-B with A = I),
+ *   U^{t+1} = U^t + step (lambda H^w(U^t) - (U^t - f));   loss = (1/N) sum_p (U^K(p) - clean(p))^2.
+ * H^w is piecewise linear in U: where the selection m(p) of Eq. act is fixed, H^w(U)(p) is the
+ * correlation of U with h_{m(p)} at p.  The gradient takes that piece (a subgradient where m
+ * switches), i.e. the chain rule through each step with m(p) held at its forward value:
+ *   g^K = dloss/dU^K = 2 (U^K - clean) / N
+ *   g^t = (1 - step) g^{t+1} + step lambda sum_p g^{t+1}(p) dH^w(U^t)(p)/dU^t
+ *   dloss/dlambda = step sum_t sum_p g^{t+1}(p) H^w(U^t)(p)
+ *   dloss/df      = step sum_t g^{t+1} + g^0
+ * where dH^w(p)/dU(q) is the weight of h_{m(p)} on the tap that reads q; under REPLICATE the
+ * taps outside the image read the clamped pixel and carry their weight to it, under ZERO they
+ * read nothing.  Dense h x w arrays (pitch w).  Returns 0, 1 on bad arguments, 2 on allocation
+ * failure.
+ */
+int oracle_unrolled_grad(const double *f, const double *clean, int32_t h, int32_t w, double lambda,
+                         double step, int32_t K, int bnd, double *loss, double *grad_lambda,
+                         double *grad_f) {
+    if (h <= 0 || w <= 0 || K < 0 || !f || !clean) return 1;
+    const size_t n = (size_t)h * (size_t)w;
+    double *U = (double *)malloc((size_t)(K + 1) * n * sizeof(double));
+    double *Hs = (double *)malloc((size_t)(K > 0 ? K : 1) * n * sizeof(double));
+    uint8_t *Ms = (uint8_t *)malloc((size_t)(K > 0 ? K : 1) * n);
+    double *g = (double *)malloc(n * sizeof(double));
+    double *gn = (double *)malloc(n * sizeof(double));
+    if (!U || !Hs || !Ms || !g || !gn) {
+        free(U); free(Hs); free(Ms); free(g); free(gn);
+        return 2;
+    }
+    memcpy(U, f, n * sizeof(double));
+    for (int32_t t = 0; t < K; ++t) {
+        const double *Ut = U + (size_t)t * n;
+        double *Un = U + (size_t)(t + 1) * n;
+        for (int32_t y = 0; y < h; ++y)
+            for (int32_t x = 0; x < w; ++x) {
+                double d[8];
+                distances(Ut, h, w, w, y, x, bnd, d);
+                const int m = select_min(d);
+                const size_t p = (size_t)y * w + x;
+                Hs[(size_t)t * n + p] = d[m];
+                Ms[(size_t)t * n + p] = (uint8_t)m;
+                Un[p] = Ut[p] + step * (lambda * d[m] - (Ut[p] - f[p]));
+            }
+    }
+    const double *UK = U + (size_t)K * n;
+    double l = 0.0;
+    for (size_t p = 0; p < n; ++p) {
+        const double r = UK[p] - clean[p];
+        l += r * r;
+        g[p] = 2.0 * r / (double)n;
+    }
+    *loss = l / (double)n;
+    double gl = 0.0;
+    for (size_t p = 0; p < n; ++p) grad_f[p] = 0.0;
+    for (int32_t t = K - 1; t >= 0; --t) {
+        for (size_t p = 0; p < n; ++p) {
+            gl += step * g[p] * Hs[(size_t)t * n + p];
+            grad_f[p] += step * g[p];
+            gn[p] = (1.0 - step) * g[p];
+        }
+        for (int32_t y = 0; y < h; ++y)
+            for (int32_t x = 0; x < w; ++x) {
+                const size_t p = (size_t)y * w + x;
+                const int m = Ms[(size_t)t * n + p];
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) {
+                        int qy = y + r - 1, qx = x + c - 1;
+                        if (qy < 0 || qy >= h || qx < 0 || qx >= w) {
+                            if (bnd == ORACLE_BND_ZERO) continue;
+                            qy = qy < 0 ? 0 : (qy >= h ? h - 1 : qy);
+                            qx = qx < 0 ? 0 : (qx >= w ? w - 1 : qx);
+                        }
+                        gn[(size_t)qy * w + qx] += step * lambda * (H12[m][r][c] / 12.0) * g[p];
+                    }
+            }
+        double *tmp = g; g = gn; gn = tmp;
+    }
+    for (size_t p = 0; p < n; ++p) grad_f[p] += g[p];
+    *grad_lambda = gl;
+    free(U); free(Hs); free(Ms); free(g); free(gn);
+    return 0;
+}

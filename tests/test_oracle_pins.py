@@ -388,3 +388,48 @@ def test_round_bf16_ties_and_carries():
 def test_round_f32_matches_cast():
     vals = np.random.default_rng(12).normal(size=1000)
     np.testing.assert_array_equal(oracle.round_storage(vals, "f32"), vals.astype(np.float32).astype(np.float64))
+
+
+# ------------------------------------------------------ unrolled denoising and its gradient
+def test_unrolled_grad_lambda_zero_closed_form():
+    """lambda = 0: U^t = f for every t, so loss = mean((f - clean)^2), dloss/df = 2 (f - clean)/N
+    and dloss/dlambda = step sum_t (1-step)^(K-1-t) sum_p g^K H^w(f) = (1 - (1-step)^K) sum_p g^K H^w(f)."""
+    f, clean = synth.make_image(12, 15, seed=40, sigma=0.1, return_clean=True)
+    f, clean = f.astype(np.float64), clean.astype(np.float64)
+    step, K = 0.3, 9
+    loss, dl, df = oracle.unrolled_grad(f, clean, 0.0, step, K)
+    gK = 2 * (f - clean) / f.size
+    assert loss == pytest.approx(np.mean((f - clean) ** 2), rel=1e-14)
+    np.testing.assert_allclose(df, gK, rtol=0, atol=1e-15)
+    want = (1 - (1 - step) ** K) * np.sum(gK * oracle.wmc_eval(f))
+    assert dl == pytest.approx(want, rel=1e-12)
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_unrolled_grad_matches_finite_differences(bnd):
+    """Central differences of the plain forward (oracle.denoise, a separate code path) against
+    the chain-rule gradient, for lambda and for f at a few pixels (steps too small to switch a
+    selection)."""
+    f, clean = synth.make_image(10, 13, seed=41, sigma=0.1, return_clean=True)
+    f, clean = f.astype(np.float64), clean.astype(np.float64)
+    lam, step, K = 1.3, 0.2, 7
+    loss, dl, df = oracle.unrolled_grad(f, clean, lam, step, K, bnd)
+    assert loss == pytest.approx(oracle.unrolled_loss(f, clean, lam, step, K, bnd), rel=1e-13)
+    eps = 1e-6
+    fd = (oracle.unrolled_loss(f, clean, lam + eps, step, K, bnd)
+          - oracle.unrolled_loss(f, clean, lam - eps, step, K, bnd)) / (2 * eps)
+    assert dl == pytest.approx(fd, rel=1e-6, abs=1e-12)
+    for (y, x) in [(0, 0), (4, 6), (9, 12), (5, 0), (0, 7)]:
+        fp, fm = f.copy(), f.copy()
+        fp[y, x] += eps
+        fm[y, x] -= eps
+        fdf = (oracle.unrolled_loss(fp, clean, lam, step, K, bnd)
+               - oracle.unrolled_loss(fm, clean, lam, step, K, bnd)) / (2 * eps)
+        assert df[y, x] == pytest.approx(fdf, rel=1e-5, abs=1e-11), (y, x)
+
+
+def test_unrolled_grad_zero_steps():
+    f, clean = synth.make_image(6, 7, seed=42, return_clean=True)
+    loss, dl, df = oracle.unrolled_grad(f, clean, 1.0, 0.25, 0)
+    assert dl == 0.0
+    np.testing.assert_allclose(df, 2 * (f.astype(np.float64) - clean) / f.size, atol=1e-16)
