@@ -63,6 +63,7 @@ def _load():
             lib.oracle_energies.argtypes = [_dp, _dp, _dp, i32, i32, i64, ctypes.c_int, _dp]
             lib.oracle_wmc_l1_primal_dual.argtypes = [_dp, _dp, _dp, _dp, i32, i32, i64, d, d, d, i32,
                                                       ctypes.c_int]
+            lib.oracle_energy_grad.argtypes = [_dp, i32, i32, ctypes.c_int, _dp]
             lib.oracle_unrolled_grad.argtypes = [_dp, _dp, i32, i32, d, d, i32, ctypes.c_int, _dp, _dp, _dp]
             lib.oracle_wmc_eval_points.argtypes = [_dp, i32, i32, i64, ctypes.c_int, _ip, _ip, i64, _dp,
                                                    _dp]
@@ -248,3 +249,14 @@ def unrolled_loss(f, clean, lam: float, step: float, K: int, boundary="replicate
     """Forward only: mean((U^K - clean)^2)."""
     u = denoise(f, lam, step, K, boundary)
     return float(np.mean((u - _f64(clean)) ** 2))
+
+
+def energy_grad(u, boundary="replicate"):
+    """d(sum_p |H^w(U)(p)|)/dU with each pixel's selection held fixed (sign(0) = 0)."""
+    u = _f64(u)
+    h, w = u.shape
+    g = np.zeros((h, w))
+    rc = _load().oracle_energy_grad(_ptr(u), h, w, _bnd(boundary), _ptr(g))
+    if rc:
+        raise ValueError(f"oracle_energy_grad failed ({rc})")
+    return g

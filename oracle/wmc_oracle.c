@@ -404,3 +404,32 @@ int oracle_unrolled_grad(const double *f, const double *clean, int32_t h, int32_
     free(U); free(Hs); free(Ms); free(g); free(gn);
     return 0;
 }
+
+/*
+ * Gradient of the WMC regulariser E = sum_p |H^w(U)(p)| (Eq. wmcr, q = 1) with each pixel's
+ * selection held fixed: dE/dU(q) = sum_p sign(H^w(p)) dH^w(p)/dU(q), the weight of h_{m(p)} on
+ * the tap that reads q (folded onto the clamped pixel under REPLICATE, dropped under ZERO);
+ * sign(0) = 0.  grad: dense h x w (pitch w).  Returns 0 or 1 on bad sizes.
+ */
+int oracle_energy_grad(const double *u, int32_t h, int32_t w, int bnd, double *grad) {
+    if (h <= 0 || w <= 0 || !u || !grad) return 1;
+    for (size_t p = 0; p < (size_t)h * w; ++p) grad[p] = 0.0;
+    for (int32_t y = 0; y < h; ++y)
+        for (int32_t x = 0; x < w; ++x) {
+            double d[8];
+            distances(u, h, w, w, y, x, bnd, d);
+            const int m = select_min(d);
+            const double s = d[m] > 0 ? 1.0 : (d[m] < 0 ? -1.0 : 0.0);
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) {
+                    int qy = y + r - 1, qx = x + c - 1;
+                    if (qy < 0 || qy >= h || qx < 0 || qx >= w) {
+                        if (bnd == ORACLE_BND_ZERO) continue;
+                        qy = qy < 0 ? 0 : (qy >= h ? h - 1 : qy);
+                        qx = qx < 0 ? 0 : (qx >= w ? w - 1 : qx);
+                    }
+                    grad[(size_t)qy * w + qx] += s * (H12[m][r][c] / 12.0);
+                }
+        }
+    return 0;
+}

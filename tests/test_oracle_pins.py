@@ -433,3 +433,31 @@ def test_unrolled_grad_zero_steps():
     loss, dl, df = oracle.unrolled_grad(f, clean, 1.0, 0.25, 0)
     assert dl == 0.0
     np.testing.assert_allclose(df, 2 * (f.astype(np.float64) - clean) / f.size, atol=1e-16)
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_energy_grad_matches_finite_differences(bnd):
+    u = synth.make_image(9, 11, seed=43, sigma=0.1).astype(np.float64)
+    g = oracle.energy_grad(u, bnd)
+    eps = 1e-7
+    for (y, x) in [(0, 0), (4, 5), (8, 10), (0, 5), (3, 0)]:
+        up, um = u.copy(), u.copy()
+        up[y, x] += eps
+        um[y, x] -= eps
+        fd = (oracle.energies(up, boundary=bnd)[0] - oracle.energies(um, boundary=bnd)[0]) / (2 * eps)
+        assert g[y, x] == pytest.approx(fd, rel=1e-5, abs=1e-8), (y, x)
+
+
+def test_energy_grad_impulse_by_hand():
+    """A unit impulse: only the impulse pixel has H^w != 0 (-1, every kernel); its selected
+    kernel is h3 (first in the Appendix order), so dE/dU = -h3 centred on the impulse:
+    +1 at the centre, -1/6 at N, NE, S, SE and -1/3 at E."""
+    u = np.zeros((5, 5))
+    u[2, 2] = 1
+    g = oracle.energy_grad(u)
+    want = np.zeros((5, 5))
+    want[2, 2] = 1.0
+    for (y, x) in [(1, 2), (1, 3), (3, 2), (3, 3)]:
+        want[y, x] = -1 / 6
+    want[2, 3] = -1 / 3
+    np.testing.assert_allclose(g, want, atol=1e-15)
