@@ -109,11 +109,23 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
     __syncthreads();
     if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (is_last && threadIdx.x < 3) {
-        __threadfence();
+    if (!is_last) return;
+    // Last CTA: thread i sums partials i, i + 256, ... in order, then a fixed shuffle tree and
+    // the 8 warp results in order -- the same order on every run.
+    __threadfence();
+    double a[3] = {0.0, 0.0, 0.0};
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] += __ldcg(partials + (int64_t)b * 3 + k);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double t = warp_sum(a[k]);
+        if (lane == 0) red[k][warp] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
         double t = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b)
-            t += *((volatile double *)partials + (int64_t)b * 3 + threadIdx.x);
+        for (int i = 0; i < kStreamWarps; ++i) t += red[threadIdx.x][i];
         out[threadIdx.x] = t;
     }
 }

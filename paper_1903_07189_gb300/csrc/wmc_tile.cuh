@@ -58,6 +58,10 @@ constexpr int kRY = 8;     // rows per thread
 constexpr int kTileWX = 2; // warps across (64 columns each)
 constexpr int kTileWY = kCH / kRY;  // warps down
 constexpr int kTileThreadsV2 = 32 * kTileWX * kTileWY;  // 512
+#ifndef WMC_TILE_MIN_BLOCKS
+#define WMC_TILE_MIN_BLOCKS 2  // CTAs per SM the register allocation must allow (1 CTA/SM with
+                               // 82 registers measured 20% slower at 4096^2)
+#endif
 
 template <typename S> struct Geom {
     static constexpr int A = 16 / (int)sizeof(S);                 // TMA x alignment (elements)
@@ -259,7 +263,7 @@ __device__ __forceinline__ void refresh_ring(float *buf, int X0, int Y0, int h, 
 }
 
 template <int T, typename S, int BND, bool BATCH>
-__global__ void __launch_bounds__(kTileThreadsV2, 2)
+__global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
     tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const TileV2Params p) {
     using G = Geom<S>;
     constexpr int LW = G::LW, LH = G::LH, P = G::P, BUF = G::BUF;
