@@ -230,6 +230,56 @@ wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t
                                  int32_t iters, wmc_boundary_t bnd, void *workspace,
                                  size_t workspace_bytes, wmc_stream_t stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Reverse mode (training through the flow).  The paper uses H^w as a descent direction and
+ * leaves the gradient of its regulariser open (Sec. III after Eq. wmcr); H^w is piecewise linear
+ * in U, and on the piece picked by the selection of Eq. act it is the correlation of U with the
+ * selected kernel h_m (Sec. IV-B).  These calls differentiate with each pixel's selection held at
+ * its forward value (a subgradient where the selection switches).  FP32 only.
+ *
+ * Unrolled denoising of a stack of n equally sized images (image i at f + i*h*ld elements):
+ *   U^0 = f,  U^{t+1} = U^t + step*(lambda_i H^w(U^t) - (U^t - f))   t = 0..K-1
+ * (the Sec. V-B flow with A = I, Jacobi; bitwise the same values as wmc_denoise on each image).
+ *   lambda: DEVICE, n floats (one per image, read by the kernels, so it may change between
+ *   graph replays).  step: > 0, shared.  K >= 0 steps.  ckpt_every >= 1: the forward keeps
+ *   U^c, U^2c, ... in the workspace and the backward recomputes the steps between checkpoints
+ *   (memory ~ (K/c + c) images instead of K).
+ *   wmc_unrolled_workspace_size: device bytes for both calls (0 for invalid sizes).
+ *   wmc_unrolled_forward: u (device, n x h x ld) = U^K.  The workspace then holds the
+ *   checkpoints that wmc_unrolled_backward reads: pass the same workspace, f, lambda, step, K,
+ *   ckpt_every and sizes, with no other call on that workspace in between.
+ *   wmc_unrolled_backward: given grad_u = dL/dU^K (device, n x h x ld), writes
+ *   grad_f = dL/df (device, n x h x ld) and grad_lambda = dL/dlambda (device, n floats).
+ *   The lambda sums run in FP64 in a fixed order (reproducible).
+ * Errors: WMC_ERR_INVALID_ARG (sizes, n outside 1..65535, K < 0, ckpt_every < 1, step <= 0,
+ *         NULL pointers), WMC_ERR_ALIAS (u overlaps f; grad_f overlaps grad_u or f; workspace
+ *         overlaps an image), WMC_ERR_WORKSPACE (too small or misaligned), WMC_ERR_CUDA.
+ */
+size_t wmc_unrolled_workspace_size(int32_t n, int32_t h, int32_t w, int64_t ld, int32_t K,
+                                   int32_t ckpt_every);
+
+wmc_status_t wmc_unrolled_forward(const float *f, const float *lambda, float step, int32_t K,
+                                  int32_t ckpt_every, int32_t n, int32_t h, int32_t w, int64_t ld,
+                                  wmc_boundary_t bnd, float *u, void *workspace,
+                                  size_t workspace_bytes, wmc_stream_t stream);
+
+wmc_status_t wmc_unrolled_backward(const float *f, const float *lambda, float step, int32_t K,
+                                   int32_t ckpt_every, int32_t n, int32_t h, int32_t w, int64_t ld,
+                                   wmc_boundary_t bnd, const float *grad_u, float *grad_f,
+                                   float *grad_lambda, void *workspace, size_t workspace_bytes,
+                                   wmc_stream_t stream);
+
+/*
+ * wmc_energy_grad: grad = d/dU sum_p |H^w(U)(p)| (the Eq. wmcr regulariser, q = 1), selection
+ * held fixed, sign(0) = 0.  u, grad: device FP32, h x w, pitch ld, must not overlap.
+ * workspace: device, >= wmc_energy_grad_workspace_size() bytes (one byte and one float per pixel).
+ */
+size_t wmc_energy_grad_workspace_size(int32_t h, int32_t w, int64_t ld);
+
+wmc_status_t wmc_energy_grad(const float *u, float *grad, int32_t h, int32_t w, int64_t ld,
+                             wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
+                             wmc_stream_t stream);
+
 /* ------------------------------------------------------------------------------------------ */
 const char *wmc_status_string(wmc_status_t status); /* static string, never NULL */
 const char *wmc_last_error(void); /* detail of the last failure on this thread ("" if none) */

@@ -402,6 +402,45 @@ __global__ void batch_copy_kernel(const wmc::BatchImage *images, const int4 *til
     }
 }
 
+// Unrolled-flow workspace: [status | checkpoints | segment/temporary stacks | g ping-pong |
+// selection bytes | dlambda partials].
+struct UnrolledLayout {
+    size_t slot, off_ckpt, off_seg, off_g, off_m, off_part, total;
+    int32_t ncp, nseg;
+    int64_t nb;
+};
+
+UnrolledLayout unrolled_layout(int32_t n, int32_t h, int32_t w, int64_t ld, int32_t K, int32_t c) {
+    UnrolledLayout L{};
+    const size_t px = (size_t)n * (size_t)h * (size_t)ld;
+    L.slot = round_up(px * sizeof(float), WMC_WORKSPACE_ALIGN);
+    L.ncp = K >= 1 ? (K - 1) / c : 0;
+    L.nseg = c - 1 > 2 ? c - 1 : 2;
+    L.nb = wmc::adjoint_select_blocks(h, w);
+    L.off_ckpt = kStatusBytes;
+    L.off_seg = L.off_ckpt + (size_t)L.ncp * L.slot;
+    L.off_g = L.off_seg + (size_t)L.nseg * L.slot;
+    L.off_m = L.off_g + 2 * L.slot;
+    L.off_part = L.off_m + round_up(px, WMC_WORKSPACE_ALIGN);
+    L.total = L.off_part + round_up((size_t)(K > 0 ? K : 1) * n * L.nb * sizeof(double), WMC_WORKSPACE_ALIGN);
+    return L;
+}
+
+wmc_status_t check_unrolled(const float *f, const float *lambda, float step, int32_t K, int32_t c,
+                            int32_t n, int32_t h, int32_t w, int64_t ld, wmc_boundary_t bnd) {
+    wmc_status_t s;
+    if ((s = check_enums(WMC_F32, bnd)) != WMC_OK) return s;
+    if ((s = check_image(h, w, ld, "image")) != WMC_OK) return s;
+    if (n < 1 || n > 65535) return fail(WMC_ERR_INVALID_ARG, "image count must be 1..65535 (got %d)", n);
+    if (h < 1 || w < 1) return fail(WMC_ERR_INVALID_ARG, "empty images");
+    if (K < 0) return fail(WMC_ERR_INVALID_ARG, "K must be >= 0 (got %d)", K);
+    if (c < 1) return fail(WMC_ERR_INVALID_ARG, "ckpt_every must be >= 1 (got %d)", c);
+    if (!std::isfinite(step) || step <= 0.0f)
+        return fail(WMC_ERR_INVALID_ARG, "step must be finite and > 0 (got %g)", step);
+    if (!f || !lambda) return fail(WMC_ERR_INVALID_ARG, "f or lambda is NULL");
+    return WMC_OK;
+}
+
 template <typename F>
 void for_each_launch(int iters, int T, F &&fn) {
     // launch k takes min(T, remaining) steps; the roles alternate so that the last launch writes
@@ -759,6 +798,159 @@ wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t
         wmc_batch_plan(imgs, n, dtype, bnd, nullptr, workspace, workspace_bytes, &plan, stream);
     if (s != WMC_OK) return s;
     return wmc_batch_run(&plan, iters, stream);
+}
+
+size_t wmc_unrolled_workspace_size(int32_t n, int32_t h, int32_t w, int64_t ld, int32_t K,
+                                   int32_t ckpt_every) {
+    if (n < 1 || h < 1 || w < 1 || ld < w || K < 0 || ckpt_every < 1) return 0;
+    return unrolled_layout(n, h, w, ld, K, ckpt_every).total;
+}
+
+wmc_status_t wmc_unrolled_forward(const float *f, const float *lambda, float step, int32_t K,
+                                  int32_t ckpt_every, int32_t n, int32_t h, int32_t w, int64_t ld,
+                                  wmc_boundary_t bnd, float *u, void *workspace,
+                                  size_t workspace_bytes, wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    wmc_status_t s = check_unrolled(f, lambda, step, K, ckpt_every, n, h, w, ld, bnd);
+    if (s != WMC_OK) return s;
+    if (!u) return fail(WMC_ERR_INVALID_ARG, "u is NULL");
+    const int64_t stride = (int64_t)h * ld;
+    const size_t nbytes = span_bytes(n * h, w, ld, 4);
+    if (overlap(u, nbytes, f, nbytes)) return fail(WMC_ERR_ALIAS, "u overlaps f");
+    const UnrolledLayout L = unrolled_layout(n, h, w, ld, K, ckpt_every);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed", L.total);
+    if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
+        return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    if (overlap(workspace, L.total, f, nbytes) || overlap(workspace, L.total, u, nbytes))
+        return fail(WMC_ERR_ALIAS, "workspace overlaps an image");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *base = static_cast<char *>(workspace);
+    cudaError_t e;
+    if (K == 0) {
+        e = cudaMemcpy2DAsync(u, ld * 4, f, ld * 4, w * 4, (size_t)n * h, cudaMemcpyDeviceToDevice, st);
+        return e == cudaSuccess ? WMC_OK : cuda_fail(e, "copy U^0");
+    }
+    const bool vec = pair_aligned(f, ld, 4) && pair_aligned(u, ld, 4);
+    float *tmp[2] = {reinterpret_cast<float *>(base + L.off_seg),
+                     reinterpret_cast<float *>(base + L.off_seg + L.slot)};
+    const float *src = f;
+    for (int32_t t = 0; t < K; ++t) {
+        float *dst;
+        if (t + 1 == K)
+            dst = u;
+        else if ((t + 1) % ckpt_every == 0)
+            dst = reinterpret_cast<float *>(base + L.off_ckpt + (size_t)((t + 1) / ckpt_every - 1) * L.slot);
+        else
+            dst = (src == tmp[0]) ? tmp[1] : tmp[0];
+        e = wmc::launch_stack_step((int)bnd, src, f, dst, lambda, step, n, h, w, ld, stride, vec, st);
+        if (e != cudaSuccess) return cuda_fail(e, "unrolled forward step");
+        src = dst;
+    }
+    return WMC_OK;
+}
+
+wmc_status_t wmc_unrolled_backward(const float *f, const float *lambda, float step, int32_t K,
+                                   int32_t ckpt_every, int32_t n, int32_t h, int32_t w, int64_t ld,
+                                   wmc_boundary_t bnd, const float *grad_u, float *grad_f,
+                                   float *grad_lambda, void *workspace, size_t workspace_bytes,
+                                   wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    wmc_status_t s = check_unrolled(f, lambda, step, K, ckpt_every, n, h, w, ld, bnd);
+    if (s != WMC_OK) return s;
+    if (!grad_u || !grad_f || !grad_lambda)
+        return fail(WMC_ERR_INVALID_ARG, "grad_u, grad_f or grad_lambda is NULL");
+    const int64_t stride = (int64_t)h * ld;
+    const size_t nbytes = span_bytes(n * h, w, ld, 4);
+    if (overlap(grad_f, nbytes, grad_u, nbytes) || overlap(grad_f, nbytes, f, nbytes))
+        return fail(WMC_ERR_ALIAS, "grad_f overlaps grad_u or f");
+    const UnrolledLayout L = unrolled_layout(n, h, w, ld, K, ckpt_every);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed", L.total);
+    if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
+        return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (K == 0) {
+        e = cudaMemcpy2DAsync(grad_f, ld * 4, grad_u, ld * 4, w * 4, (size_t)n * h,
+                              cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(grad_lambda, 0, (size_t)n * sizeof(float), st);
+        return e == cudaSuccess ? WMC_OK : cuda_fail(e, "K = 0 backward");
+    }
+    char *base = static_cast<char *>(workspace);
+    const bool vec = pair_aligned(f, ld, 4);
+    auto ckpt = [&](int i) { return reinterpret_cast<float *>(base + L.off_ckpt + (size_t)i * L.slot); };
+    auto seg = [&](int i) { return reinterpret_cast<float *>(base + L.off_seg + (size_t)i * L.slot); };
+    float *gbuf[2] = {reinterpret_cast<float *>(base + L.off_g),
+                      reinterpret_cast<float *>(base + L.off_g + L.slot)};
+    uint8_t *msel = reinterpret_cast<uint8_t *>(base + L.off_m);
+    double *part = reinterpret_cast<double *>(base + L.off_part);
+    const float *g_in = grad_u;
+    int gi = 0;
+    const int c = ckpt_every;
+    const int nsegs = (K + c - 1) / c;
+    for (int sgi = nsegs - 1; sgi >= 0; --sgi) {
+        const int t0 = sgi * c, t1 = (t0 + c < K) ? t0 + c : K;
+        const float *start = (sgi == 0) ? f : ckpt(sgi - 1);
+        // recompute U^{t0+1} .. U^{t1-1} of this segment
+        const float *prev = start;
+        for (int j = 1; j < t1 - t0; ++j) {
+            e = wmc::launch_stack_step((int)bnd, prev, f, seg(j - 1), lambda, step, n, h, w, ld, stride,
+                                       vec, st);
+            if (e != cudaSuccess) return cuda_fail(e, "recompute step");
+            prev = seg(j - 1);
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            const float *Ut = (t == t0) ? start : seg(t - t0 - 1);
+            e = wmc::launch_adjoint_select((int)bnd, Ut, g_in, msel, nullptr, part + (size_t)t * n * L.nb,
+                                           n, h, w, ld, stride, st);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint select");
+            float *g_out = gbuf[gi];
+            e = wmc::launch_adjoint_gather((int)bnd, g_in, msel, g_out, grad_f, lambda, step,
+                                           1.0f - step, 0.0f, t == K - 1, t == 0, n, h, w, ld,
+                                           stride, st);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint gather");
+            g_in = g_out;
+            gi ^= 1;
+        }
+    }
+    e = wmc::launch_lambda_grad(part, K, n, L.nb, step, grad_lambda, st);
+    if (e != cudaSuccess) return cuda_fail(e, "dlambda reduction");
+    return WMC_OK;
+}
+
+size_t wmc_energy_grad_workspace_size(int32_t h, int32_t w, int64_t ld) {
+    if (h < 1 || w < 1 || ld < w) return 0;
+    const size_t px = (size_t)h * (size_t)ld;
+    return round_up(px, WMC_WORKSPACE_ALIGN) + round_up(px * sizeof(float), WMC_WORKSPACE_ALIGN);
+}
+
+wmc_status_t wmc_energy_grad(const float *u, float *grad, int32_t h, int32_t w, int64_t ld,
+                             wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
+                             wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    wmc_status_t s;
+    if ((s = check_enums(WMC_F32, bnd)) != WMC_OK) return s;
+    if ((s = check_image(h, w, ld, "u")) != WMC_OK) return s;
+    if (h == 0 || w == 0) return WMC_OK;
+    if (!u || !grad) return fail(WMC_ERR_INVALID_ARG, "NULL image pointer");
+    const size_t nbytes = span_bytes(h, w, ld, 4);
+    if (overlap(u, nbytes, grad, nbytes)) return fail(WMC_ERR_ALIAS, "grad overlaps u");
+    const size_t need = wmc_energy_grad_workspace_size(h, w, ld);
+    if (!workspace || workspace_bytes < need)
+        return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed", need);
+    if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
+        return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    uint8_t *msel = static_cast<uint8_t *>(workspace);
+    float *sgn = reinterpret_cast<float *>(static_cast<char *>(workspace) +
+                                           round_up((size_t)h * ld, WMC_WORKSPACE_ALIGN));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = wmc::launch_adjoint_select((int)bnd, u, nullptr, msel, sgn, nullptr, 1, h, w, ld,
+                                               (int64_t)h * ld, st);
+    if (e == cudaSuccess)
+        e = wmc::launch_adjoint_gather((int)bnd, sgn, msel, grad, nullptr, nullptr, 0.0f, 0.0f,
+                                       1.0f / 12.0f, 0, 0, 1, h, w, ld, (int64_t)h * ld, st);
+    return e == cudaSuccess ? WMC_OK : cuda_fail(e, "energy gradient");
 }
 
 size_t wmc_denoise_noalloc_max_bytes(void) { return kNoAllocScratchBytes; }

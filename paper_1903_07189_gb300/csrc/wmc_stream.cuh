@@ -27,6 +27,11 @@ struct StreamParams {
     int64_t ldu, ldf, ldo;
     int32_t h, w;
     float c_keep, c_f, c_h;
+    // stacks (n images of h x w, image i at offset i * img_stride elements in u, f and out):
+    // blockIdx.y is the image; lambda comes from device memory and c_h = step * lambda / 12
+    int64_t img_stride;
+    const float *lam;
+    float step;
 };
 
 // Two adjacent elements of row `row` (already clamped or validated) starting at column x.
@@ -59,22 +64,28 @@ __device__ __forceinline__ int row_index(int y, int h, bool *ok) {
     return min(max(y, 0), h - 1);
 }
 
-template <typename S, int BND, int MODE, bool VEC>
+template <typename S, int BND, int MODE, bool VEC, bool STACK = false>
 __global__ void __launch_bounds__(kStreamWarps * 32, 3)
     stream_kernel(const StreamParams p) {
     constexpr int R = kStreamRY;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int w = p.w, h = p.h;
+    float c_h = p.c_h;
+    int64_t img_off = 0;
+    if (STACK) {
+        img_off = (int64_t)blockIdx.y * p.img_stride;
+        c_h = p.step * __ldg(p.lam + blockIdx.y) / 12.0f;  // as the host computes it
+    }
     // 1-D grid: block b covers row strip b / nbx and column block b % nbx (512 columns).
     const int nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
     const int by = (int)(blockIdx.x / nbx), bx = (int)(blockIdx.x - (unsigned)by * nbx);
     const int x = ((bx * kStreamWarps + warp) * 32 + lane) * 2;
     if ((x & ~63) >= w) return;  // whole warp right of the image (warp-uniform)
     const int y0 = by * R;
-    const S *__restrict__ u = static_cast<const S *>(p.u);
-    const S *__restrict__ f = static_cast<const S *>(p.f);
-    S *__restrict__ out = static_cast<S *>(p.out);
+    const S *__restrict__ u = static_cast<const S *>(p.u) + img_off;
+    const S *__restrict__ f = p.f ? static_cast<const S *>(p.f) + img_off : nullptr;
+    S *__restrict__ out = static_cast<S *>(p.out) + img_off;
 
     // ---- issue every load of the strip first: R + 2 rows of pairs, the two outer columns
     // (lanes 0 and 31 only) and the R rows of f
@@ -106,7 +117,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 3)
         if (lane == 0) lf[k] = el[k];
         if (lane == 31) rt[k] = er[k];
     }
-    const float2 ch = make_float2(p.c_h, p.c_h), ck = make_float2(p.c_keep, p.c_keep);
+    const float2 ch = make_float2(c_h, c_h), ck = make_float2(p.c_keep, p.c_keep);
     const float2 cf = make_float2(p.c_f, p.c_f);
 #pragma unroll
     for (int k = 0; k < R; ++k) {

@@ -66,6 +66,13 @@ SIGNATURES = {
                               ctypes.POINTER(BatchPlan), _vp]),
     "wmc_batch_run": (_i32, [ctypes.POINTER(BatchPlan), _i32, _vp]),
     "wmc_denoise_batched": (_i32, [ctypes.POINTER(Image), _i32, _i32, _i32, _i32, _vp, _sz, _vp]),
+    "wmc_unrolled_workspace_size": (_sz, [_i32, _i32, _i32, _i64, _i32, _i32]),
+    "wmc_unrolled_forward": (_i32, [_vp, _vp, _f32, _i32, _i32, _i32, _i32, _i32, _i64, _i32, _vp, _vp, _sz,
+                                    _vp]),
+    "wmc_unrolled_backward": (_i32, [_vp, _vp, _f32, _i32, _i32, _i32, _i32, _i32, _i64, _i32, _vp, _vp, _vp,
+                                     _vp, _sz, _vp]),
+    "wmc_energy_grad_workspace_size": (_sz, [_i32, _i32, _i64]),
+    "wmc_energy_grad": (_i32, [_vp, _vp, _i32, _i32, _i64, _i32, _vp, _sz, _vp]),
     "wmc_status_string": (ctypes.c_char_p, [_i32]),
     "wmc_last_error": (ctypes.c_char_p, []),
     "wmc_version": (_i32, []),
@@ -288,6 +295,112 @@ def denoise_batched(fs, lams, steps=None, iters: int = 100, boundary: str = "rep
                     steps_per_launch: int = 0):
     """Plan and run one batch; returns the output tensors."""
     return Batch(fs, lams, steps, outs, boundary, steps_per_launch).run(iters)
+
+
+def _stack(t: torch.Tensor, name: str):
+    """(ptr, n, h, w, ld) of an FP32 (n, h, w) CUDA tensor whose image i starts at i*h*ld."""
+    if not t.is_cuda or t.dtype != torch.float32 or t.dim() != 3:
+        raise ValueError(f"{name} must be a float32 CUDA tensor of shape (n, h, w)")
+    n, h, w = t.shape
+    ld = max(t.stride(1), w) if h > 1 else w
+    if t.stride(2) != 1 or (h > 1 and t.stride(1) < w) or (n > 1 and t.stride(0) != h * ld):
+        raise ValueError(f"{name}: rows must have unit stride and images a stride of h * ld")
+    return t.data_ptr(), n, h, w, ld
+
+
+def unrolled_workspace_size(n: int, h: int, w: int, K: int, ckpt_every: int, ld: int | None = None) -> int:
+    return load().wmc_unrolled_workspace_size(n, h, w, w if ld is None else ld, K, ckpt_every)
+
+
+def unrolled_forward(f: torch.Tensor, lam: torch.Tensor, step: float, K: int, ckpt_every: int = 7,
+                     boundary: str = "replicate", out: torch.Tensor | None = None,
+                     workspace: torch.Tensor | None = None):
+    """U^K of K denoising steps of each image of the (n, h, w) stack f, lambda per image (a CUDA
+    tensor of n floats).  Returns (U^K, workspace); the workspace holds the checkpoints that
+    unrolled_backward needs."""
+    pf, n, h, w, ld = _stack(f, "f")
+    if lam.dtype != torch.float32 or lam.numel() != n or not lam.is_cuda or not lam.is_contiguous():
+        raise ValueError("lam must be a contiguous float32 CUDA tensor with one value per image")
+    lib = load()
+    if out is None:
+        out = torch.empty_strided(f.shape, f.stride(), dtype=f.dtype, device=f.device)
+    po, n2, h2, w2, ld2 = _stack(out, "out")
+    if (n2, h2, w2, ld2) != (n, h, w, ld):
+        raise ValueError("out must match f in shape and pitch")
+    if workspace is None:
+        workspace = _workspace(lib.wmc_unrolled_workspace_size(n, h, w, ld, K, ckpt_every), f.device)
+    _check(lib.wmc_unrolled_forward(pf, lam.data_ptr(), float(step), int(K), int(ckpt_every), n, h, w, ld,
+                                    BOUNDARY[boundary], po, workspace.data_ptr(), workspace.numel(),
+                                    _stream(f.device)), "wmc_unrolled_forward")
+    return out, workspace
+
+
+def unrolled_backward(f: torch.Tensor, lam: torch.Tensor, step: float, K: int, grad_u: torch.Tensor,
+                      workspace: torch.Tensor, ckpt_every: int = 7, boundary: str = "replicate"):
+    """(dL/df, dL/dlambda) from dL/dU^K, reading the checkpoints unrolled_forward left in
+    `workspace` (selection held fixed)."""
+    pf, n, h, w, ld = _stack(f, "f")
+    grad_u = grad_u.contiguous() if f.is_contiguous() else grad_u
+    pg, n2, h2, w2, ld2 = _stack(grad_u, "grad_u")
+    if (n2, h2, w2, ld2) != (n, h, w, ld):
+        raise ValueError("grad_u must match f in shape and pitch")
+    grad_f = torch.empty_strided(f.shape, f.stride(), dtype=f.dtype, device=f.device)
+    grad_lam = torch.empty(n, dtype=torch.float32, device=f.device)
+    _check(load().wmc_unrolled_backward(pf, lam.data_ptr(), float(step), int(K), int(ckpt_every), n, h, w,
+                                        ld, BOUNDARY[boundary], pg, grad_f.data_ptr(), grad_lam.data_ptr(),
+                                        workspace.data_ptr(), workspace.numel(), _stream(f.device)),
+           "wmc_unrolled_backward")
+    return grad_f, grad_lam
+
+
+class UnrolledDenoise(torch.autograd.Function):
+    """Autograd node of K unrolled denoising steps: apply(f, lam, step, K, ckpt_every, boundary).
+
+    f: (n, h, w) float32 CUDA stack; lam: (n,) float32 CUDA tensor.  Gradients flow to f and lam;
+    the backward recomputes the steps between checkpoints (every `ckpt_every` steps)."""
+
+    @staticmethod
+    def forward(ctx, f, lam, step, K, ckpt_every=7, boundary="replicate"):
+        f = f.contiguous()
+        lam = lam.contiguous()
+        u, ws = unrolled_forward(f, lam, step, K, ckpt_every, boundary)
+        ctx.save_for_backward(f, lam)
+        ctx.ws, ctx.step, ctx.K, ctx.c, ctx.bnd = ws, step, K, ckpt_every, boundary
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        f, lam = ctx.saved_tensors
+        gf, gl = unrolled_backward(f, lam, ctx.step, ctx.K, grad_u.contiguous(), ctx.ws, ctx.c, ctx.bnd)
+        return gf, gl, None, None, None, None
+
+
+def unrolled_denoise(f: torch.Tensor, lam: torch.Tensor, step: float, K: int, ckpt_every: int = 7,
+                     boundary: str = "replicate") -> torch.Tensor:
+    """Differentiable K-step denoising of an (n, h, w) stack (or one (h, w) image)."""
+    squeeze = f.dim() == 2
+    if squeeze:
+        f = f.unsqueeze(0)
+    lam = lam.reshape(-1)
+    u = UnrolledDenoise.apply(f, lam, step, K, ckpt_every, boundary)
+    return u[0] if squeeze else u
+
+
+def energy_grad(u: torch.Tensor, boundary: str = "replicate", out: torch.Tensor | None = None) -> torch.Tensor:
+    """d/dU sum_p |H^w(U)(p)| (selection held fixed, sign(0) = 0), FP32."""
+    p, h, w, ld = _img(u, "u")
+    if u.dtype != torch.float32:
+        raise ValueError("energy_grad supports float32 only")
+    if out is None:
+        out = torch.empty_strided(u.shape, u.stride(), dtype=u.dtype, device=u.device)
+    po, h2, w2, ld2 = _img(out, "out")
+    if (h2, w2, ld2) != (h, w, ld):
+        raise ValueError("out must match u in shape and pitch")
+    lib = load()
+    ws = _workspace(lib.wmc_energy_grad_workspace_size(h, w, ld), u.device)
+    _check(lib.wmc_energy_grad(p, po, h, w, ld, BOUNDARY[boundary], ws.data_ptr(), ws.numel(),
+                               _stream(u.device)), "wmc_energy_grad")
+    return out
 
 
 def psnr(sse: float, n: int, peak: float = 1.0) -> float:

@@ -148,3 +148,45 @@ def test_batch_validation(lib):
     assert need > 0 and need % 256 == 0
     assert lib.wmc_batch_workspace_size(_images([(A, B, 8, 8, 7, 1.0, 0.25)]), 1, 0, None) == 0
     assert lib.wmc_batch_run(ctypes.byref(wmc.BatchPlan()), 5, None) == INVALID  # not planned
+
+
+def test_unrolled_validation(lib):
+    f = ctypes.c_void_p(0x100000)
+    lam = ctypes.c_void_p(0x200000)
+    u = ctypes.c_void_p(0x300000)
+    ws = ctypes.c_void_p(0x10000000)
+    big = 1 << 40
+    assert lib.wmc_unrolled_workspace_size(0, 8, 8, 8, 4, 2) == 0
+    assert lib.wmc_unrolled_workspace_size(1, 8, 8, 4, 4, 2) == 0
+    assert lib.wmc_unrolled_workspace_size(1, 8, 8, 8, 4, 0) == 0
+    assert lib.wmc_unrolled_workspace_size(2, 8, 8, 8, 9, 3) > lib.wmc_unrolled_workspace_size(2, 8, 8, 8, 3, 3)
+    fwd = lambda *a: lib.wmc_unrolled_forward(*a)
+    # n, K, ckpt_every, step, NULL pointers
+    assert fwd(f, lam, 0.25, 4, 2, 0, 8, 8, 8, 0, u, ws, big, None) == INVALID
+    assert fwd(f, lam, 0.25, -1, 2, 1, 8, 8, 8, 0, u, ws, big, None) == INVALID
+    assert fwd(f, lam, 0.25, 4, 0, 1, 8, 8, 8, 0, u, ws, big, None) == INVALID
+    assert fwd(f, lam, 0.0, 4, 2, 1, 8, 8, 8, 0, u, ws, big, None) == INVALID
+    assert fwd(f, lam, float("nan"), 4, 2, 1, 8, 8, 8, 0, u, ws, big, None) == INVALID
+    assert fwd(None, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, u, ws, big, None) == INVALID
+    assert fwd(f, None, 0.25, 4, 2, 1, 8, 8, 8, 0, u, ws, big, None) == INVALID
+    assert fwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 7, u, ws, big, None) == INVALID  # boundary
+    assert fwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, f, ws, big, None) == ALIAS
+    assert fwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, u, ws, 16, None) == WORKSPACE
+    assert fwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, u, ctypes.c_void_p(0x10000010), big, None) == WORKSPACE
+    bwd = lib.wmc_unrolled_backward
+    assert bwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, u, None, lam, ws, big, None) == INVALID
+    assert bwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, u, u, lam, ws, big, None) == ALIAS
+    assert bwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, u, ctypes.c_void_p(0x400000), lam, ws, 16, None) == WORKSPACE
+
+
+def test_energy_grad_validation(lib):
+    u = ctypes.c_void_p(0x100000)
+    g = ctypes.c_void_p(0x300000)
+    ws = ctypes.c_void_p(0x10000000)
+    assert lib.wmc_energy_grad_workspace_size(8, 8, 4) == 0
+    need = lib.wmc_energy_grad_workspace_size(8, 8, 8)
+    assert need >= 8 * 8 * 5
+    assert lib.wmc_energy_grad(u, g, 8, 8, 4, 0, ws, need, None) == INVALID
+    assert lib.wmc_energy_grad(u, u, 8, 8, 8, 0, ws, need, None) == ALIAS
+    assert lib.wmc_energy_grad(u, g, 8, 8, 8, 0, ws, need - 1, None) == WORKSPACE
+    assert lib.wmc_energy_grad(None, g, 8, 8, 8, 0, ws, need, None) == INVALID
