@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--steps-per-launch", type=int, default=0)
     ap.add_argument("--iters", type=int, default=ITERS, help="override (profiling runs only)")
-    ap.add_argument("--workload", default="scale", choices=["scale", "precision", "batch"],
-                    help="scale: the headline 4096^2 run; precision / batch: the reduced-storage "
-                         "and uneven-batch measurements (one JSON line each, not the headline)")
+    ap.add_argument("--workload", default="scale", choices=["scale", "precision", "batch", "diff"],
+                    help="scale: the headline 4096^2 run; precision / batch / diff: the reduced-"
+                         "storage, uneven-batch and reverse-mode measurements (one JSON line "
+                         "each, not the headline)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -71,6 +72,28 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def replica_seed(rank: int) -> int:
+    """Input seed of a replica: rank 0 times the workload image (seed 1); other ranks get their
+    own image of the same recipe (replicas share nothing)."""
+    return 1 + 1000 * rank
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values (all-reduce MAX; the identity for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, slowest_ms: float) -> float:
+    """Whole-job throughput in G units/s: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (slowest_ms * 1e-3) / 1e9
 
 
 def peaks():
@@ -177,7 +200,7 @@ def run_gpu(args):
     from paper_1903_07189_gb300 import synth, wmc
     wmc.load()
 
-    u_host = synth.make_image(H, W, seed=1 + 1000 * rank, n_bumps=64, n_shapes=32, sigma=SIGMA)
+    u_host = synth.make_image(H, W, seed=replica_seed(rank), n_bumps=64, n_shapes=32, sigma=SIGMA)
     f = torch.from_numpy(u_host).to(dev)
     hw = torch.empty_like(f)
     out = torch.empty_like(f)
@@ -226,14 +249,9 @@ def run_gpu(args):
     clocks = clk.summary()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     den_ms = [a.elapsed_time(b) for a, b in zip(d0, d1)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    units = H * W * iters * args.steps * world
-    value = units / (total_ms * 1e-3) / 1e9
+    value = job_rate(H * W * iters * args.steps, world, total_ms)
 
     # dominant kernel: the flow kernel, n_launch launches per denoise call (T steps each)
     launch_ms = statistics.mean(den_ms) / n_launch
@@ -272,12 +290,8 @@ def run_gpu(args):
             wmc.denoise_host(fh, LAM, STEP, iters, out=oh, workspace=hws, device=dev)
             st.synchronize()
         barrier()
-        dt = (time.perf_counter() - t0) / ne
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": H * W * iters * world / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
+        dt = max_over_ranks((time.perf_counter() - t0) / ne, world, dev)
+        e2e = {"value": job_rate(H * W * iters, world, dt * 1e3), "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
                "d2h_bytes_per_step": H * W * 4, "call": "wmc_denoise_host (pinned host f in, U out)"}
 
     cpu = None
@@ -440,6 +454,73 @@ def run_batch(args):
     return 0
 
 
+def run_diff(args):
+    """Training through the unrolled flow: 32 images of 512 x 512 (seed 2000+i, 8 bumps + 4
+    shapes, sigma 0.05), one learnable lambda per image (init 1.0), K = 50 denoising steps with
+    step 0.25, checkpoints every 7 steps, loss = mean squared error of U^K against the clean
+    image.  Reports forward, backward and forward+backward pixel-steps/s (n*h*w*K per call), the
+    device memory the checkpoints save, and the loss over a few gradient steps on lambda."""
+    import torch
+    from paper_1903_07189_gb300 import synth, wmc
+    dev = torch.device("cuda", 0)
+    n, h, w, K, c, step = 32, 512, 512, 50, 7, 0.25
+    pairs = [synth.make_image(h, w, seed=2000 + i, n_bumps=8, n_shapes=4, sigma=0.05,
+                              return_clean=True) for i in range(n)]
+    f = torch.from_numpy(np.stack([p[0] for p in pairs]).astype(np.float32)).to(dev)
+    clean = torch.from_numpy(np.stack([p[1] for p in pairs]).astype(np.float32)).to(dev)
+    lam = torch.full((n,), 1.0, device=dev, requires_grad=True)
+
+    def fwd_bwd():
+        u = wmc.unrolled_denoise(f, lam, step, K, ckpt_every=c)
+        loss = ((u - clean) ** 2).mean()
+        lam.grad = None
+        loss.backward()
+        return loss
+
+    for _ in range(max(3, args.warmup)):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    reps = max(3, min(args.steps, 20))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.reset_peak_memory_stats(dev)
+    base_mem = torch.cuda.memory_allocated(dev)
+    for a, m, e in ev:
+        a.record()
+        u = wmc.unrolled_denoise(f, lam, step, K, ckpt_every=c)
+        loss = ((u - clean) ** 2).mean()
+        m.record()
+        lam.grad = None
+        loss.backward()
+        e.record()
+    torch.cuda.synchronize()
+    peak = torch.cuda.max_memory_allocated(dev) - base_mem
+    t_f = min(a.elapsed_time(m) for a, m, _ in ev)
+    t_b = min(m.elapsed_time(e) for _, m, e in ev)
+    t_fb = min(a.elapsed_time(e) for a, _, e in ev)
+    units = n * h * w * K
+    # a few Adam steps on lambda: the loss must go down
+    opt = torch.optim.Adam([lam], lr=0.1)
+    losses = []
+    for _ in range(5):
+        opt.zero_grad()
+        losses.append(float(fwd_bwd()))
+        opt.step()
+    line = {"workload": "diff", "metric": "gigapixel-steps/s of unrolled denoising, forward + backward",
+            "unit": "Gpix-step/s", "config": {
+                "images": n, "h": h, "w": w, "K": K, "ckpt_every": c, "step": step, "lambda_init": 1.0,
+                "loss": "MSE(U^K, clean)", "dtype": "f32", "inputs": "synthetic, seed 2000+i, 8 bumps + "
+                "4 shapes, sigma 0.05"},
+            "results": {"fwd_bwd": units / (t_fb * 1e-3) / 1e9, "fwd": units / (t_f * 1e-3) / 1e9,
+                        "bwd": units / (t_b * 1e-3) / 1e9,
+                        "ms": {"fwd": t_f, "bwd": t_b, "fwd_bwd": t_fb},
+                        "peak_extra_mib": peak / 2**20,
+                        "no_checkpoint_mib": n * h * w * 4 * (K + 1) / 2**20,
+                        "adam_losses": losses, "lambda_mean_after": float(lam.mean())}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -448,6 +529,8 @@ def main():
         return run_precision(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "diff":
+        return run_diff(args)
     return run_gpu(args)
 
 
