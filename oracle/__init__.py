@@ -61,7 +61,7 @@ def _load():
             lib.oracle_wmc_flow.argtypes = [_dp, _dp, _dp, i32, i32, i64, d, d, i32, ctypes.c_int, d,
                                             ctypes.c_int]
             lib.oracle_energies.argtypes = [_dp, _dp, _dp, i32, i32, i64, ctypes.c_int, _dp]
-            lib.oracle_wmc_l1_primal_dual.argtypes = [_dp, _dp, _dp, _dp, i32, i32, i64, d, d, d, i32,
+            lib.oracle_wmc_l1_primal_dual.argtypes = [_dp, _dp, _dp, _dp, _dp, i32, i32, i64, d, d, d, i32,
                                                       ctypes.c_int]
             lib.oracle_energy_grad.argtypes = [_dp, i32, i32, ctypes.c_int, _dp]
             lib.oracle_unrolled_grad.argtypes = [_dp, _dp, i32, i32, d, d, i32, ctypes.c_int, _dp, _dp, _dp]
@@ -179,14 +179,16 @@ def energies(u, f=None, clean=None, boundary="replicate"):
 
 
 def l1_primal_dual(f, lam: float, step: float, alpha: float, iters: int, boundary="replicate",
-                   u0=None):
-    """L1-fidelity primal-dual iteration of Sec. V-C; returns (U, d)."""
+                   u0=None, d0=None):
+    """L1-fidelity primal-dual iteration of Sec. V-C from (U^0, d^0) = (u0 or f, d0 or 0);
+    returns (U, d)."""
     f = _f64(f)
     h, w = f.shape
     u0_ = None if u0 is None else _f64(u0)
+    d0_ = None if d0 is None else _f64(d0)
     out = np.zeros((h, w))
     d = np.zeros((h, w))
-    rc = _load().oracle_wmc_l1_primal_dual(_ptr(f), _ptr(u0_), _ptr(out), _ptr(d), h, w, w,
+    rc = _load().oracle_wmc_l1_primal_dual(_ptr(f), _ptr(u0_), _ptr(d0_), _ptr(out), _ptr(d), h, w, w,
                                            float(lam), float(step), float(alpha), int(iters),
                                            _bnd(boundary))
     if rc:

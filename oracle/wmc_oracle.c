@@ -240,12 +240,14 @@ int oracle_energies(const double *u, const double *f, const double *clean, int32
 }
 
 /*
- * L1-fidelity primal-dual iteration of Sec. V-C with A = I, from U^0 = u0 (or f) and d^0 = 0:
+ * L1-fidelity primal-dual iteration of Sec. V-C with A = I, from U^0 = u0 (or f) and d^0 = d0
+ * (or 0):
  *   r = U^t - f + d^t;  d^{t+1} = clip(r, -alpha, alpha);
  *   U^{t+1} = U^t + step * (lambda * H^w(U^t) - (2 d^{t+1} - d^t) / alpha).
  * d_out (optional) receives d^iters.  Returns 0, 1 on bad arguments, 2 on allocation failure.
  */
-int oracle_wmc_l1_primal_dual(const double *f, const double *u0, double *u_out, double *d_out,
+int oracle_wmc_l1_primal_dual(const double *f, const double *u0, const double *d0, double *u_out,
+                              double *d_out,
                               int32_t h, int32_t w, int64_t ld, double lambda, double step,
                               double alpha, int32_t iters, int bnd) {
     if (check_dims(h, w, ld) || iters < 0 || !f || !(alpha > 0.0)) return 1;
@@ -261,7 +263,10 @@ int oracle_wmc_l1_primal_dual(const double *f, const double *u0, double *u_out, 
     }
     const double *src = u0 ? u0 : f;
     for (int32_t y = 0; y < h; ++y)
-        for (int32_t x = 0; x < w; ++x) U[(size_t)y * w + x] = src[(int64_t)y * ld + x];
+        for (int32_t x = 0; x < w; ++x) {
+            U[(size_t)y * w + x] = src[(int64_t)y * ld + x];
+            if (d0) D[(size_t)y * w + x] = d0[(int64_t)y * ld + x];
+        }
     for (int32_t t = 0; t < iters; ++t) {
         oracle_wmc_eval(U, Hw, h, w, w, w, bnd, NULL, NULL);
         for (int32_t y = 0; y < h; ++y)

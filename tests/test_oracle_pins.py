@@ -366,6 +366,26 @@ def test_primal_dual_constant_is_fixed():
     assert np.all(d == 0)
 
 
+def test_primal_dual_resume_is_exact():
+    """(U^n, d^n) carry the whole state: n + m iterations equal n, then m from (U^n, d^n)."""
+    f = synth.make_image(21, 17, seed=41, sigma=0.1, dtype=np.float64)
+    u7, d7 = oracle.l1_primal_dual(f, 1.5, 0.05, 0.08, 7)
+    u3, d3 = oracle.l1_primal_dual(f, 1.5, 0.05, 0.08, 3)
+    u7b, d7b = oracle.l1_primal_dual(f, 1.5, 0.05, 0.08, 4, u0=u3, d0=d3)
+    assert np.array_equal(u7, u7b) and np.array_equal(d7, d7b)
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_primal_dual_large_alpha_is_curvature_flow(bnd):
+    """alpha -> infinity: d stays tiny relative to alpha, the data term (2d^{t+1} - d^t)/alpha
+    vanishes, and one iteration is one mean-curvature-flow step U + step*lambda*H^w(U)
+    (Eq. MCF), which pins how lambda and H^w enter the update."""
+    f = synth.make_image(19, 23, seed=42, sigma=0.1, dtype=np.float64)
+    u0 = f + 0.3 * synth.make_image(19, 23, seed=43, sigma=0.05, dtype=np.float64)
+    u1, _ = oracle.l1_primal_dual(f, 1.7, 0.2, 1e12, 1, bnd, u0=u0)
+    np.testing.assert_allclose(u1, oracle.mcf(u0, 0.2 * 1.7, 1, bnd), rtol=0, atol=1e-10)
+
+
 # ------------------------------------------------------------------- storage emulation
 def test_round_f16_matches_numpy():
     rng = np.random.default_rng(11)
