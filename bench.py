@@ -48,6 +48,10 @@ BYTES_PER_PX_LAUNCH = 12  # read U, read f, write U (FP32): algorithmic bytes of
 FMA_OPS_PER_PX_ITER = 27
 SMS, FP32_LANES_PER_SM = 152, 128
 DEFAULT_T = 4
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one 4-step tile-kernel launch on
+# this image, from an ncu capture of a warm-L2 launch (67.2 MB read + 24.2 MB written); valid for
+# the default 4 steps per launch only.
+TILE_T4_DRAM_BYTES = 91.4e6
 
 
 def parse():
@@ -58,7 +62,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--steps-per-launch", type=int, default=0)
     ap.add_argument("--iters", type=int, default=ITERS, help="override (profiling runs only)")
-    ap.add_argument("--workload", default="scale", choices=["scale", "precision", "batch", "diff"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "precision", "batch", "diff", "l1"],
                     help="scale: the headline 4096^2 run; precision / batch / diff: the reduced-"
                          "storage, uneven-batch and reverse-mode measurements (one JSON line "
                          "each, not the headline)")
@@ -262,7 +266,8 @@ def run_gpu(args):
     fp32_achieved = FMA_OPS_PER_PX_ITER * H * W * T / (launch_ms * 1e-3) / 1e12
     if T > 1:
         roofline = {"bound": "alu", "achieved": fp32_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": fp32_achieved / fp32_peak, "traffic": None,
+                    "frac": fp32_achieved / fp32_peak,
+                    "traffic": TILE_T4_DRAM_BYTES if (T == 4 and iters == ITERS) else None,
                     "kernel": f"wmc::tile_v2_kernel<T={T}> (flow, {T} Jacobi steps per launch)",
                     "peak_kind": f"FP32 FMA pipe lane-operations (an FMA counts once): {SMS} SMs x {FP32_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz "
                                  "(unit counts and the sampled clock)",
@@ -454,6 +459,58 @@ def run_batch(args):
     return 0
 
 
+def run_l1(args):
+    """L1-fidelity primal-dual iteration (Sec. V-C, A = I) on the 4096^2 workload image: lambda 50,
+    step 0.01, alpha 0.05 (step/alpha inside the stable range of the (U, d) update), 200
+    iterations, one streaming launch per iteration.  Algorithmic bytes per pixel-iteration: read
+    U, f, d and write U, d (20 B in FP32)."""
+    import torch
+    from paper_1903_07189_gb300 import synth, wmc
+    dev = torch.device("cuda", 0)
+    iters = 200 if args.iters == ITERS else args.iters
+    lam, step, alpha = 50.0, 0.01, 0.05
+    f_np, clean_np = synth.scale_image(SIGMA, return_clean=True)
+    f = torch.from_numpy(f_np).to(dev)
+    clean = torch.from_numpy(clean_np).to(dev)
+    out = torch.empty_like(f)
+    d = torch.empty_like(f)
+    ws = torch.empty(wmc.load().wmc_denoise_l1_workspace_size(H, W, W), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def run():
+        d.zero_()
+        wmc.denoise_l1(f, lam, step, alpha, iters, d=d, out=out, workspace=ws)
+
+    for _ in range(max(3, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(e))
+    ms = statistics.median(ts)
+    launch_ms = ms / iters
+    peak, peak_kind = peaks()
+    gbs = 20 * H * W / (launch_ms * 1e-3) / 1e9
+    en = wmc.energy(out, None, clean).cpu()
+    line = {"workload": "l1", "metric": METRIC, "unit": UNIT, "config": {
+                "image": WORKLOAD.split(":")[0], "iters": iters, "lambda": lam, "step": step,
+                "alpha": alpha, "dtype": "f32", "l2": "flushed before each timed run"},
+            "results": {"value": H * W * iters / (ms * 1e-3) / 1e9, "ms": ms,
+                        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                     "frac": gbs / peak, "peak_kind": peak_kind,
+                                     "bytes_per_px_iter": 20, "launch_ms": launch_ms},
+                        "psnr_vs_clean_db": wmc.psnr(float(en[2]), H * W),
+                        "psnr_input_db": wmc.psnr(float(((f.double() - clean.double()) ** 2).sum()), H * W)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_diff(args):
     """Training through the unrolled flow: 32 images of 512 x 512 (seed 2000+i, 8 bumps + 4
     shapes, sigma 0.05), one learnable lambda per image (init 1.0), K = 50 denoising steps with
@@ -531,6 +588,8 @@ def main():
         return run_batch(args)
     if args.workload == "diff":
         return run_diff(args)
+    if args.workload == "l1":
+        return run_l1(args)
     return run_gpu(args)
 
 

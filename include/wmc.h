@@ -231,6 +231,28 @@ wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t
                                  size_t workspace_bytes, wmc_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
+ * wmc_denoise_l1: the L1-fidelity model min_U ||U - f||_1 + lambda R(U) solved by the primal-dual
+ * iteration of Sec. V-C with A = I (b eliminated):
+ *   r = U^t - f + d^t;  d^{t+1} = clip(r, -alpha, alpha);
+ *   U^{t+1} = U^t + step * (lambda H^w(U^t) - (2 d^{t+1} - d^t) / alpha)      t = 0..iters-1
+ * The paper gives neither alpha nor step; both are arguments (alpha > 0 "small").
+ *   f: device FP32, h x w, pitch ld.  u0: U^0 (device; NULL = f; may equal u for resuming in
+ *   place).  u: output U^iters.  d: the scaled dual variable, device FP32 with pitch ld, read as
+ *   d^0 and overwritten with d^iters; NULL = start from d^0 = 0 and discard it.
+ *   workspace: device, >= wmc_denoise_l1_workspace_size() bytes (status word, one ping-pong
+ *   image, one d image), aligned to WMC_WORKSPACE_ALIGN.  One kernel launch per iteration.
+ * Errors: WMC_ERR_INVALID_ARG (sizes, lambda < 0, step <= 0, alpha <= 0, non-finite values,
+ *         iters < 0, NULL f or u), WMC_ERR_ALIAS (u overlaps f or, unless equal, u0; d overlaps
+ *         f, u or u0; workspace overlaps an image), WMC_ERR_WORKSPACE, WMC_ERR_CUDA.
+ */
+size_t wmc_denoise_l1_workspace_size(int32_t h, int32_t w, int64_t ld);
+
+wmc_status_t wmc_denoise_l1(const float *f, const float *u0, float *u, float *d, int32_t h, int32_t w,
+                            int64_t ld, float lambda, float step, float alpha, int32_t iters,
+                            wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
+                            wmc_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
  * Reverse mode (training through the flow).  The paper uses H^w as a descent direction and
  * leaves the gradient of its regulariser open (Sec. III after Eq. wmcr); H^w is piecewise linear
  * in U, and on the piece picked by the selection of Eq. act it is the correlation of U with the

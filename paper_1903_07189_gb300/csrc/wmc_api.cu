@@ -800,6 +800,78 @@ wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t
     return wmc_batch_run(&plan, iters, stream);
 }
 
+size_t wmc_denoise_l1_workspace_size(int32_t h, int32_t w, int64_t ld) {
+    if (h < 0 || w < 0 || ld < w) return 0;
+    return kStatusBytes + 2 * image_bytes(h, ld, WMC_F32);
+}
+
+wmc_status_t wmc_denoise_l1(const float *f, const float *u0, float *u, float *d, int32_t h, int32_t w,
+                            int64_t ld, float lambda, float step, float alpha, int32_t iters,
+                            wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
+                            wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    wmc_status_t s;
+    if ((s = check_enums(WMC_F32, bnd)) != WMC_OK) return s;
+    if ((s = check_image(h, w, ld, "image")) != WMC_OK) return s;
+    if (!std::isfinite(lambda) || lambda < 0.0f)
+        return fail(WMC_ERR_INVALID_ARG, "lambda must be finite and >= 0 (got %g)", lambda);
+    if (!std::isfinite(step) || step <= 0.0f)
+        return fail(WMC_ERR_INVALID_ARG, "step must be finite and > 0 (got %g)", step);
+    if (!std::isfinite(alpha) || alpha <= 0.0f)
+        return fail(WMC_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
+    if (iters < 0) return fail(WMC_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
+    if (h == 0 || w == 0) return WMC_OK;
+    if (!f || !u) return fail(WMC_ERR_INVALID_ARG, "f or u is NULL");
+    if (!u0) u0 = f;
+    const size_t n = span_bytes(h, w, ld, 4);
+    if (overlap(u, n, f, n)) return fail(WMC_ERR_ALIAS, "u overlaps f");
+    if (u0 != u && overlap(u, n, u0, n)) return fail(WMC_ERR_ALIAS, "u overlaps u0");
+    if (d && (overlap(d, n, f, n) || overlap(d, n, u, n) || overlap(d, n, u0, n)))
+        return fail(WMC_ERR_ALIAS, "d overlaps f, u or u0");
+    const size_t need = wmc_denoise_l1_workspace_size(h, w, ld);
+    if (!workspace || workspace_bytes < need)
+        return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed", need);
+    if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
+        return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    if (overlap(workspace, need, f, n) || overlap(workspace, need, u, n) ||
+        overlap(workspace, need, u0, n) || (d && overlap(workspace, need, d, n)))
+        return fail(WMC_ERR_ALIAS, "workspace overlaps an image");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *base = static_cast<char *>(workspace) + kStatusBytes;
+    float *tmp = reinterpret_cast<float *>(base);
+    float *dw = d ? d : reinterpret_cast<float *>(base + image_bytes(h, ld, WMC_F32));
+    cudaError_t e;
+    if (!d) {  // d^0 = 0
+        e = cudaMemset2DAsync(dw, ld * 4, 0, w * 4, h, st);
+        if (e != cudaSuccess) return cuda_fail(e, "clear d");
+    }
+    const float *src = u0;
+    if (iters == 0) {
+        if (u0 != u) {
+            e = cudaMemcpy2DAsync(u, ld * 4, u0, ld * 4, w * 4, h, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "copy U^0");
+        }
+        return WMC_OK;
+    }
+    // step t writes u when iters-1-t is even, so the last step lands in u; U^0 read from u itself
+    // is moved to the workspace first when the first step would overwrite it
+    if (u0 == u && ((iters - 1) % 2 == 0)) {
+        e = cudaMemcpy2DAsync(tmp, ld * 4, u, ld * 4, w * 4, h, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copy U^0");
+        src = tmp;
+    }
+    const bool vec = pair_aligned(src, ld, 4) && pair_aligned(f, ld, 4) && pair_aligned(u, ld, 4) &&
+                     pair_aligned(tmp, ld, 4) && pair_aligned(dw, ld, 4);
+    const float c_h = step * lambda / 12.0f, c_d = step / alpha;
+    for (int32_t t = 0; t < iters; ++t) {
+        float *dst = ((iters - 1 - t) % 2 == 0) ? u : tmp;
+        e = wmc::launch_l1_step((int)bnd, src, f, dw, dst, h, w, ld, c_h, c_d, alpha, vec, st);
+        if (e != cudaSuccess) return cuda_fail(e, "primal-dual step");
+        src = dst;
+    }
+    return WMC_OK;
+}
+
 size_t wmc_unrolled_workspace_size(int32_t n, int32_t h, int32_t w, int64_t ld, int32_t K,
                                    int32_t ckpt_every) {
     if (n < 1 || h < 1 || w < 1 || ld < w || K < 0 || ckpt_every < 1) return 0;

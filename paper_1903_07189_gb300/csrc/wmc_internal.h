@@ -51,4 +51,9 @@ cudaError_t launch_adjoint_gather(int bnd, const float *g_in, const uint8_t *m, 
 cudaError_t launch_lambda_grad(const double *partials, int32_t K, int32_t n, int64_t nb, float step,
                                float *grad_lambda, cudaStream_t st);
 
+// One L1 primal-dual step (wmc_l1.cu): out = U^{t+1}, d updated in place.  FP32.
+cudaError_t launch_l1_step(int bnd, const float *u, const float *f, float *d, float *out, int32_t h,
+                           int32_t w, int64_t ld, float c_h, float c_d, float alpha, bool vec,
+                           cudaStream_t st);
+
 }  // namespace wmc

@@ -66,6 +66,9 @@ SIGNATURES = {
                               ctypes.POINTER(BatchPlan), _vp]),
     "wmc_batch_run": (_i32, [ctypes.POINTER(BatchPlan), _i32, _vp]),
     "wmc_denoise_batched": (_i32, [ctypes.POINTER(Image), _i32, _i32, _i32, _i32, _vp, _sz, _vp]),
+    "wmc_denoise_l1_workspace_size": (_sz, [_i32, _i32, _i64]),
+    "wmc_denoise_l1": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i64, _f32, _f32, _f32, _i32, _i32, _vp, _sz,
+                              _vp]),
     "wmc_unrolled_workspace_size": (_sz, [_i32, _i32, _i32, _i64, _i32, _i32]),
     "wmc_unrolled_forward": (_i32, [_vp, _vp, _f32, _i32, _i32, _i32, _i32, _i32, _i64, _i32, _vp, _vp, _sz,
                                     _vp]),
@@ -295,6 +298,32 @@ def denoise_batched(fs, lams, steps=None, iters: int = 100, boundary: str = "rep
                     steps_per_launch: int = 0):
     """Plan and run one batch; returns the output tensors."""
     return Batch(fs, lams, steps, outs, boundary, steps_per_launch).run(iters)
+
+
+def denoise_l1(f: torch.Tensor, lam: float = 1.0, step: float = 0.1, alpha: float = 0.1,
+               iters: int = 100, boundary: str = "replicate", u0: torch.Tensor | None = None,
+               d: torch.Tensor | None = None, out: torch.Tensor | None = None,
+               workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """L1-fidelity primal-dual iteration (Sec. V-C, A = I) on an FP32 CUDA image.  d, if given,
+    holds d^0 and receives d^iters (None: d^0 = 0)."""
+    p, h, w, ld = _img(f, "f")
+    if f.dtype != torch.float32:
+        raise ValueError("denoise_l1 supports float32 only")
+    if out is None:
+        out = torch.empty_strided(f.shape, f.stride(), dtype=f.dtype, device=f.device)
+    for t, n in [(u0, "u0"), (d, "d"), (out, "out")]:
+        if t is not None:
+            _, h2, w2, ld2 = _img(t, n)
+            if (h2, w2, ld2) != (h, w, ld) or t.dtype != torch.float32:
+                raise ValueError(f"{n} must match f in shape, pitch and dtype")
+    lib = load()
+    if workspace is None:
+        workspace = _workspace(lib.wmc_denoise_l1_workspace_size(h, w, ld), f.device)
+    _check(lib.wmc_denoise_l1(p, u0.data_ptr() if u0 is not None else None, out.data_ptr(),
+                              d.data_ptr() if d is not None else None, h, w, ld, float(lam), float(step),
+                              float(alpha), int(iters), BOUNDARY[boundary], workspace.data_ptr(),
+                              workspace.numel(), _stream(f.device)), "wmc_denoise_l1")
+    return out
 
 
 def _stack(t: torch.Tensor, name: str):

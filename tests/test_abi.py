@@ -190,3 +190,26 @@ def test_energy_grad_validation(lib):
     assert lib.wmc_energy_grad(u, u, 8, 8, 8, 0, ws, need, None) == ALIAS
     assert lib.wmc_energy_grad(u, g, 8, 8, 8, 0, ws, need - 1, None) == WORKSPACE
     assert lib.wmc_energy_grad(None, g, 8, 8, 8, 0, ws, need, None) == INVALID
+
+
+def test_l1_validation(lib):
+    f = ctypes.c_void_p(0x100000)
+    u = ctypes.c_void_p(0x300000)
+    d = ctypes.c_void_p(0x500000)
+    ws = ctypes.c_void_p(0x10000000)
+    need = lib.wmc_denoise_l1_workspace_size(8, 8, 8)
+    assert need >= 2 * 8 * 8 * 4
+    assert lib.wmc_denoise_l1_workspace_size(8, 8, 4) == 0
+    call = lambda f_, u0, u_, d_, lam, step, alpha, iters, ws_=ws, nbytes=need: lib.wmc_denoise_l1(
+        f_, u0, u_, d_, 8, 8, 8, lam, step, alpha, iters, 0, ws_, nbytes, None)
+    assert call(f, None, u, d, -1.0, 0.1, 0.1, 3) == INVALID
+    assert call(f, None, u, d, 1.0, 0.0, 0.1, 3) == INVALID
+    assert call(f, None, u, d, 1.0, 0.1, 0.0, 3) == INVALID
+    assert call(f, None, u, d, 1.0, 0.1, float("inf"), 3) == INVALID
+    assert call(f, None, u, d, 1.0, 0.1, 0.1, -1) == INVALID
+    assert call(None, None, u, d, 1.0, 0.1, 0.1, 3) == INVALID
+    assert call(f, None, f, d, 1.0, 0.1, 0.1, 3) == ALIAS
+    assert call(f, None, u, u, 1.0, 0.1, 0.1, 3) == ALIAS
+    assert call(f, None, u, d, 1.0, 0.1, 0.1, 3, nbytes=need - 1) == WORKSPACE
+    assert call(f, None, u, d, 1.0, 0.1, 0.1, 3, ws_=ctypes.c_void_p(0x10000008)) == WORKSPACE
+    assert call(f, None, u, d, 1.0, 0.1, 0.1, 3, ws_=ctypes.c_void_p(0x300000)) == ALIAS
