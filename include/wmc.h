@@ -293,14 +293,11 @@ wmc_status_t wmc_unrolled_backward(const float *f, const float *lambda, float st
 
 /*
  * wmc_energy_grad: grad = d/dU sum_p |H^w(U)(p)| (the Eq. wmcr regulariser, q = 1), selection
- * held fixed, sign(0) = 0.  u, grad: device FP32, h x w, pitch ld, must not overlap.
- * workspace: device, >= wmc_energy_grad_workspace_size() bytes (one byte and one float per pixel).
+ * held fixed, sign(0) = 0.  u, grad: device FP32, h x w, pitch ld, must not overlap.  One kernel
+ * launch, no workspace.
  */
-size_t wmc_energy_grad_workspace_size(int32_t h, int32_t w, int64_t ld);
-
 wmc_status_t wmc_energy_grad(const float *u, float *grad, int32_t h, int32_t w, int64_t ld,
-                             wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
-                             wmc_stream_t stream);
+                             wmc_boundary_t bnd, wmc_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------ */
 const char *wmc_status_string(wmc_status_t status); /* static string, never NULL */

@@ -42,25 +42,24 @@ __device__ __forceinline__ float half_laplace12_sel(float nw, float n, float ne,
     const float corners = (nw + se) + (ne + sw);
     const float edges = (n + s) + (w + e);
     const float L = fmaf(-12.0f, c, fmaf(2.0f, edges, corners));
-    const float a[4] = {fmaf(2.0f, q, A - B), fmaf(2.0f, p, A + B), fmaf(2.0f, p + q, A),
-                        fmaf(2.0f, p - q, B)};
+    const float a1 = fmaf(2.0f, q, A - B);
+    const float a2 = fmaf(2.0f, p, A + B);
+    const float a5 = fmaf(2.0f, p + q, A);
+    const float a6 = fmaf(2.0f, p - q, B);
     const float aL = fabsf(L);
-    float t = aL - fabsf(a[0]);
-    int j = 0;
-#pragma unroll
-    for (int k = 1; k < 4; ++k) {
-        const float tk = aL - fabsf(a[k]);
-        if (fabsf(tk) < fabsf(t)) {
-            t = tk;
-            j = k;
-        }
-    }
-    const float Ls = fmaf(0x1p-40f, a[0], L);
-    // candidate L + a_j is h_{direct}, L - a_j its antipode; the value returned is
-    // L - sign(Ls)|a_j|, i.e. + a_j exactly when the signs of Ls and a_j differ
-    const int direct[4] = {0, 1, 4, 5}, anti[4] = {2, 3, 6, 7};
-    const bool use_direct = (a[j] == 0.0f) || (signbit(Ls) != signbit(a[j]));
-    *m = use_direct ? direct[j] : anti[j];
+    // the same comparisons in the same order as select12; aj and jd track the winner's odd
+    // part and the kernel index of its "L + a_j" candidate (h1, h2, h5, h6)
+    float t = aL - fabsf(a1), aj = a1;
+    int jd = 0;
+    const float t2 = aL - fabsf(a2), t5 = aL - fabsf(a5), t6 = aL - fabsf(a6);
+    if (fabsf(t2) < fabsf(t)) { t = t2; aj = a2; jd = 1; }
+    if (fabsf(t5) < fabsf(t)) { t = t5; aj = a5; jd = 4; }
+    if (fabsf(t6) < fabsf(t)) { t = t6; aj = a6; jd = 5; }
+    const float Ls = fmaf(0x1p-40f, a1, L);
+    // the value returned is L - sign(Ls)|a_j|: the "L + a_j" kernel when the signs of Ls and a_j
+    // differ (or a_j = 0), else its antipode (index + 2: h3, h4, h7, h8)
+    const bool use_direct = (aj == 0.0f) || (signbit(Ls) != signbit(aj));
+    *m = use_direct ? jd : jd + 2;
     return __int_as_float(__float_as_int(t) ^ (__float_as_int(Ls) & 0x80000000));
 }
 
@@ -70,168 +69,299 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// ---------------------------------------------------------------------------------- pass A
-// For every pixel p of image blockIdx.y: m(p) and either
-//   - partials[blockIdx.y * gridDim.x + blockIdx.x] = sum over the CTA's pixels of g(p) * 12 H^w(p)
-//   - or, when sign_out != nullptr, sign_out(p) = sign(H^w(p)) (energy gradient).
-template <int BND>
-__global__ void __launch_bounds__(kStreamWarps * 32)
-    adjoint_select_kernel(const float *__restrict__ U, const float *__restrict__ g,
-                          uint8_t *__restrict__ mout, float *__restrict__ sign_out,
-                          double *__restrict__ partials, int h, int w, int64_t ld,
-                          int64_t img_stride) {
-    constexpr int R = kStreamRY;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
-    const int by = (int)(blockIdx.x / nbx), bx = (int)(blockIdx.x - (unsigned)by * nbx);
-    const int x = ((bx * kStreamWarps + warp) * 32 + lane) * 2;
-    const int y0 = by * R;
-    const int64_t off = (int64_t)blockIdx.y * img_stride;
-    U += off;
-    mout += off;
-    if (g) g += off;
-    if (sign_out) sign_out += off;
-    float acc = 0.0f;
-    if ((x & ~63) < w) {
-        float2 v[R + 2];
-        float el[R + 2], er[R + 2];
-#pragma unroll
-        for (int k = 0; k < R + 2; ++k) {
-            bool ok;
-            const int y = row_index<BND>(y0 - 1 + k, h, &ok);
-            const float *row = U + (int64_t)y * ld;
-            v[k] = load_pair<float, BND, false>(row, x, w, ok);
-            el[k] = (lane == 0) ? load_one<float, BND>(row, x - 1, w, ok) : 0.0f;
-            er[k] = (lane == 31) ? load_one<float, BND>(row, x + 2, w, ok) : 0.0f;
-        }
-        float lf[R + 2], rt[R + 2];
-#pragma unroll
-        for (int k = 0; k < R + 2; ++k) {
-            lf[k] = __shfl_up_sync(0xffffffffu, v[k].y, 1);
-            rt[k] = __shfl_down_sync(0xffffffffu, v[k].x, 1);
-            if (lane == 0) lf[k] = el[k];
-            if (lane == 31) rt[k] = er[k];
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const int y = y0 + k;
-            if (y >= h) break;
-            int m0, m1;
-            const float h0 = half_laplace12_sel(lf[k], v[k].x, v[k].y, lf[k + 1], v[k + 1].x,
-                                                v[k + 1].y, lf[k + 2], v[k + 2].x, v[k + 2].y, &m0);
-            const float h1 = half_laplace12_sel(v[k].x, v[k].y, rt[k], v[k + 1].x, v[k + 1].y,
-                                                rt[k + 1], v[k + 2].x, v[k + 2].y, rt[k + 2], &m1);
-            const int64_t o = (int64_t)y * ld + x;
-            if (x < w) {
-                mout[o] = (uint8_t)m0;
-                if (sign_out) sign_out[o] = h0 > 0.0f ? 1.0f : (h0 < 0.0f ? -1.0f : 0.0f);
-                if (g) acc = fmaf(g[o], h0, acc);
-            }
-            if (x + 1 < w) {
-                mout[o + 1] = (uint8_t)m1;
-                if (sign_out) sign_out[o + 1] = h1 > 0.0f ? 1.0f : (h1 < 0.0f ? -1.0f : 0.0f);
-                if (g) acc = fmaf(g[o + 1], h1, acc);
-            }
+// ------------------------------------------------------------------------- one adjoint step
+// One CTA owns a kTX x kTY tile of q and stages in shared memory
+//   U on the tile + 2 rings (the selection of every p next to the tile needs U around p),
+//   g on the tile + 1 ring (0 outside the image), and m(p) on the tile + 1 ring.
+// Phase 1 loads (a warp per row, lanes along it; every load issued before the first store),
+// phase 2 selects m(p) (and, for the flow, adds g(p) * 12 H^w(p) over the tile's own pixels into
+// the dlambda partial; for the energy, sets g(p) = sign(H^w(p))), phase 3 gathers
+//   g_out(q) = c_self g(q) + c_nb * sum_p sum_o [p + o reads q] W12[m(p)][o] g(p)
+// with c_nb = step * lambda[img] / 12 (flow) or 1/12 (energy), and
+//   grad_f(q) = (first ? 0 : grad_f(q)) + step g(q) (+ g_out(q) when last).
+// In phases 2 and 3 a thread owns one column and walks kRows rows down it with a 3-row window in
+// registers, so each new row costs 3 shared loads instead of 9.
+constexpr int kTX = 64, kTY = 32, kAdjThreads = 256;
+constexpr int kGroups = kAdjThreads / kTX;  // row groups
+constexpr int kRows = kTY / kGroups;        // rows per thread
+
+int64_t adjoint_blocks(int32_t h, int32_t w) {
+    return (int64_t)((w + kTX - 1) / kTX) * ((h + kTY - 1) / kTY);
+}
+
+using AdjU = float[kTY + 4][kTX + 4];
+using AdjG = float[kTY + 2][kTX + 2];
+using AdjM = uint8_t[kTY + 2][kTX + 2];
+
+// Selection at p = tile (r, cc) from its 3x3 U window; returns g(p) * 12 H^w(p) for the dlambda
+// partial when p is one of the tile's own pixels (flow), else 0.
+template <int BND, bool ENERGY, bool CHECK>
+__device__ __forceinline__ float adjoint_select_one(AdjU &us, AdjG &gs, AdjM &ms, int r, int cc,
+                                                    int x0, int y0, int h, int w, float nw, float n,
+                                                    float ne, float wv, float ce, float e, float sw,
+                                                    float sv, float se) {
+    if (CHECK) {
+        const int y = y0 + r, x = x0 + cc;
+        if (y < 0 || y >= h || x < 0 || x >= w) {
+            ms[r + 1][cc + 1] = 0;
+            if (ENERGY) gs[r + 1][cc + 1] = 0.0f;
+            return 0.0f;
         }
     }
-    if (!partials) return;
-    __shared__ double red[kStreamWarps];
-    const double s = warp_sum_d((double)acc);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kStreamWarps; ++i) t += red[i];
-        partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    int m;
+    const float h12 = half_laplace12_sel(nw, n, ne, wv, ce, e, sw, sv, se, &m);
+    ms[r + 1][cc + 1] = (uint8_t)m;
+    if (ENERGY) {
+        gs[r + 1][cc + 1] = h12 > 0.0f ? 1.0f : (h12 < 0.0f ? -1.0f : 0.0f);
+        return 0.0f;
+    }
+    return (r >= 0 && r < kTY && cc >= 0 && cc < kTX) ? gs[r + 1][cc + 1] * h12 : 0.0f;
+}
+
+// kRows selections down column c from row r0, a 3-row U window carried in registers.
+template <int BND, bool ENERGY, bool CHECK>
+__device__ __forceinline__ float adjoint_select_rows(AdjU &us, AdjG &gs, AdjM &ms, int c, int r0,
+                                                     int x0, int y0, int h, int w) {
+    float acc = 0.0f;
+    float a0 = us[r0 + 1][c + 1], a1 = us[r0 + 1][c + 2], a2 = us[r0 + 1][c + 3];
+    float b0 = us[r0 + 2][c + 1], b1 = us[r0 + 2][c + 2], b2 = us[r0 + 2][c + 3];
+#pragma unroll
+    for (int k = 0; k < kRows; ++k) {
+        const int r = r0 + k;
+        const float d0 = us[r + 3][c + 1], d1 = us[r + 3][c + 2], d2 = us[r + 3][c + 3];
+        const float t = adjoint_select_one<BND, ENERGY, CHECK>(us, gs, ms, r, c, x0, y0, h, w, a0, a1,
+                                                               a2, b0, b1, b2, d0, d1, d2);
+        if (!ENERGY) acc += t;
+        a0 = b0; a1 = b1; a2 = b2;
+        b0 = d0; b1 = d1; b2 = d2;
+    }
+    return acc;
+}
+
+// Gather of kRows outputs q down column c from row r0 (see the kernel's comment).
+template <int BND, bool CHECK>
+__device__ __forceinline__ void adjoint_gather_rows(AdjG &gs, AdjM &ms, float (&taps)[8][9],
+                                                    float *__restrict__ g_out,
+                                                    float *__restrict__ grad_f, int c, int r0,
+                                                    int x0, int y0, int h, int w, int64_t ld,
+                                                    float step, float c_self, float c_nb, int first,
+                                                    int last) {
+    const int qx = x0 + c;
+    float g0[3], g1[3], g2[3];
+    int m0[3], m1[3], m2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        g0[k] = gs[r0][c + k];
+        m0[k] = ms[r0][c + k];
+        g1[k] = gs[r0 + 1][c + k];
+        m1[k] = ms[r0 + 1][c + k];
+    }
+    // the grad_f reads of all rows go out before the gather arithmetic
+    float gfv[kRows];
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+        gfv[j] = 0.0f;
+        const int qy = y0 + r0 + j;
+        if (grad_f && !first && (!CHECK || (qy < h && qx < w))) gfv[j] = grad_f[(int64_t)qy * ld + qx];
+    }
+    int64_t o = (int64_t)(y0 + r0) * ld + qx;
+#pragma unroll
+    for (int j = 0; j < kRows; ++j, o += ld) {
+        const int r = r0 + j;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            g2[k] = gs[r + 2][c + k];
+            m2[k] = ms[r + 2][c + k];
+        }
+        const int qy = y0 + r;
+        if (!CHECK || (qy < h && qx < w)) {
+            // p = q + (dy, dx) reads q through its tap (-dy, -dx): index (1-dy)*3 + (1-dx);
+            // p outside the image carries g = 0
+            float a = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                a = fmaf(taps[m0[k]][8 - k], g0[k], a);  // dy = -1
+                a = fmaf(taps[m1[k]][5 - k], g1[k], a);  // dy = 0
+                a = fmaf(taps[m2[k]][2 - k], g2[k], a);  // dy = +1
+            }
+            if (BND == BND_REPLICATE && CHECK) {
+                // Taps that leave the image read the clamped pixel.  On the first row, the taps
+                // of row-0 pixels pointing up (oy = -1) also read q; likewise for the last row,
+                // the first and last columns, and, at a corner, the diagonal tap of q itself.
+                const bool top = qy == 0, bottom = qy == h - 1, left = qx == 0, right = qx == w - 1;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    if (top) a = fmaf(taps[m1[k]][2 - k], g1[k], a);
+                    if (bottom) a = fmaf(taps[m1[k]][8 - k], g1[k], a);
+                }
+                if (left) {
+                    a = fmaf(taps[m0[1]][6], g0[1], a);
+                    a = fmaf(taps[m1[1]][3], g1[1], a);
+                    a = fmaf(taps[m2[1]][0], g2[1], a);
+                }
+                if (right) {
+                    a = fmaf(taps[m0[1]][8], g0[1], a);
+                    a = fmaf(taps[m1[1]][5], g1[1], a);
+                    a = fmaf(taps[m2[1]][2], g2[1], a);
+                }
+                if (top && left) a = fmaf(taps[m1[1]][0], g1[1], a);
+                if (top && right) a = fmaf(taps[m1[1]][2], g1[1], a);
+                if (bottom && left) a = fmaf(taps[m1[1]][6], g1[1], a);
+                if (bottom && right) a = fmaf(taps[m1[1]][8], g1[1], a);
+            }
+            const float gq = g1[1];
+            const float out = fmaf(c_nb, a, c_self * gq);
+            g_out[o] = out;
+            if (grad_f) {
+                float v = fmaf(step, gq, gfv[j]);
+                if (last) v += out;
+                grad_f[o] = v;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            g0[k] = g1[k]; m0[k] = m1[k];
+            g1[k] = g2[k]; m1[k] = m2[k];
+        }
     }
 }
 
-// ---------------------------------------------------------------------------------- pass B
-// g_out(q) = c_self * g_in(q) + c_nb(img) * sum_p sum_o [p + o reads q] W12[m(p)][o] g_in(p)
-// with c_nb = step * lambda[img] / 12 (flow) or 1/12 (energy), and optionally
-//   grad_f(q) = (first ? 0 : grad_f(q)) + step * g_in(q) (+ g_out(q) when last).
-constexpr int kGX = 32, kGY = 8;
-
-template <int BND>
-__global__ void __launch_bounds__(kGX * kGY)
-    adjoint_gather_kernel(const float *__restrict__ g_in, const uint8_t *__restrict__ m,
-                          float *__restrict__ g_out, float *__restrict__ grad_f,
-                          const float *__restrict__ lam, float step, float c_self, float c_nb_fixed,
-                          int first, int last, int h, int w, int64_t ld, int64_t img_stride) {
+template <int BND, bool ENERGY>
+__global__ void __launch_bounds__(kAdjThreads, 4)
+    adjoint_step_kernel(const float *__restrict__ U, const float *__restrict__ g_in,
+                        float *__restrict__ g_out, float *__restrict__ grad_f,
+                        double *__restrict__ partials, const float *__restrict__ lam, float step,
+                        float c_self, float c_nb_fixed, int first, int last, int h, int w, int64_t ld,
+                        int64_t img_stride) {
+    constexpr int UW = kTX + 4, UH = kTY + 4, GW = kTX + 2, GH = kTY + 2;
+    constexpr int NW = kAdjThreads / 32;
     __shared__ float taps[8][9];
-    __shared__ float gs[kGY + 2][kGX + 2];
-    __shared__ uint8_t ms[kGY + 2][kGX + 2];
-    const int tid = threadIdx.y * kGX + threadIdx.x;
+    __shared__ float us[UH][UW];
+    __shared__ float gs[GH][GW];
+    __shared__ uint8_t ms[GH][GW];
+    __shared__ double red[NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < 72) taps[tid / 9][tid % 9] = kH12Taps[tid / 9][tid % 9];
-    const int64_t off = (int64_t)blockIdx.z * img_stride;
-    g_in += off;
-    m += off;
+    const int64_t off = (int64_t)blockIdx.y * img_stride;
+    U += off;
     g_out += off;
+    if (!ENERGY) g_in += off;
     if (grad_f) grad_f += off;
-    const int qx0 = blockIdx.x * kGX, qy0 = blockIdx.y * kGY;
-    // halo tile: g and m of p = q + (-1..1, -1..1); pixels outside the image carry g = 0
-    for (int i = tid; i < (kGY + 2) * (kGX + 2); i += kGX * kGY) {
-        const int r = i / (kGX + 2), c = i % (kGX + 2);
-        const int y = qy0 - 1 + r, x = qx0 - 1 + c;
-        const bool in = (y >= 0) & (y < h) & (x >= 0) & (x < w);
-        gs[r][c] = in ? g_in[(int64_t)y * ld + x] : 0.0f;
-        ms[r][c] = in ? m[(int64_t)y * ld + x] : 0;
+    const int nbx = (w + kTX - 1) / kTX;
+    const int by = (int)(blockIdx.x / nbx), bx = (int)(blockIdx.x - (unsigned)by * nbx);
+    const int x0 = bx * kTX, y0 = by * kTY;
+
+    // ---- phase 1: rows warp, warp + NW, ...; columns lane, lane + 32, lane + 64
+    {
+        constexpr int RU = (UH + NW - 1) / NW, RG = (GH + NW - 1) / NW;
+        int ux[3], gx[3];
+        bool uok[3], gok[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int cu = lane + 32 * k, xu = x0 - 2 + cu;
+            uok[k] = cu < UW && (BND == BND_REPLICATE || (xu >= 0 && xu < w));
+            ux[k] = min(max(xu, 0), w - 1);
+            const int cg = lane + 32 * k, xg = x0 - 1 + cg;
+            gok[k] = cg < GW && xg >= 0 && xg < w;
+            gx[k] = min(max(xg, 0), w - 1);
+        }
+        float uv[RU][3];
+#pragma unroll
+        for (int j = 0; j < RU; ++j) {
+            const int r = warp + NW * j, y = y0 - 2 + r;
+            const bool rok = r < UH && (BND == BND_REPLICATE || (y >= 0 && y < h));
+            const float *row = U + (int64_t)min(max(y, 0), h - 1) * ld;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) uv[j][k] = (rok && uok[k]) ? row[ux[k]] : 0.0f;
+        }
+        float gv[RG][3];
+        if (!ENERGY) {
+#pragma unroll
+            for (int j = 0; j < RG; ++j) {
+                const int r = warp + NW * j, y = y0 - 1 + r;
+                const bool rok = r < GH && y >= 0 && y < h;
+                const float *row = g_in + (int64_t)min(max(y, 0), h - 1) * ld;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gv[j][k] = (rok && gok[k]) ? row[gx[k]] : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RU; ++j) {
+            const int r = warp + NW * j;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (r < UH && lane + 32 * k < UW) us[r][lane + 32 * k] = uv[j][k];
+        }
+        if (!ENERGY) {
+#pragma unroll
+            for (int j = 0; j < RG; ++j) {
+                const int r = warp + NW * j;
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (r < GH && lane + 32 * k < GW) gs[r][lane + 32 * k] = gv[j][k];
+            }
+        }
     }
     __syncthreads();
-    const int qx = qx0 + threadIdx.x, qy = qy0 + threadIdx.y;
-    if (qx >= w || qy >= h) return;
-    const float c_nb = lam ? step * __ldg(lam + blockIdx.z) / 12.0f : c_nb_fixed;
+
+    // ---- phase 2: p at tile (r, c) <-> ms/gs[r + 1][c + 1], U window us[r + 1 .. r + 3][c + 1 .. c + 3]
+    // Tiles whose ring lies inside the image (all but the border tiles) skip every bounds check.
+    const bool interior = x0 >= 1 && y0 >= 1 && x0 + kTX < w && y0 + kTY < h;
+    const int c = tid % kTX, grp = tid / kTX;
     float acc = 0.0f;
-    const bool edge = (BND == BND_REPLICATE) &&
-                      ((qx == 0) | (qx == w - 1) | (qy == 0) | (qy == h - 1));
-    if (!edge) {
-        // every p = q - o inside the image read q through tap o only
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int r = threadIdx.y + 1 + dy, c = threadIdx.x + 1 + dx;
-                const int o = (1 - dy) * 3 + (1 - dx);  // tap of p that reads q
-                acc = fmaf(taps[ms[r][c]][o], gs[r][c], acc);
-            }
-    } else {
-        // image edge under REPLICATE: p's taps that fall outside the image read the clamped
-        // pixel, so several taps of one p may read q
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int py = qy + dy, px = qx + dx;
-                if (py < 0 || py >= h || px < 0 || px >= w) continue;
-                const int r = threadIdx.y + 1 + dy, c = threadIdx.x + 1 + dx;
-                const float gp = gs[r][c];
-                const int mm = ms[r][c];
-                for (int oy = -1; oy <= 1; ++oy)
-                    for (int ox = -1; ox <= 1; ++ox) {
-                        const int ry = min(max(py + oy, 0), h - 1), rx = min(max(px + ox, 0), w - 1);
-                        if (ry == qy && rx == qx) acc = fmaf(taps[mm][(oy + 1) * 3 + (ox + 1)], gp, acc);
-                    }
-            }
+    if (interior)
+        acc = adjoint_select_rows<BND, ENERGY, false>(us, gs, ms, c, grp * kRows, x0, y0, h, w);
+    else
+        acc = adjoint_select_rows<BND, ENERGY, true>(us, gs, ms, c, grp * kRows, x0, y0, h, w);
+    // the ring: rows -1 and kTY (all kTX + 2 columns), columns -1 and kTX (rows 0 .. kTY-1)
+    for (int i = tid; i < 2 * GW + 2 * kTY; i += kAdjThreads) {
+        int r, cc;
+        if (i < 2 * GW) {
+            r = i < GW ? -1 : kTY;
+            cc = (i < GW ? i : i - GW) - 1;
+        } else {
+            const int k = i - 2 * GW;
+            cc = k < kTY ? -1 : kTX;
+            r = k < kTY ? k : k - kTY;
+        }
+        adjoint_select_one<BND, ENERGY, true>(us, gs, ms, r, cc, x0, y0, h, w,
+                                              us[r + 1][cc + 1], us[r + 1][cc + 2], us[r + 1][cc + 3],
+                                              us[r + 2][cc + 1], us[r + 2][cc + 2], us[r + 2][cc + 3],
+                                              us[r + 3][cc + 1], us[r + 3][cc + 2], us[r + 3][cc + 3]);
     }
-    const float gq = gs[threadIdx.y + 1][threadIdx.x + 1];
-    const float out = fmaf(c_nb, acc, c_self * gq);
-    const int64_t o = (int64_t)qy * ld + qx;
-    g_out[o] = out;
-    if (grad_f) {
-        float v = first ? 0.0f : grad_f[o];
-        v = fmaf(step, gq, v);
-        if (last) v += out;
-        grad_f[o] = v;
+    if (!ENERGY && partials) {
+        const double sacc = warp_sum_d((double)acc);
+        if (lane == 0) red[warp] = sacc;
     }
+    __syncthreads();
+    if (!ENERGY && partials && tid == 0) {
+        double t = 0.0;
+        for (int k = 0; k < NW; ++k) t += red[k];
+        partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+
+    // ---- phase 3
+    const float c_nb = ENERGY ? c_nb_fixed : step * __ldg(lam + blockIdx.y) / 12.0f;
+    if (interior)
+        adjoint_gather_rows<BND, false>(gs, ms, taps, g_out, grad_f, c, grp * kRows, x0, y0, h, w, ld,
+                                        step, c_self, c_nb, first, last);
+    else
+        adjoint_gather_rows<BND, true>(gs, ms, taps, g_out, grad_f, c, grp * kRows, x0, y0, h, w, ld,
+                                       step, c_self, c_nb, first, last);
 }
 
 // ---------------------------------------------------------------------------------- dlambda
 // grad_lambda[i] = step / 12 * sum over steps t and CTAs b of partials[t][i][b], in a fixed order.
 __global__ void lambda_grad_kernel(const double *__restrict__ partials, int K, int n, int nb,
                                    float step, float *__restrict__ grad_lambda) {
-    const int i = blockIdx.x;
+    const int img = blockIdx.x;
+    const int64_t total = (int64_t)K * nb;
+    // thread i adds the partials i, i + blockDim.x, ... of this image (t-major), then a fixed tree
     double a = 0.0;
-    for (int t = 0; t < K; ++t)
-        for (int b = threadIdx.x; b < nb; b += blockDim.x)
-            a += partials[((int64_t)t * n + i) * nb + b];
+    for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+        const int64_t t = i / nb, b = i - t * nb;
+        a += partials[(t * n + img) * nb + b];
+    }
     __shared__ double red[32];
     a = warp_sum_d(a);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
@@ -239,41 +369,35 @@ __global__ void lambda_grad_kernel(const double *__restrict__ partials, int K, i
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) t += red[k];
-        grad_lambda[i] = (float)((double)step / 12.0 * t);
+        grad_lambda[img] = (float)((double)step / 12.0 * t);
     }
 }
 
 // ------------------------------------------------------------------------------- launchers
-int64_t adjoint_select_blocks(int32_t h, int32_t w) {
-    const int64_t nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
-    const int64_t nby = (h + kStreamRY - 1) / kStreamRY;
-    return nbx * nby;
-}
-
-cudaError_t launch_adjoint_select(int bnd, const float *U, const float *g, uint8_t *m,
-                                  float *sign_out, double *partials, int32_t n, int32_t h,
-                                  int32_t w, int64_t ld, int64_t img_stride, cudaStream_t st) {
-    const int64_t nb = adjoint_select_blocks(h, w);
+cudaError_t launch_adjoint_step(int bnd, const float *U, const float *g_in, float *g_out,
+                                float *grad_f, double *partials, const float *lam, float step,
+                                int first, int last, int32_t n, int32_t h, int32_t w, int64_t ld,
+                                int64_t img_stride, cudaStream_t st) {
+    const int64_t nb = adjoint_blocks(h, w);
     if (nb > 0x7fffffffLL || n > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)nb, (unsigned)n);
+    const float c_self = 1.0f - step;
     if (bnd == BND_ZERO)
-        adjoint_select_kernel<BND_ZERO><<<grid, kStreamWarps * 32, 0, st>>>(U, g, m, sign_out, partials, h, w, ld, img_stride);
+        adjoint_step_kernel<BND_ZERO, false><<<grid, kAdjThreads, 0, st>>>(U, g_in, g_out, grad_f, partials, lam, step, c_self, 0.0f, first, last, h, w, ld, img_stride);
     else
-        adjoint_select_kernel<BND_REPLICATE><<<grid, kStreamWarps * 32, 0, st>>>(U, g, m, sign_out, partials, h, w, ld, img_stride);
+        adjoint_step_kernel<BND_REPLICATE, false><<<grid, kAdjThreads, 0, st>>>(U, g_in, g_out, grad_f, partials, lam, step, c_self, 0.0f, first, last, h, w, ld, img_stride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_gather(int bnd, const float *g_in, const uint8_t *m, float *g_out,
-                                  float *grad_f, const float *lam, float step, float c_self,
-                                  float c_nb, int first, int last, int32_t n, int32_t h, int32_t w,
-                                  int64_t ld, int64_t img_stride, cudaStream_t st) {
-    if (n > 65535 || (h + kGY - 1) / kGY > 65535) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)((w + kGX - 1) / kGX), (unsigned)((h + kGY - 1) / kGY), (unsigned)n);
-    dim3 block(kGX, kGY);
+cudaError_t launch_energy_grad(int bnd, const float *U, float *grad, int32_t h, int32_t w, int64_t ld,
+                               cudaStream_t st) {
+    const int64_t nb = adjoint_blocks(h, w);
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)nb, 1u);
     if (bnd == BND_ZERO)
-        adjoint_gather_kernel<BND_ZERO><<<grid, block, 0, st>>>(g_in, m, g_out, grad_f, lam, step, c_self, c_nb, first, last, h, w, ld, img_stride);
+        adjoint_step_kernel<BND_ZERO, true><<<grid, kAdjThreads, 0, st>>>(U, nullptr, grad, nullptr, nullptr, nullptr, 0.0f, 0.0f, 1.0f / 12.0f, 0, 0, h, w, ld, 0);
     else
-        adjoint_gather_kernel<BND_REPLICATE><<<grid, block, 0, st>>>(g_in, m, g_out, grad_f, lam, step, c_self, c_nb, first, last, h, w, ld, img_stride);
+        adjoint_step_kernel<BND_REPLICATE, true><<<grid, kAdjThreads, 0, st>>>(U, nullptr, grad, nullptr, nullptr, nullptr, 0.0f, 0.0f, 1.0f / 12.0f, 0, 0, h, w, ld, 0);
     return cudaGetLastError();
 }
 
@@ -299,7 +423,8 @@ cudaError_t launch_stack_step(int bnd, const float *u, const float *f, float *ou
     p.img_stride = img_stride;
     p.lam = lam;
     p.step = step;
-    const int64_t nb = adjoint_select_blocks(h, w);
+    const int64_t nb = (int64_t)((w + kStreamWarps * 64 - 1) / (kStreamWarps * 64)) *
+                       ((h + kStreamRY - 1) / kStreamRY);
     if (nb > 0x7fffffffLL || n > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)nb, (unsigned)n);
     const unsigned b = kStreamWarps * 32;

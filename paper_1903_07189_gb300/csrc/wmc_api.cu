@@ -403,9 +403,9 @@ __global__ void batch_copy_kernel(const wmc::BatchImage *images, const int4 *til
 }
 
 // Unrolled-flow workspace: [status | checkpoints | segment/temporary stacks | g ping-pong |
-// selection bytes | dlambda partials].
+// dlambda partials].
 struct UnrolledLayout {
-    size_t slot, off_ckpt, off_seg, off_g, off_m, off_part, total;
+    size_t slot, off_ckpt, off_seg, off_g, off_part, total;
     int32_t ncp, nseg;
     int64_t nb;
 };
@@ -416,12 +416,11 @@ UnrolledLayout unrolled_layout(int32_t n, int32_t h, int32_t w, int64_t ld, int3
     L.slot = round_up(px * sizeof(float), WMC_WORKSPACE_ALIGN);
     L.ncp = K >= 1 ? (K - 1) / c : 0;
     L.nseg = c - 1 > 2 ? c - 1 : 2;
-    L.nb = wmc::adjoint_select_blocks(h, w);
+    L.nb = wmc::adjoint_blocks(h, w);
     L.off_ckpt = kStatusBytes;
     L.off_seg = L.off_ckpt + (size_t)L.ncp * L.slot;
     L.off_g = L.off_seg + (size_t)L.nseg * L.slot;
-    L.off_m = L.off_g + 2 * L.slot;
-    L.off_part = L.off_m + round_up(px, WMC_WORKSPACE_ALIGN);
+    L.off_part = L.off_g + 2 * L.slot;
     L.total = L.off_part + round_up((size_t)(K > 0 ? K : 1) * n * L.nb * sizeof(double), WMC_WORKSPACE_ALIGN);
     return L;
 }
@@ -955,7 +954,6 @@ wmc_status_t wmc_unrolled_backward(const float *f, const float *lambda, float st
     auto seg = [&](int i) { return reinterpret_cast<float *>(base + L.off_seg + (size_t)i * L.slot); };
     float *gbuf[2] = {reinterpret_cast<float *>(base + L.off_g),
                       reinterpret_cast<float *>(base + L.off_g + L.slot)};
-    uint8_t *msel = reinterpret_cast<uint8_t *>(base + L.off_m);
     double *part = reinterpret_cast<double *>(base + L.off_part);
     const float *g_in = grad_u;
     int gi = 0;
@@ -974,14 +972,10 @@ wmc_status_t wmc_unrolled_backward(const float *f, const float *lambda, float st
         }
         for (int t = t1 - 1; t >= t0; --t) {
             const float *Ut = (t == t0) ? start : seg(t - t0 - 1);
-            e = wmc::launch_adjoint_select((int)bnd, Ut, g_in, msel, nullptr, part + (size_t)t * n * L.nb,
-                                           n, h, w, ld, stride, st);
-            if (e != cudaSuccess) return cuda_fail(e, "adjoint select");
             float *g_out = gbuf[gi];
-            e = wmc::launch_adjoint_gather((int)bnd, g_in, msel, g_out, grad_f, lambda, step,
-                                           1.0f - step, 0.0f, t == K - 1, t == 0, n, h, w, ld,
-                                           stride, st);
-            if (e != cudaSuccess) return cuda_fail(e, "adjoint gather");
+            e = wmc::launch_adjoint_step((int)bnd, Ut, g_in, g_out, grad_f, part + (size_t)t * n * L.nb,
+                                         lambda, step, t == K - 1, t == 0, n, h, w, ld, stride, st);
+            if (e != cudaSuccess) return cuda_fail(e, "adjoint step");
             g_in = g_out;
             gi ^= 1;
         }
@@ -991,15 +985,8 @@ wmc_status_t wmc_unrolled_backward(const float *f, const float *lambda, float st
     return WMC_OK;
 }
 
-size_t wmc_energy_grad_workspace_size(int32_t h, int32_t w, int64_t ld) {
-    if (h < 1 || w < 1 || ld < w) return 0;
-    const size_t px = (size_t)h * (size_t)ld;
-    return round_up(px, WMC_WORKSPACE_ALIGN) + round_up(px * sizeof(float), WMC_WORKSPACE_ALIGN);
-}
-
 wmc_status_t wmc_energy_grad(const float *u, float *grad, int32_t h, int32_t w, int64_t ld,
-                             wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
-                             wmc_stream_t stream) {
+                             wmc_boundary_t bnd, wmc_stream_t stream) {
     g_last_error[0] = 0;
     wmc_status_t s;
     if ((s = check_enums(WMC_F32, bnd)) != WMC_OK) return s;
@@ -1008,20 +995,7 @@ wmc_status_t wmc_energy_grad(const float *u, float *grad, int32_t h, int32_t w, 
     if (!u || !grad) return fail(WMC_ERR_INVALID_ARG, "NULL image pointer");
     const size_t nbytes = span_bytes(h, w, ld, 4);
     if (overlap(u, nbytes, grad, nbytes)) return fail(WMC_ERR_ALIAS, "grad overlaps u");
-    const size_t need = wmc_energy_grad_workspace_size(h, w, ld);
-    if (!workspace || workspace_bytes < need)
-        return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed", need);
-    if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
-        return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
-    uint8_t *msel = static_cast<uint8_t *>(workspace);
-    float *sgn = reinterpret_cast<float *>(static_cast<char *>(workspace) +
-                                           round_up((size_t)h * ld, WMC_WORKSPACE_ALIGN));
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = wmc::launch_adjoint_select((int)bnd, u, nullptr, msel, sgn, nullptr, 1, h, w, ld,
-                                               (int64_t)h * ld, st);
-    if (e == cudaSuccess)
-        e = wmc::launch_adjoint_gather((int)bnd, sgn, msel, grad, nullptr, nullptr, 0.0f, 0.0f,
-                                       1.0f / 12.0f, 0, 0, 1, h, w, ld, (int64_t)h * ld, st);
+    cudaError_t e = wmc::launch_energy_grad((int)bnd, u, grad, h, w, ld, (cudaStream_t)stream);
     return e == cudaSuccess ? WMC_OK : cuda_fail(e, "energy gradient");
 }
 

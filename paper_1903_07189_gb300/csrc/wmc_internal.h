@@ -37,17 +37,17 @@ cudaError_t launch_energy(int dtype, const void *u, const void *f, const void *c
                           cudaStream_t st);
 
 // Adjoint (wmc_adjoint.cu).  Stacks: n images, image i at offset i * img_stride elements.
-int64_t adjoint_select_blocks(int32_t h, int32_t w);
+// adjoint_blocks: CTAs per image of one adjoint step (one dlambda partial each).
+int64_t adjoint_blocks(int32_t h, int32_t w);
 cudaError_t launch_stack_step(int bnd, const float *u, const float *f, float *out, const float *lam,
                               float step, int32_t n, int32_t h, int32_t w, int64_t ld,
                               int64_t img_stride, bool vec, cudaStream_t st);
-cudaError_t launch_adjoint_select(int bnd, const float *U, const float *g, uint8_t *m,
-                                  float *sign_out, double *partials, int32_t n, int32_t h,
-                                  int32_t w, int64_t ld, int64_t img_stride, cudaStream_t st);
-cudaError_t launch_adjoint_gather(int bnd, const float *g_in, const uint8_t *m, float *g_out,
-                                  float *grad_f, const float *lam, float step, float c_self,
-                                  float c_nb, int first, int last, int32_t n, int32_t h, int32_t w,
-                                  int64_t ld, int64_t img_stride, cudaStream_t st);
+cudaError_t launch_adjoint_step(int bnd, const float *U, const float *g_in, float *g_out,
+                                float *grad_f, double *partials, const float *lam, float step,
+                                int first, int last, int32_t n, int32_t h, int32_t w, int64_t ld,
+                                int64_t img_stride, cudaStream_t st);
+cudaError_t launch_energy_grad(int bnd, const float *U, float *grad, int32_t h, int32_t w, int64_t ld,
+                               cudaStream_t st);
 cudaError_t launch_lambda_grad(const double *partials, int32_t K, int32_t n, int64_t nb, float step,
                                float *grad_lambda, cudaStream_t st);
 

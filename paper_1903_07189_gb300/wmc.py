@@ -74,8 +74,7 @@ SIGNATURES = {
                                     _vp]),
     "wmc_unrolled_backward": (_i32, [_vp, _vp, _f32, _i32, _i32, _i32, _i32, _i32, _i64, _i32, _vp, _vp, _vp,
                                      _vp, _sz, _vp]),
-    "wmc_energy_grad_workspace_size": (_sz, [_i32, _i32, _i64]),
-    "wmc_energy_grad": (_i32, [_vp, _vp, _i32, _i32, _i64, _i32, _vp, _sz, _vp]),
+    "wmc_energy_grad": (_i32, [_vp, _vp, _i32, _i32, _i64, _i32, _vp]),
     "wmc_status_string": (ctypes.c_char_p, [_i32]),
     "wmc_last_error": (ctypes.c_char_p, []),
     "wmc_version": (_i32, []),
@@ -425,10 +424,8 @@ def energy_grad(u: torch.Tensor, boundary: str = "replicate", out: torch.Tensor 
     po, h2, w2, ld2 = _img(out, "out")
     if (h2, w2, ld2) != (h, w, ld):
         raise ValueError("out must match u in shape and pitch")
-    lib = load()
-    ws = _workspace(lib.wmc_energy_grad_workspace_size(h, w, ld), u.device)
-    _check(lib.wmc_energy_grad(p, po, h, w, ld, BOUNDARY[boundary], ws.data_ptr(), ws.numel(),
-                               _stream(u.device)), "wmc_energy_grad")
+    _check(load().wmc_energy_grad(p, po, h, w, ld, BOUNDARY[boundary], _stream(u.device)),
+           "wmc_energy_grad")
     return out
 
 

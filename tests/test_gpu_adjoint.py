@@ -50,6 +50,40 @@ def trajectory_gap(f, lam, step, K, bnd):
     return min(gaps)
 
 
+def gap_map(u, bnd):
+    """Per pixel: |runner-up| - |winner| of the FP64 candidates, and the winner's value."""
+    hw, cand, index = oracle.wmc_eval(u, bnd, candidates=True)
+    mag = np.abs(cand)
+    idx = (index.astype(np.int64) - 1)[..., None]
+    win = np.take_along_axis(mag, idx, axis=2)[..., 0]
+    mag_o = mag.copy()
+    np.put_along_axis(mag_o, idx, np.inf, axis=2)
+    return mag_o.min(axis=2) - win, hw
+
+
+def dilate(mask, r):
+    """Chebyshev dilation of a boolean image by r pixels."""
+    out = mask.copy()
+    h, w = mask.shape
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            src = mask[max(-dy, 0):h - max(dy, 0), max(-dx, 0):w - max(dx, 0)]
+            out[max(dy, 0):h - max(-dy, 0), max(dx, 0):w - max(-dx, 0)] |= src
+    return out
+
+
+def unrolled_ambiguity(f, lam, step, K, bnd):
+    """Pixels of dL/df that a near-tie at some step may touch: a selection at step t enters
+    g^t within 1 pixel and reaches grad_f within t + 1 more (one pixel per earlier step)."""
+    u = f.astype(np.float64)
+    mask = np.zeros(f.shape, dtype=bool)
+    for t in range(K):
+        gap, _ = gap_map(u, bnd)
+        mask |= dilate(gap <= GAP, t + 1)
+        u = oracle.denoise(f.astype(np.float64), lam, step, 1, bnd, u0=u)
+    return mask
+
+
 def find_clean_seed(h, w, lam, step, K, bnd, start):
     for seed in range(start, start + 40):
         f = image(h, w, seed)
@@ -85,6 +119,25 @@ def test_unrolled_gradient_matches_oracle(bnd, shape):
     assert abs(float(gl[0]) - dl) <= 1e-4 * abs(dl) + 1e-9, (seed, float(gl[0]), dl)
     loss_gpu = float(((u[0].double().cpu().numpy() - clean) ** 2).mean())
     assert abs(loss_gpu - loss) <= 1e-5 * loss
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+@pytest.mark.parametrize("shape", [(70, 140), (97, 65)])
+def test_unrolled_gradient_multi_tile(bnd, shape):
+    """Several 64 x 32 adjoint tiles with ragged edges: away from the pixels a near-tie can
+    touch, dL/df matches to FP32 accuracy; dL/dlambda (a sum over every pixel) to 1e-3."""
+    h, w = shape
+    lam, step, K = 1.0, 0.25, 4
+    f = image(h, w, seed=h + w)
+    clean = synth.make_image(h, w, seed=h + w, sigma=0.0, dtype=np.float32)
+    mask = unrolled_ambiguity(f, lam, step, K, bnd)
+    assert mask.mean() < 0.2, mask.mean()
+    loss, dl, df = oracle.unrolled_grad(f, clean, lam, step, K, bnd)
+    _, gf, gl = gpu_grads([f], [lam], step, K, 3, bnd, clean=[clean])
+    gf = gf[0].cpu().double().numpy()
+    err = np.abs(gf - df)[~mask]
+    assert err.max() <= 1e-5 * np.abs(df).max() + 1e-9, err.max()
+    assert abs(float(gl[0]) - dl) <= 1e-3 * abs(dl), (float(gl[0]), dl)
 
 
 def test_unrolled_gradient_larger_case_near_ties_local():
@@ -180,19 +233,17 @@ def test_autograd_function_matches_abi_and_finite_difference():
 
 
 @pytest.mark.parametrize("bnd", ["replicate", "zero"])
-@pytest.mark.parametrize("shape", [(30, 30), (17, 45)])
+@pytest.mark.parametrize("shape", [(30, 30), (17, 45), (100, 200), (257, 131)])
 def test_energy_grad_matches_oracle(bnd, shape):
-    for seed in range(200, 240):
-        u = image(*shape, seed=seed)
-        u64 = u.astype(np.float64)
-        # the selection and the sign of H^w must both be unambiguous in FP32
-        if min_gap(u64, bnd) > GAP and np.abs(oracle.wmc_eval(u64, bnd)).min() > GAP:
-            break
-    else:
-        raise AssertionError("no seed without near-ties found")
-    ref = oracle.energy_grad(u.astype(np.float64), bnd)
+    """Exact (FP32 rounding) wherever no pixel next to q has a near-tie or a near-zero H^w."""
+    u = image(*shape, seed=200 + shape[0])
+    u64 = u.astype(np.float64)
+    gap, hw = gap_map(u64, bnd)
+    mask = dilate((gap <= GAP) | (np.abs(hw) <= GAP), 1)
+    assert mask.mean() < 0.05, mask.mean()
+    ref = oracle.energy_grad(u64, bnd)
     got = wmc().energy_grad(torch.from_numpy(u).to(DEV), bnd).cpu().double().numpy()
-    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(got[~mask], ref[~mask], rtol=0, atol=1e-6)
 
 
 def test_energy_grad_constant_image_is_zero():
