@@ -218,13 +218,16 @@ def run_gpu(args):
     n_launch = math.ceil(iters / T)
 
     def step():
+        v0.record()
         wmc.eval(f, out=hw)
+        v1.record()
         e0.record()
         wmc.denoise(f, LAM, STEP, iters, out=out, steps_per_launch=T, workspace=ws)
         e1.record()
         wmc.energy(out, f, None, out=energies, workspace=ews)
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         step()
@@ -239,12 +242,14 @@ def run_gpu(args):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     d0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     d1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with Clocks(local) as clk:
         barrier()
         wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
-            e0, e1 = d0[k], d1[k]
+            e0, e1, v0, v1 = d0[k], d1[k], ev0[k], ev1[k]
             starts[k].record()
             step()
             ends[k].record()
@@ -253,6 +258,7 @@ def run_gpu(args):
     clocks = clk.summary()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     den_ms = [a.elapsed_time(b) for a, b in zip(d0, d1)]
+    eval_ms = statistics.median(a.elapsed_time(b) for a, b in zip(ev0, ev1))
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
     value = job_rate(H * W * iters * args.steps, world, total_ms)
@@ -272,6 +278,9 @@ def run_gpu(args):
                     "peak_kind": f"FP32 FMA pipe lane-operations (an FMA counts once): {SMS} SMs x {FP32_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz "
                                  "(unit counts and the sampled clock)",
                     "algorithmic_ops_per_px_iter": FMA_OPS_PER_PX_ITER, "launch_ms": launch_ms,
+                    # the same iterations unblocked would move 12 B per pixel-iteration
+                    "unblocked_equivalent": {"gbs": value * BYTES_PER_PX_LAUNCH,
+                                             "frac": value * BYTES_PER_PX_LAUNCH / peak},
                     "hbm": {"achieved": hbm_achieved, "peak": peak, "unit": "GB/s", "frac": hbm_achieved / peak,
                             "peak_kind": peak_kind}}
     else:
@@ -312,6 +321,10 @@ def run_gpu(args):
                 "config": {"workload": WORKLOAD, "l2": "flushed before each timed step (256 MiB write)",
                            "steps_per_launch": T, "iters": iters, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "eval": {"ms": eval_ms, "gpix_s": H * W / (eval_ms * 1e-3) / 1e9,
+                         "hbm_gbs": 8 * H * W / (eval_ms * 1e-3) / 1e9,
+                         "hbm_frac": 8 * H * W / (eval_ms * 1e-3) / 1e9 / peak,
+                         "kernel": "wmc::stream_kernel (eval), 8 B per pixel"},
                 "gpu_launches": args.steps * (2 + n_launch), "clocks": clocks,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
@@ -395,21 +408,11 @@ def run_batch(args):
     lams = [l for _, l in params]
     steps = [0.5 / (1 + l) for l in lams]
     px = sum(h * w for h, w in sizes)
-    Ts = [args.steps_per_launch] if args.steps_per_launch else [2, 3, 4, 6]
-    # steps-per-launch chosen by timing a short run of each candidate on this batch
-    tune = {}
-    for T in Ts:
-        b = wmc.Batch(fs, lams, steps, steps_per_launch=T)
-        b.run(2 * T)
-        torch.cuda.synchronize()
-        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        b.run(12 * T)
-        e.record()
-        torch.cuda.synchronize()
-        tune[T] = a.elapsed_time(e) / (12 * T)
-        del b
-    T = min(tune, key=tune.get)
+    # steps per launch picked by the library's autotuner (times each candidate on this batch)
+    if args.steps_per_launch:
+        T, tune = args.steps_per_launch, {}
+    else:
+        T, tune = wmc.batch_autotune(fs, lams, steps)
     b = wmc.Batch(fs, lams, steps, steps_per_launch=T)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())

@@ -230,6 +230,24 @@ wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t
                                  int32_t iters, wmc_boundary_t bnd, void *workspace,
                                  size_t workspace_bytes, wmc_stream_t stream);
 
+/*
+ * wmc_batch_autotune: picks the steps per launch for a batch by timing it.  For each candidate
+ * (NULL = {2, 3, 4, 5, 6, 8}) it plans the batch, runs it once untimed, then runs about
+ * trial_iters iterations (rounded up to whole launches) between two CUDA events, and keeps the
+ * fastest per iteration.  ms_per_iter (optional, host, n_candidates floats) receives the timings.
+ * The trials write the images' outputs (u) and synchronise `stream`; do not capture this call.
+ *   workspace: device, >= wmc_batch_autotune_workspace_size() bytes (the largest plan).
+ *   best: host, receives {steps_per_launch, tile = 0} for wmc_batch_plan.
+ * Errors: as wmc_batch_plan; WMC_ERR_INVALID_ARG for candidates outside 1..8, n_candidates
+ *         outside 1..64 or trial_iters < 1; WMC_ERR_TIMEOUT if a trial reported a timed-out load.
+ */
+size_t wmc_batch_autotune_workspace_size(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype);
+
+wmc_status_t wmc_batch_autotune(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                                wmc_boundary_t bnd, const int32_t *candidates, int32_t n_candidates,
+                                int32_t trial_iters, void *workspace, size_t workspace_bytes,
+                                wmc_config_t *best, float *ms_per_iter, wmc_stream_t stream);
+
 /* ------------------------------------------------------------------------------------------
  * wmc_denoise_l1: the L1-fidelity model min_U ||U - f||_1 + lambda R(U) solved by the primal-dual
  * iteration of Sec. V-C with A = I (b eliminated):

@@ -799,6 +799,85 @@ wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t
     return wmc_batch_run(&plan, iters, stream);
 }
 
+size_t wmc_batch_autotune_workspace_size(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype) {
+    size_t best = 0;
+    for (int T = 1; T <= wmc::kMaxSteps; ++T) {
+        wmc_config_t c{T, 0};
+        const size_t b = wmc_batch_workspace_size(imgs, n, dtype, &c);
+        if (b == 0) return 0;
+        best = b > best ? b : best;
+    }
+    return best;
+}
+
+wmc_status_t wmc_batch_autotune(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                                wmc_boundary_t bnd, const int32_t *candidates, int32_t n_candidates,
+                                int32_t trial_iters, void *workspace, size_t workspace_bytes,
+                                wmc_config_t *best, float *ms_per_iter, wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    static const int32_t kDefaultCandidates[] = {2, 3, 4, 5, 6, 8};
+    if (!best) return fail(WMC_ERR_INVALID_ARG, "best is NULL");
+    if (!candidates) {
+        candidates = kDefaultCandidates;
+        n_candidates = (int32_t)(sizeof kDefaultCandidates / sizeof kDefaultCandidates[0]);
+    }
+    if (n_candidates < 1 || n_candidates > 64)
+        return fail(WMC_ERR_INVALID_ARG, "n_candidates must be 1..64 (got %d)", n_candidates);
+    for (int32_t k = 0; k < n_candidates; ++k)
+        if (candidates[k] < 1 || candidates[k] > wmc::kMaxSteps)
+            return fail(WMC_ERR_INVALID_ARG, "candidate %d: steps per launch must be 1..%d (got %d)", k,
+                        wmc::kMaxSteps, candidates[k]);
+    if (trial_iters < 1) return fail(WMC_ERR_INVALID_ARG, "trial_iters must be >= 1 (got %d)", trial_iters);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return cuda_fail(e, "event create");
+    }
+    float best_ms = 0.0f;
+    int best_T = 0;
+    wmc_status_t s = WMC_OK;
+    for (int32_t k = 0; k < n_candidates && s == WMC_OK; ++k) {
+        const wmc_config_t c{candidates[k], 0};
+        wmc_batch_t plan;
+        s = wmc_batch_plan(imgs, n, dtype, bnd, &c, workspace, workspace_bytes, &plan, stream);
+        if (s != WMC_OK) break;
+        // one untimed run (first-launch costs), then the timed one; each covers whole launches
+        const int it = ((trial_iters + c.steps_per_launch - 1) / c.steps_per_launch) * c.steps_per_launch;
+        if ((s = wmc_batch_run(&plan, c.steps_per_launch, stream)) != WMC_OK) break;
+        if ((e = cudaEventRecord(a, st)) != cudaSuccess) { s = cuda_fail(e, "event record"); break; }
+        if ((s = wmc_batch_run(&plan, it, stream)) != WMC_OK) break;
+        if ((e = cudaEventRecord(b, st)) != cudaSuccess || (e = cudaEventSynchronize(b)) != cudaSuccess) {
+            s = cuda_fail(e, "event sync");
+            break;
+        }
+        float ms = 0.0f;
+        if ((e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) { s = cuda_fail(e, "event time"); break; }
+        const float per_iter = ms / (float)it;
+        if (ms_per_iter) ms_per_iter[k] = per_iter;
+        if (best_T == 0 || per_iter < best_ms) {
+            best_ms = per_iter;
+            best_T = c.steps_per_launch;
+        }
+        const unsigned int *status = static_cast<const unsigned int *>(workspace);
+        unsigned int hs = 0;
+        if ((e = cudaMemcpy(&hs, status, sizeof hs, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            s = cuda_fail(e, "read status");
+            break;
+        }
+        if (hs) s = fail(WMC_ERR_TIMEOUT, "a tile load timed out during the trial of %d steps per launch",
+                         c.steps_per_launch);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (s != WMC_OK) return s;
+    best->steps_per_launch = best_T;
+    best->tile = 0;
+    return WMC_OK;
+}
+
 size_t wmc_denoise_l1_workspace_size(int32_t h, int32_t w, int64_t ld) {
     if (h < 0 || w < 0 || ld < w) return 0;
     return kStatusBytes + 2 * image_bytes(h, ld, WMC_F32);

@@ -66,6 +66,9 @@ SIGNATURES = {
                               ctypes.POINTER(BatchPlan), _vp]),
     "wmc_batch_run": (_i32, [ctypes.POINTER(BatchPlan), _i32, _vp]),
     "wmc_denoise_batched": (_i32, [ctypes.POINTER(Image), _i32, _i32, _i32, _i32, _vp, _sz, _vp]),
+    "wmc_batch_autotune_workspace_size": (_sz, [ctypes.POINTER(Image), _i32, _i32]),
+    "wmc_batch_autotune": (_i32, [ctypes.POINTER(Image), _i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32), _i32,
+                                  _i32, _vp, _sz, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_float), _vp]),
     "wmc_denoise_l1_workspace_size": (_sz, [_i32, _i32, _i64]),
     "wmc_denoise_l1": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i64, _f32, _f32, _f32, _i32, _i32, _vp, _sz,
                               _vp]),
@@ -291,6 +294,39 @@ class Batch:
 
     def check_status(self):
         check_status(self.workspace)
+
+
+def batch_autotune(fs, lams, steps=None, outs=None, boundary: str = "replicate", candidates=(2, 3, 4, 5, 6, 8),
+                   trial_iters: int = 24):
+    """Time the batch at each candidate steps-per-launch (wmc_batch_autotune); returns
+    (best steps per launch, {candidate: ms per iteration}).  Writes the outputs."""
+    if not fs:
+        raise ValueError("empty batch")
+    dt = fs[0].dtype
+    if steps is None:
+        steps = [default_step(l) for l in lams]
+    if outs is None:
+        outs = [torch.empty_strided(f.shape, f.stride(), dtype=f.dtype, device=f.device) for f in fs]
+    n = len(fs)
+    imgs = (Image * n)()
+    for i, (f, u, l, st) in enumerate(zip(fs, outs, lams, steps)):
+        pf, h, w, ld = _img(f, f"fs[{i}]")
+        pu, h2, w2, ld2 = _img(u, f"outs[{i}]")
+        if (h2, w2, ld2) != (h, w, ld) or f.dtype != dt or u.dtype != dt:
+            raise ValueError(f"image {i}: f and out must share shape, pitch and dtype")
+        imgs[i] = Image(pf, pu, h, w, ld, float(l), float(st))
+    lib = load()
+    size = lib.wmc_batch_autotune_workspace_size(imgs, n, DTYPES[dt])
+    if size == 0:
+        raise WMCError(1, "wmc_batch_autotune_workspace_size", "invalid batch")
+    ws = _workspace(size, fs[0].device)
+    cand = (ctypes.c_int32 * len(candidates))(*candidates)
+    times = (ctypes.c_float * len(candidates))()
+    best = Config(0, 0)
+    _check(lib.wmc_batch_autotune(imgs, n, DTYPES[dt], BOUNDARY[boundary], cand, len(candidates), int(trial_iters),
+                                  ws.data_ptr(), ws.numel(), ctypes.byref(best), times, _stream(fs[0].device)),
+           "wmc_batch_autotune")
+    return best.steps_per_launch, {c: float(t) for c, t in zip(candidates, times)}
 
 
 def denoise_batched(fs, lams, steps=None, iters: int = 100, boundary: str = "replicate", outs=None,

@@ -210,3 +210,18 @@ def test_l1_validation(lib):
     assert call(f, None, u, d, 1.0, 0.1, 0.1, 3, nbytes=need - 1) == WORKSPACE
     assert call(f, None, u, d, 1.0, 0.1, 0.1, 3, ws_=ctypes.c_void_p(0x10000008)) == WORKSPACE
     assert call(f, None, u, d, 1.0, 0.1, 0.1, 3, ws_=ctypes.c_void_p(0x300000)) == ALIAS
+
+
+def test_batch_autotune_validation(lib):
+    imgs = (wmc.Image * 1)()
+    imgs[0] = wmc.Image(0x100000, 0x300000, 8, 8, 8, 1.0, 0.25)
+    need = lib.wmc_batch_autotune_workspace_size(imgs, 1, 0)
+    assert need > 0
+    best = wmc.Config(0, 0)
+    ws = ctypes.c_void_p(0x10000000)
+    bad = (ctypes.c_int32 * 2)(2, 9)
+    assert lib.wmc_batch_autotune(imgs, 1, 0, 0, bad, 2, 8, ws, need, ctypes.byref(best), None, None) == INVALID
+    good = (ctypes.c_int32 * 1)(4)
+    assert lib.wmc_batch_autotune(imgs, 1, 0, 0, good, 0, 8, ws, need, ctypes.byref(best), None, None) == INVALID
+    assert lib.wmc_batch_autotune(imgs, 1, 0, 0, good, 1, 0, ws, need, ctypes.byref(best), None, None) == INVALID
+    assert lib.wmc_batch_autotune(imgs, 1, 0, 0, good, 1, 8, ws, need, None, None, None) == INVALID

@@ -96,3 +96,13 @@ def test_batch_alias_rejected():
     with pytest.raises(wmc().WMCError) as e:
         wmc().Batch(fs, lams, steps, outs=outs)
     assert e.value.status == 2
+
+
+def test_autotune_picks_a_candidate_and_the_plan_matches_single_images():
+    fs, lams, steps = batch_inputs(seed=4)
+    T, times = wmc().batch_autotune(fs, lams, steps, candidates=(2, 4, 8), trial_iters=8)
+    assert T in (2, 4, 8)
+    assert all(t > 0 for t in times.values()) and times[T] == min(times.values())
+    outs = wmc().denoise_batched(fs, lams, steps, iters=9, steps_per_launch=T)
+    for f, l, st, o in zip(fs, lams, steps, outs):
+        assert torch.equal(o, wmc().denoise(f, l, st, 9, steps_per_launch=T))
