@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the CPU-baseline l
 benchmark use this package; the CUDA library never does, and this package never imports the
 library.  The arithmetic lives in ``wmc_oracle.c`` (plain C, FP64, written from the paper's
 definitions: the half-window kernels of Sec. IV-B, Eq. conv, Eq. act, the gradient flow of
-Sec. V-B, Eq. MCF, the primal-dual update of Sec. V-C and the regulariser of Eq. wmcr).  This
+Sec. V-B, Eq. MCF, the primal-dual update of Sec. V-C, the regulariser of Eq. wmcr, and the
+conventional finite-difference discretisation of Eq. rhs that Sec. V-D compares against).  This
 module only compiles it with gcc and marshals numpy arrays in and out.
 """
 from __future__ import annotations
@@ -64,6 +65,8 @@ def _load():
             lib.oracle_wmc_l1_primal_dual.argtypes = [_dp, _dp, _dp, _dp, _dp, i32, i32, i64, d, d, d, i32,
                                                       ctypes.c_int]
             lib.oracle_energy_grad.argtypes = [_dp, i32, i32, ctypes.c_int, _dp]
+            lib.oracle_fd_eval.argtypes = [_dp, _dp, i32, i32, i64, i64, ctypes.c_int]
+            lib.oracle_fd_flow.argtypes = [_dp, _dp, _dp, i32, i32, i64, d, d, i32, ctypes.c_int, d]
             lib.oracle_unrolled_grad.argtypes = [_dp, _dp, i32, i32, d, d, i32, ctypes.c_int, _dp, _dp, _dp]
             lib.oracle_wmc_eval_points.argtypes = [_dp, i32, i32, i64, ctypes.c_int, _ip, _ip, i64, _dp,
                                                    _dp]
@@ -262,3 +265,28 @@ def energy_grad(u, boundary="replicate"):
     if rc:
         raise ValueError(f"oracle_energy_grad failed ({rc})")
     return g
+
+
+def fd_eval(u, boundary="replicate"):
+    """Finite-difference WMC of Eq. rhs (central differences; 0 where the gradient is zero)."""
+    u = _f64(u)
+    h, w = u.shape
+    hw = np.zeros((h, w))
+    rc = _load().oracle_fd_eval(_ptr(u), _ptr(hw), h, w, w, w, _bnd(boundary))
+    if rc:
+        raise ValueError(f"oracle_fd_eval failed ({rc})")
+    return hw
+
+
+def fd_flow(f, lam: float, step: float, iters: int, boundary="replicate", mu: float = 1.0, u0=None):
+    """`iters` Jacobi steps of U <- U + step*(lam*H_fd(U) - mu*(U - f)) (f None: mean-curvature flow)."""
+    ref = _f64(f if f is not None else u0)
+    h, w = ref.shape
+    f_ = None if f is None else _f64(f)
+    u0_ = None if u0 is None else _f64(u0)
+    out = np.zeros((h, w))
+    rc = _load().oracle_fd_flow(_ptr(f_), _ptr(u0_), _ptr(out), h, w, w, float(lam), float(step), int(iters),
+                                _bnd(boundary), float(mu))
+    if rc:
+        raise ValueError(f"oracle_fd_flow failed ({rc})")
+    return out

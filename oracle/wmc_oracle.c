@@ -30,6 +30,9 @@
  *     of the scaled dual d, then the U step with lambda H^w - (2 d^{t+1} - d^t)/alpha).
  *   - storage rounding: FP64 -> bfloat16 / binary16 round-to-nearest-even, taken straight from
  *     the FP64 bit pattern (no double rounding through FP32).
+ *   - the conventional discretisation the paper compares against (Sec. V-D): Eq. rhs,
+ *     H = Laplacian(U) - (U_y^2 U_yy + 2 U_x U_y U_xy + U_x^2 U_xx) / (U_x^2 + U_y^2), with
+ *     central differences (unit spacing, rows downwards) and the same boundary rules.
  */
 #include <math.h>
 #include <stdint.h>
@@ -436,5 +439,74 @@ int oracle_energy_grad(const double *u, int32_t h, int32_t w, int bnd, double *g
                     grad[(size_t)qy * w + qx] += s * (H12[m][r][c] / 12.0);
                 }
         }
+    return 0;
+}
+
+/*
+ * Conventional finite-difference WMC of Eq. rhs, the comparator of Sec. V-D: at every pixel
+ *   U_x = (E - W)/2, U_y = (S - N)/2, U_xx = E - 2C + W, U_yy = S - 2C + N,
+ *   U_xy = ((SE - NE) - (SW - NW))/4   (y runs downwards, so S is row y+1),
+ *   H = (U_xx + U_yy) - (U_y^2 U_yy + 2 U_x U_y U_xy + U_x^2 U_xx) / (U_x^2 + U_y^2),
+ * and H = 0 where the central-difference gradient is exactly zero (the |grad U| factor of
+ * Eq. wmc vanishes there).  Neighbours outside the image follow `bnd`.
+ */
+int oracle_fd_eval(const double *u, double *hw, int32_t h, int32_t w, int64_t ld_u, int64_t ld_hw,
+                   int bnd) {
+    if (check_dims(h, w, ld_u) || check_dims(h, w, ld_hw)) return 1;
+#pragma omp parallel for schedule(static) num_threads(g_threads)
+    for (int32_t y = 0; y < h; ++y)
+        for (int32_t x = 0; x < w; ++x) {
+            const double C = sample(u, h, w, ld_u, y, x, bnd);
+            const double N = sample(u, h, w, ld_u, y - 1, x, bnd);
+            const double S = sample(u, h, w, ld_u, y + 1, x, bnd);
+            const double W = sample(u, h, w, ld_u, y, x - 1, bnd);
+            const double E = sample(u, h, w, ld_u, y, x + 1, bnd);
+            const double NW = sample(u, h, w, ld_u, y - 1, x - 1, bnd);
+            const double NE = sample(u, h, w, ld_u, y - 1, x + 1, bnd);
+            const double SW = sample(u, h, w, ld_u, y + 1, x - 1, bnd);
+            const double SE = sample(u, h, w, ld_u, y + 1, x + 1, bnd);
+            const double ux = (E - W) / 2.0, uy = (S - N) / 2.0;
+            const double uxx = E - 2.0 * C + W, uyy = S - 2.0 * C + N;
+            const double uxy = ((SE - NE) - (SW - NW)) / 4.0;
+            const double g2 = ux * ux + uy * uy;
+            double H = 0.0;
+            if (g2 > 0.0)
+                H = (uxx + uyy) - (uy * uy * uyy + 2.0 * ux * uy * uxy + ux * ux * uxx) / g2;
+            hw[(int64_t)y * ld_hw + x] = H;
+        }
+    return 0;
+}
+
+/* The flow of oracle_wmc_flow with the finite-difference H of oracle_fd_eval (FP64 storage). */
+int oracle_fd_flow(const double *f, const double *u0, double *u_out, int32_t h, int32_t w,
+                   int64_t ld, double lambda, double step, int32_t iters, int bnd, double mu) {
+    if (check_dims(h, w, ld) || iters < 0) return 1;
+    if (!u0 && !f) return 1;
+    if (mu != 0.0 && !f) return 1;
+    if (h == 0 || w == 0) return 0;
+    size_t n = (size_t)h * (size_t)w;
+    double *U = (double *)malloc(n * sizeof(double));
+    double *V = (double *)malloc(n * sizeof(double));
+    double *Hw = (double *)malloc(n * sizeof(double));
+    if (!U || !V || !Hw) {
+        free(U); free(V); free(Hw);
+        return 2;
+    }
+    const double *src = u0 ? u0 : f;
+    for (int32_t y = 0; y < h; ++y)
+        for (int32_t x = 0; x < w; ++x) U[(size_t)y * w + x] = src[(int64_t)y * ld + x];
+    for (int32_t t = 0; t < iters; ++t) {
+        oracle_fd_eval(U, Hw, h, w, w, w, bnd);
+        for (int32_t y = 0; y < h; ++y)
+            for (int32_t x = 0; x < w; ++x) {
+                const size_t p = (size_t)y * w + x;
+                const double fv = f ? f[(int64_t)y * ld + x] : 0.0;
+                V[p] = U[p] + step * (lambda * Hw[p] - mu * (U[p] - fv));
+            }
+        double *tmp = U; U = V; V = tmp;
+    }
+    for (int32_t y = 0; y < h; ++y)
+        for (int32_t x = 0; x < w; ++x) u_out[(int64_t)y * ld + x] = U[(size_t)y * w + x];
+    free(U); free(V); free(Hw);
     return 0;
 }

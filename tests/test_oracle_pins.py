@@ -481,3 +481,82 @@ def test_energy_grad_impulse_by_hand():
         want[y, x] = -1 / 6
     want[2, 3] = -1 / 3
     np.testing.assert_allclose(g, want, atol=1e-15)
+
+
+# ------------------------------------------- conventional finite-difference WMC (Eq. rhs)
+def _grid(h, w):
+    y, x = np.mgrid[0:h, 0:w].astype(np.float64)
+    return y, x
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_fd_straight_level_lines_give_zero(bnd):
+    """U depending on x alone has straight level lines: curvature 0 at every interior pixel
+    (and, under REPLICATE, at the border too)."""
+    y, x = _grid(12, 17)
+    u = np.sin(0.4 * x) + 0.1 * x * x
+    hw = oracle.fd_eval(u, bnd)
+    inner = hw[1:-1, 1:-1] if bnd == "zero" else hw
+    np.testing.assert_allclose(inner, 0.0, atol=1e-12)
+
+
+def test_fd_paraboloid_is_two():
+    """U = (x-cx)^2 + (y-cy)^2: central differences are exact on quadratics, grad = 2(x-cx, y-cy),
+    Laplacian 4, normal second derivative 2, so H = 2 wherever the gradient is non-zero; the
+    centre (zero gradient) gives 0 by definition."""
+    y, x = _grid(11, 13)
+    u = (x - 6.0) ** 2 + (y - 5.0) ** 2
+    hw = oracle.fd_eval(u, "replicate")
+    expect = np.full(u.shape, 2.0)
+    expect[5, 6] = 0.0
+    np.testing.assert_allclose(hw[1:-1, 1:-1], expect[1:-1, 1:-1], atol=1e-12)
+
+
+def test_fd_saddle_closed_form():
+    """U = (x-a)(y-b): U_x = y-b, U_y = x-a, U_xy = 1, U_xx = U_yy = 0, so
+    H = -2 (x-a)(y-b) / ((x-a)^2 + (y-b)^2)."""
+    y, x = _grid(9, 10)
+    X, Y = x - 4.5, y - 3.5
+    hw = oracle.fd_eval(X * Y, "replicate")
+    expect = -2.0 * X * Y / (X * X + Y * Y)
+    np.testing.assert_allclose(hw[1:-1, 1:-1], expect[1:-1, 1:-1], atol=1e-12)
+
+
+def test_fd_gaussian_matches_continuous_wmc():
+    """A radial Gaussian g(r) = exp(-r^2 / (2 s^2)) has circular level lines; Eq. wmc gives
+    |grad U| * div(grad U / |grad U|) = g'(r) / r = -g / s^2.  Central differences converge to it
+    at second order in 1/s."""
+    s = 12.0
+    y, x = _grid(81, 81)
+    r2 = (x - 40.0) ** 2 + (y - 40.0) ** 2
+    g = np.exp(-r2 / (2 * s * s))
+    hw = oracle.fd_eval(g, "replicate")
+    cont = -g / (s * s)
+    sel = (r2 > 4.0) & (r2 < (2.5 * s) ** 2)
+    rel = np.abs(hw[sel] - cont[sel]).max() / np.abs(cont[sel]).max()
+    assert rel < 0.02, rel
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_fd_rotation_and_flip_equivariance(bnd):
+    u = synth.make_image(15, 15, seed=61, sigma=0.1, dtype=np.float64)
+    hw = oracle.fd_eval(u, bnd)
+    np.testing.assert_allclose(oracle.fd_eval(np.rot90(u).copy(), bnd), np.rot90(hw), atol=1e-12)
+    np.testing.assert_allclose(oracle.fd_eval(u[:, ::-1].copy(), bnd), hw[:, ::-1], atol=1e-12)
+    np.testing.assert_allclose(oracle.fd_eval(u.T.copy(), bnd), hw.T, atol=1e-12)
+
+
+def test_fd_flow_without_regulariser_relaxes_to_f():
+    """lambda = 0: U^t = f + (1 - step)^t (U^0 - f) exactly (pins mu, the sign of the data term
+    and the step count)."""
+    f = synth.make_image(8, 9, seed=62, sigma=0.1, dtype=np.float64)
+    u0 = f + 0.25
+    out = oracle.fd_flow(f, 0.0, 0.3, 5, u0=u0)
+    np.testing.assert_allclose(out, f + 0.7 ** 5 * 0.25, atol=1e-14)
+
+
+def test_fd_flow_one_step_uses_fd_operator():
+    """One mean-curvature step (f None) is U + step * lambda * H_fd(U)."""
+    u = synth.make_image(10, 12, seed=63, sigma=0.1, dtype=np.float64)
+    out = oracle.fd_flow(None, 2.0, 0.1, 1, mu=0.0, u0=u)
+    np.testing.assert_allclose(out, u + 0.2 * oracle.fd_eval(u), atol=1e-14)
