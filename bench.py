@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--steps-per-launch", type=int, default=0)
     ap.add_argument("--iters", type=int, default=ITERS, help="override (profiling runs only)")
-    ap.add_argument("--workload", default="scale", choices=["scale", "precision", "batch", "diff", "l1"],
+    ap.add_argument("--workload", default="scale", choices=["scale", "precision", "batch", "diff", "l1", "fd"],
                     help="scale: the headline 4096^2 run; precision / batch / diff: the reduced-"
                          "storage, uneven-batch and reverse-mode measurements (one JSON line "
                          "each, not the headline)")
@@ -324,7 +324,7 @@ def run_gpu(args):
                 "eval": {"ms": eval_ms, "gpix_s": H * W / (eval_ms * 1e-3) / 1e9,
                          "hbm_gbs": 8 * H * W / (eval_ms * 1e-3) / 1e9,
                          "hbm_frac": 8 * H * W / (eval_ms * 1e-3) / 1e9 / peak,
-                         "kernel": "wmc::stream_kernel (eval), 8 B per pixel"},
+                         "kernel": "wmc::stream4_kernel (eval, 4 cells per lane), 8 B per pixel"},
                 "gpu_launches": args.steps * (2 + n_launch), "clocks": clocks,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
@@ -514,6 +514,48 @@ def run_l1(args):
     return 0
 
 
+def run_fd(args):
+    """The conventional finite-difference WMC of Eq. rhs (the comparator of Sec. V-D) on the
+    4096^2 workload image: one evaluation pass (8 B per pixel) and 100 denoising iterations with
+    lambda 1, step 0.1 (one streaming launch each, 12 B per pixel-iteration)."""
+    import torch
+    from paper_1903_07189_gb300 import synth, wmc
+    dev = torch.device("cuda", 0)
+    iters = 100 if args.iters == ITERS else args.iters
+    f = torch.from_numpy(synth.scale_image(SIGMA)).to(dev)
+    hw, out = torch.empty_like(f), torch.empty_like(f)
+    ws = torch.empty(wmc.load().wmc_denoise_workspace_size(H, W, W, 0), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(3, args.warmup)):
+        wmc.eval_fd(f, out=hw)
+        wmc.denoise_fd(f, 1.0, 0.1, iters, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    te, tf = [], []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        wmc.eval_fd(f, out=hw)
+        b.record()
+        wmc.denoise_fd(f, 1.0, 0.1, iters, out=out, workspace=ws)
+        c.record()
+        torch.cuda.synchronize()
+        te.append(a.elapsed_time(b))
+        tf.append(b.elapsed_time(c))
+    peak, peak_kind = peaks()
+    me, mf = statistics.median(te), statistics.median(tf)
+    line = {"workload": "fd", "metric": METRIC, "unit": UNIT, "config": {
+                "image": WORKLOAD.split(":")[0], "iters": iters, "lambda": 1.0, "step": 0.1, "dtype": "f32",
+                "l2": "flushed before each timed run"},
+            "results": {"eval_gpix_s": H * W / (me * 1e-3) / 1e9, "eval_ms": me,
+                        "eval_hbm_frac": 8 * H * W / (me * 1e-3) / 1e9 / peak,
+                        "flow_gpix_iter_s": H * W * iters / (mf * 1e-3) / 1e9, "flow_ms": mf,
+                        "flow_hbm_frac": 12 * H * W * iters / (mf * 1e-3) / 1e9 / peak,
+                        "peak_gbs": peak, "peak_kind": peak_kind}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_diff(args):
     """Training through the unrolled flow: 32 images of 512 x 512 (seed 2000+i, 8 bumps + 4
     shapes, sigma 0.05), one learnable lambda per image (init 1.0), K = 50 denoising steps with
@@ -593,6 +635,8 @@ def main():
         return run_diff(args)
     if args.workload == "l1":
         return run_l1(args)
+    if args.workload == "fd":
+        return run_fd(args)
     return run_gpu(args)
 
 

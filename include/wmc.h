@@ -249,6 +249,25 @@ wmc_status_t wmc_batch_autotune(const wmc_image_t *imgs, int32_t n, wmc_dtype_t 
                                 wmc_config_t *best, float *ms_per_iter, wmc_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------
+ * The conventional discretisation the paper compares its scheme with (Sec. V-D): Eq. rhs,
+ *   H = (U_xx + U_yy) - (U_y^2 U_yy + 2 U_x U_y U_xy + U_x^2 U_xx) / (U_x^2 + U_y^2),
+ * with central differences of unit spacing (U_x = (E - W)/2, U_xy = ((SE - NE) - (SW - NW))/4,
+ * rows downwards) and H = 0 where the central-difference gradient is exactly zero.
+ *   wmc_eval_fd: as wmc_eval, with this H.
+ *   wmc_denoise_fd: as wmc_denoise (f NULL = mean-curvature flow), with this H and one streaming
+ *   launch per iteration; workspace as wmc_denoise_workspace_size().
+ * Errors: as wmc_eval / wmc_denoise.
+ */
+wmc_status_t wmc_eval_fd(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_u,
+                         int64_t ld_hw, wmc_dtype_t dtype, wmc_boundary_t bnd,
+                         wmc_stream_t stream);
+
+wmc_status_t wmc_denoise_fd(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
+                            wmc_dtype_t dtype, float lambda, float step, int32_t iters,
+                            wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
+                            wmc_stream_t stream);
+
+/* ------------------------------------------------------------------------------------------
  * wmc_denoise_l1: the L1-fidelity model min_U ||U - f||_1 + lambda R(U) solved by the primal-dual
  * iteration of Sec. V-C with A = I (b eliminated):
  *   r = U^t - f + d^t;  d^{t+1} = clip(r, -alpha, alpha);

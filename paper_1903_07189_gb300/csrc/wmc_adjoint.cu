@@ -423,9 +423,14 @@ cudaError_t launch_stack_step(int bnd, const float *u, const float *f, float *ou
     p.img_stride = img_stride;
     p.lam = lam;
     p.step = step;
+    if (n > 65535) return cudaErrorInvalidConfiguration;
+    if (quad_aligned<float>(p) && img_stride % 4 == 0) {
+        if (bnd == BND_ZERO) return launch_stream4<BND_ZERO, MODE_FLOW, true>(p, (unsigned)n, st);
+        return launch_stream4<BND_REPLICATE, MODE_FLOW, true>(p, (unsigned)n, st);
+    }
     const int64_t nb = (int64_t)((w + kStreamWarps * 64 - 1) / (kStreamWarps * 64)) *
                        ((h + kStreamRY - 1) / kStreamRY);
-    if (nb > 0x7fffffffLL || n > 65535) return cudaErrorInvalidConfiguration;
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)nb, (unsigned)n);
     const unsigned b = kStreamWarps * 32;
     if (bnd == BND_ZERO) {

@@ -162,7 +162,8 @@ size_t image_bytes(int32_t h, int64_t ld, wmc_dtype_t dtype) {
 // (first kStatusBytes) followed by one image.
 wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
                       wmc_dtype_t dtype, float lambda, float step, int32_t iters,
-                      wmc_boundary_t bnd, int steps_per_launch, void *ws, cudaStream_t st) {
+                      wmc_boundary_t bnd, int steps_per_launch, void *ws, cudaStream_t st,
+                      bool fd = false) {
     const size_t es = elem_size(dtype);
     if (!u0) u0 = f;
     if (h == 0 || w == 0) return WMC_OK;
@@ -179,10 +180,11 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return cuda_fail(e, "clear status");
 
-    const int T = steps_per_launch;
+    const int T = fd ? 1 : steps_per_launch;  // the finite-difference comparator streams
     const int nl = (iters + T - 1) / T;  // launches; the last takes the remainder
     const float mu = f ? 1.0f : 0.0f;
-    const float c_keep = 1.0f - step * mu, c_f = step * mu, c_h = step * lambda / 12.0f;
+    const float c_keep = 1.0f - step * mu, c_f = step * mu;
+    const float c_h = fd ? step * lambda : step * lambda / 12.0f;
     // Ping-pong between u and the workspace so that the last launch writes u.  When U^0
     // already lives in u, the first launch must write the workspace; if the parity then
     // ends in the workspace, one copy finishes the job.
@@ -225,7 +227,8 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
             sp.c_keep = c_keep;
             sp.c_f = c_f;
             sp.c_h = c_h;
-            e = wmc::launch_stream((int)dtype, wmc::MODE_FLOW, (int)bnd, sp, vec, st);
+            e = wmc::launch_stream((int)dtype, fd ? wmc::MODE_FD_FLOW : wmc::MODE_FLOW, (int)bnd, sp,
+                                   vec, st);
         } else {
             wmc::TileV2Params tp{};
             tp.u = src;
@@ -511,8 +514,9 @@ const char *wmc_last_error(void) { return g_last_error; }
 
 int32_t wmc_version(void) { return 100; }
 
-wmc_status_t wmc_eval(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_u, int64_t ld_hw,
-                      wmc_dtype_t dtype, wmc_boundary_t bnd, wmc_stream_t stream) {
+static wmc_status_t eval_impl(int mode, float scale, const void *u, void *hw, int32_t h, int32_t w,
+                              int64_t ld_u, int64_t ld_hw, wmc_dtype_t dtype, wmc_boundary_t bnd,
+                              wmc_stream_t stream) {
     g_last_error[0] = 0;
     wmc_status_t s;
     if ((s = check_enums(dtype, bnd)) != WMC_OK) return s;
@@ -530,11 +534,23 @@ wmc_status_t wmc_eval(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_
     p.ldo = ld_hw;
     p.h = h;
     p.w = w;
-    p.c_h = 1.0f / 12.0f;
+    p.c_h = scale;
     const bool vec = pair_aligned(u, ld_u, es) && pair_aligned(hw, ld_hw, es);
-    cudaError_t e = wmc::launch_stream((int)dtype, wmc::MODE_EVAL, (int)bnd, p, vec, (cudaStream_t)stream);
+    cudaError_t e = wmc::launch_stream((int)dtype, mode, (int)bnd, p, vec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
     return WMC_OK;
+}
+
+wmc_status_t wmc_eval(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_u, int64_t ld_hw,
+                      wmc_dtype_t dtype, wmc_boundary_t bnd, wmc_stream_t stream) {
+    // the kernels carry 12 * H^w; the output scale brings it back
+    return eval_impl(wmc::MODE_EVAL, 1.0f / 12.0f, u, hw, h, w, ld_u, ld_hw, dtype, bnd, stream);
+}
+
+wmc_status_t wmc_eval_fd(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_u,
+                         int64_t ld_hw, wmc_dtype_t dtype, wmc_boundary_t bnd,
+                         wmc_stream_t stream) {
+    return eval_impl(wmc::MODE_FD_EVAL, 1.0f, u, hw, h, w, ld_u, ld_hw, dtype, bnd, stream);
 }
 
 size_t wmc_denoise_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype) {
@@ -566,6 +582,32 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
     }
     return run_flow(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, T, workspace,
                     (cudaStream_t)stream);
+}
+
+wmc_status_t wmc_denoise_fd(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
+                            wmc_dtype_t dtype, float lambda, float step, int32_t iters,
+                            wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
+                            wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    int T = 0;
+    wmc_status_t s =
+        check_flow_args(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, nullptr, &T);
+    if (s != WMC_OK) return s;
+    if (h == 0 || w == 0) return WMC_OK;
+    if (iters > 0) {
+        const size_t need = wmc_denoise_workspace_size(h, w, ld, dtype);
+        if (!workspace || workspace_bytes < need)
+            return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need,
+                        workspace ? workspace_bytes : (size_t)0);
+        if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
+            return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+        const size_t n = span_bytes(h, w, ld, elem_size(dtype));
+        if (overlap(workspace, need, f, n) || overlap(workspace, need, u, n) ||
+            overlap(workspace, need, u0, n))
+            return fail(WMC_ERR_ALIAS, "workspace overlaps an image");
+    }
+    return run_flow(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, 1, workspace,
+                    (cudaStream_t)stream, true);
 }
 
 wmc_status_t wmc_denoise(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,

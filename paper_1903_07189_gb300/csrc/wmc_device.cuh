@@ -63,6 +63,23 @@ __device__ __forceinline__ float half_laplace12(float nw, float n, float ne, flo
     return select12(L, a1, a2, a5, a6);
 }
 
+// Conventional finite-difference WMC of Eq. rhs at the centre of a 3x3 neighbourhood (rows: n*
+// above, s* below), central differences with unit spacing:
+//   H = (U_xx + U_yy) - (U_y^2 U_yy + 2 U_x U_y U_xy + U_x^2 U_xx) / (U_x^2 + U_y^2),
+// and 0 where the central-difference gradient is exactly zero.  U_x and U_y are differences of
+// two stored values (exact, or correct to one rounding), so the quotient keeps FP32 relative
+// accuracy even where the gradient is small.
+__device__ __forceinline__ float fd_wmc(float nw, float n, float ne, float w, float c, float e,
+                                        float sw, float s, float se) {
+    const float ux = 0.5f * (e - w), uy = 0.5f * (s - n);
+    const float uxx = fmaf(-2.0f, c, e) + w, uyy = fmaf(-2.0f, c, s) + n;
+    const float uxy = 0.25f * ((se - ne) - (sw - nw));
+    const float g2 = fmaf(ux, ux, uy * uy);
+    if (!(g2 > 0.0f)) return 0.0f;
+    const float num = fmaf(uy * uy, uyy, fmaf(2.0f * ux * uy, uxy, ux * ux * uxx));
+    return (uxx + uyy) - num / g2;
+}
+
 // The same for two cells at once (lane .x = one cell, .y = the other): the twenty linear
 // operations run as packed FP32x2 instructions (sm_100+), each lane rounding exactly as the
 // scalar operation above (a - b is computed as fma(b, -1, a), which is exact in the product),

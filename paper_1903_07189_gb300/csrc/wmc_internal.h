@@ -7,7 +7,8 @@
 
 namespace wmc {
 
-enum Mode { MODE_EVAL = 0, MODE_FLOW = 1 };
+// MODE_FD_*: the same passes with the conventional finite-difference WMC of Eq. rhs.
+enum Mode { MODE_EVAL = 0, MODE_FLOW = 1, MODE_FD_EVAL = 2, MODE_FD_FLOW = 3 };
 
 constexpr int kMaxSteps = 8;
 

@@ -50,6 +50,8 @@ _vp, _i32, _i64, _f32, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ct
 SIGNATURES = {
     "wmc_eval": (_i32, [_vp, _vp, _i32, _i32, _i64, _i64, _i32, _i32, _vp]),
     "wmc_denoise_workspace_size": (_sz, [_i32, _i32, _i64, _i32]),
+    "wmc_eval_fd": (_i32, [_vp, _vp, _i32, _i32, _i64, _i64, _i32, _i32, _vp]),
+    "wmc_denoise_fd": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp, _sz, _vp]),
     "wmc_denoise": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp, _sz, _vp]),
     "wmc_denoise_ex": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32,
                               ctypes.POINTER(Config), _vp, _sz, _vp]),
@@ -140,6 +142,45 @@ def eval(u: torch.Tensor, boundary: str = "replicate", out: torch.Tensor | None 
         raise ValueError("out must match u in shape and dtype")
     _check(load().wmc_eval(p, po, h, w, ld, ldo, DTYPES[u.dtype], BOUNDARY[boundary], _stream(u.device)),
            "wmc_eval")
+    return out
+
+
+def eval_fd(u: torch.Tensor, boundary: str = "replicate", out: torch.Tensor | None = None) -> torch.Tensor:
+    """Conventional finite-difference WMC of Eq. rhs (the comparator of Sec. V-D)."""
+    p, h, w, ld = _img(u, "u")
+    if out is None:
+        out = torch.empty_like(u, memory_format=torch.contiguous_format)
+    po, ho, wo, ldo = _img(out, "out")
+    if (ho, wo) != (h, w) or out.dtype != u.dtype:
+        raise ValueError("out must match u in shape and dtype")
+    _check(load().wmc_eval_fd(p, po, h, w, ld, ldo, DTYPES[u.dtype], BOUNDARY[boundary], _stream(u.device)),
+           "wmc_eval_fd")
+    return out
+
+
+def denoise_fd(f: torch.Tensor | None, lam: float = 1.0, step: float = 0.1, iters: int = 100,
+               boundary: str = "replicate", u0: torch.Tensor | None = None, out: torch.Tensor | None = None,
+               workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """The flow of `denoise` with the finite-difference H of Eq. rhs (f None: mean-curvature flow
+    from u0)."""
+    ref = f if f is not None else u0
+    if ref is None:
+        raise ValueError("f or u0 is required")
+    p, h, w, ld = _img(ref, "f" if f is not None else "u0")
+    if out is None:
+        out = torch.empty_strided(ref.shape, ref.stride(), dtype=ref.dtype, device=ref.device)
+    for t, n in [(f, "f"), (u0, "u0"), (out, "out")]:
+        if t is not None:
+            _, h2, w2, ld2 = _img(t, n)
+            if (h2, w2, ld2) != (h, w, ld) or t.dtype != ref.dtype:
+                raise ValueError(f"{n} must match in shape, pitch and dtype")
+    lib = load()
+    if workspace is None:
+        workspace = _workspace(lib.wmc_denoise_workspace_size(h, w, ld, DTYPES[ref.dtype]), ref.device)
+    _check(lib.wmc_denoise_fd(f.data_ptr() if f is not None else None, u0.data_ptr() if u0 is not None else None,
+                              out.data_ptr(), h, w, ld, DTYPES[ref.dtype], float(lam), float(step), int(iters),
+                              BOUNDARY[boundary], workspace.data_ptr(), workspace.numel(), _stream(ref.device)),
+           "wmc_denoise_fd")
     return out
 
 
