@@ -119,6 +119,7 @@ template <> struct Store<float> {
         return __ldg(reinterpret_cast<const float2 *>(p));
     }
     static __device__ __forceinline__ float round(float v) { return v; }
+    static __device__ __forceinline__ float2 round2(float2 v) { return v; }
     static __device__ __forceinline__ void store(float *p, float v) { *p = v; }
     static __device__ __forceinline__ void store2(float *p, float a, float b) {
         *reinterpret_cast<float2 *>(p) = make_float2(a, b);
@@ -136,6 +137,14 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float round(float v) {
         return __bfloat162float(__float2bfloat16_rn(v));
     }
+    // both lanes rounded by one paired conversion (each to nearest even, as round())
+    static __device__ __forceinline__ float2 round2(float2 v) {
+        return __bfloat1622float2(__floats2bfloat162_rn(v.x, v.y));
+    }
+    // two elements packed in 32 bits (lower address in the low half) widened to FP32
+    static __device__ __forceinline__ float2 unpack2(uint32_t bits) {
+        return make_float2(__uint_as_float(bits << 16), __uint_as_float(bits & 0xffff0000u));
+    }
     static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v) {
         *p = __float2bfloat16_rn(v);
     }
@@ -152,6 +161,14 @@ template <> struct Store<__half> {
     }
     static __device__ __forceinline__ float round(float v) {
         return __half2float(__float2half_rn(v));
+    }
+    static __device__ __forceinline__ float2 round2(float2 v) {
+        return __half22float2(__floats2half2_rn(v.x, v.y));
+    }
+    static __device__ __forceinline__ float2 unpack2(uint32_t bits) {
+        __half2 hv;
+        memcpy(&hv, &bits, sizeof bits);
+        return __half22float2(hv);
     }
     static __device__ __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ void store2(__half *p, float a, float b) {

@@ -203,9 +203,10 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
         float2 v = __ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k]));
         const int i = c.ib + k;
         if (WMODE == WRITE_INTERIOR) {
+            const float2 rv = Store<S>::round2(v);
             float *d = dst + i * P + c.j;
-            d[0] = Store<S>::round(v.x);
-            d[32] = Store<S>::round(v.y);
+            d[0] = rv.x;
+            d[32] = rv.y;
         } else if (WMODE == WRITE_BORDER) {
             // tiles touching the border: cells outside the image keep 0 (ZERO) or are left
             // for the ring refresh after the step (REPLICATE)
@@ -213,12 +214,13 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
             const bool rin = (gy >= 0) & (gy < c.h);
             const bool in0 = rin & c.cin0, in1 = rin & c.cin1;
             float *d = dst + i * P + c.j;
+            const float2 rv = Store<S>::round2(v);
             if (BND == BND_ZERO) {
-                d[0] = in0 ? Store<S>::round(v.x) : 0.0f;
-                d[32] = in1 ? Store<S>::round(v.y) : 0.0f;
+                d[0] = in0 ? rv.x : 0.0f;
+                d[32] = in1 ? rv.y : 0.0f;
             } else {
-                if (in0) d[0] = Store<S>::round(v.x);
-                if (in1) d[32] = Store<S>::round(v.y);
+                if (in0) d[0] = rv.x;
+                if (in1) d[32] = rv.y;
             }
         } else {
             if ((c.out_rows >> k) & 1u) {
@@ -383,10 +385,17 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
             if (tid == 0 && p.status) atomicOr(p.status, 1u);
             return;
         }
-        if (sizeof(S) != 4) {  // widen the staged 16-bit box
-            const S *stage = reinterpret_cast<const S *>(buf1 + BUF);
-            for (int idx = tid; idx < LH * LW; idx += kTileThreadsV2)
-                buf0[idx] = Store<S>::to_float(stage[idx]);
+        if constexpr (sizeof(S) != 4) {  // widen the staged 16-bit box, 8 elements per 16-byte access
+            static_assert((LH * LW) % 8 == 0, "the staged box is a whole number of 16-byte chunks");
+            const uint4 *stage = reinterpret_cast<const uint4 *>(buf1 + BUF);
+            float4 *dst4 = reinterpret_cast<float4 *>(buf0);
+            for (int q = tid; q < LH * LW / 8; q += kTileThreadsV2) {
+                const uint4 raw = stage[q];
+                const float2 a = Store<S>::unpack2(raw.x), b = Store<S>::unpack2(raw.y);
+                const float2 c2 = Store<S>::unpack2(raw.z), d2 = Store<S>::unpack2(raw.w);
+                dst4[2 * q] = make_float4(a.x, a.y, b.x, b.y);
+                dst4[2 * q + 1] = make_float4(c2.x, c2.y, d2.x, d2.y);
+            }
             __syncthreads();
         }
     } else {
