@@ -213,6 +213,7 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
     const void *src = u0;
     int src_id = 0;
     int done = 0;
+    bool prev_tile = false;
     for (int k = 0; k < nl; ++k) {
         const int s = (iters - done) < T ? (iters - done) : T;
         void *dst = bufs[k & 1];
@@ -242,9 +243,11 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
             tp.c_f = c_f;
             tp.c_h = c_h;
             tp.status = status;
+            tp.pdl = prev_tile ? 1 : 0;  // follows a tile launch: may overlap its tail
             e = launch_tile(dtype, bnd, s, &maps[src_id], tp, -1, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "flow kernel launch");
+        prev_tile = s > 1;
         src = dst;
         src_id = 1 + (k & 1);
         done += s;

@@ -45,6 +45,7 @@
 #include <cuda.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "wmc_device.cuh"
@@ -108,7 +109,17 @@ struct TileV2Params {
     // both
     int32_t owt, oht;     // output tile size
     unsigned int *status; // device status word (bit 0: a bounded wait gave up) or nullptr
+    int32_t pdl;          // host side: launch as a programmatic dependent of the previous launch
 };
+
+// Programmatic dependent launch: a launch made with the programmatic-serialization attribute may
+// start while the previous kernel in the stream finishes (its CTAs fill the SMs the last wave
+// leaves idle and do their set-up); griddep_wait() then blocks until that kernel has completed
+// and its writes are visible.  Both are no-ops for a launch made without the attribute.
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // ------------------------------------------------------------------ TMA / mbarrier helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -264,79 +275,60 @@ __device__ __forceinline__ void refresh_ring(float *buf, int X0, int Y0, int h, 
     }
 }
 
-template <int T, typename S, int BND, bool BATCH>
-__global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
-    tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const TileV2Params p) {
-    using G = Geom<S>;
-    constexpr int LW = G::LW, LH = G::LH, P = G::P, BUF = G::BUF;
-    constexpr int M = Out<S, T>::M;
-
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    float *buf0 = reinterpret_cast<float *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    float *buf1 = buf0 + BUF;
-
-    // ---- this CTA's job: image, buffers, coefficients and output tile
-    const S *u;
-    const S *f;
-    TileCtx c;
+// One tile's job: which image buffers, coefficients and output tile.
+template <typename S> struct TileJob {
+    const S *u;                // U^t (read through `map` when use_tma)
+    const S *f;                // f or nullptr
     const CUtensorMap *map;
-    bool use_tma;
-    int x0, y0;
-    float c_f;
     int64_t ld;
-    if (BATCH) {
-        const int4 t = p.tiles[blockIdx.x];
-        const BatchImage &im = p.images[t.x];
-        u = static_cast<const S *>(im.buf[p.src_role]);
-        f = static_cast<const S *>(im.buf[0]);
-        ld = im.ld;
-        c.h = im.h;
-        c.w = im.w;
-        c.c_keep = im.c_keep;
-        c.c_h = im.c_h;
-        c_f = im.c_f;
-        map = &im.map[p.src_role];
-        use_tma = im.use_tma[p.src_role] != 0;
-        x0 = t.y;
-        y0 = t.z;
-    } else {
-        u = static_cast<const S *>(p.u);
-        f = static_cast<const S *>(p.f);
-        ld = p.ld;
-        c.h = p.h;
-        c.w = p.w;
-        c.c_keep = p.c_keep;
-        c.c_h = p.c_h;
-        c_f = p.c_f;
-        map = &tmap;
-        use_tma = p.use_tma != 0;
-        const int ty = blockIdx.x / p.ntx, tx = blockIdx.x - ty * p.ntx;
-        x0 = tx * p.owt;
-        y0 = ty * p.oht;
-    }
+    int h, w;
+    float c_keep, c_h, c_f;
+    int x0, y0;                // output tile origin
+    bool use_tma;
+};
+
+// Everything a CTA does for one tile: load the window of U^t, take T steps in shared memory and
+// write the output tile through `out_of()` (called after the steps, so the output pointer is not
+// kept in registers through them).  `phase` is the mbarrier parity this tile's load completes.
+// Returns false if the window load timed out (the status word is set).
+template <int T, typename S, int BND, typename OutFn>
+__device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
+                                         unsigned int *status, float *buf0, float *buf1,
+                                         uint64_t *bar, uint32_t phase, OutFn out_of) {
+    using G = Geom<S>;
+    constexpr int LW = G::LW, LH = G::LH, BUF = G::BUF;
+    constexpr int M = Out<S, T>::M;
+    TileCtx c;
+    c.h = jb.h;
+    c.w = jb.w;
+    c.c_keep = jb.c_keep;
+    c.c_h = jb.c_h;
     const int h = c.h, w = c.w;
+    const int x0 = jb.x0, y0 = jb.y0;
     const int X0 = x0 - M, Y0 = y0 - T;
     const int tid = threadIdx.x;
     const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
 
-    // ---- issue the load of the window of U^t (thread 0 alone owns the barrier: it initialises
-    // it, issues the copy and later waits for it, so the other threads never poll it)
-    if (use_tma) {
+    // ---- issue the load of the window of U^t (thread 0 alone owns the barrier: it issues the
+    // copy and later waits for it, so the other threads never poll it).  U^t is the previous
+    // launch's output: wait for that launch first (every later access of this CTA to U^t or to
+    // the output buffer comes after this thread's wait through the CTA barriers below).
+    if (jb.use_tma) {
         if (tid == 0) {
-            mbar_init(smem_u32(&bar), 1);
+            griddep_wait();
             void *dst = (sizeof(S) == 4) ? static_cast<void *>(buf0)
                                          : static_cast<void *>(buf1 + BUF);  // staging
-            mbar_expect_tx(smem_u32(&bar), (uint32_t)(LW * LH * sizeof(S)));
-            tma_load_2d(smem_u32(dst), map, X0, Y0, smem_u32(&bar));
+            mbar_expect_tx(smem_u32(bar), (uint32_t)(LW * LH * sizeof(S)));
+            tma_load_2d(smem_u32(dst), jb.map, X0, Y0, smem_u32(bar));
         }
     } else {
+        constexpr int P = G::P;
+        griddep_wait();
         for (int idx = tid; idx < LH * LW; idx += kTileThreadsV2) {
             const int i = idx / LW, j = idx - (idx / LW) * LW;
             const int gy = Y0 + i, gx = X0 + j;
             float v = 0.0f;
-            if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = Store<S>::load(u + (int64_t)gy * ld + gx);
+            if (gy >= 0 && gy < h && gx >= 0 && gx < w) v = Store<S>::load(jb.u + (int64_t)gy * jb.ld + gx);
             buf0[i * P + j] = v;
         }
     }
@@ -350,8 +342,8 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
     c.gx = X0 + c.j;
     c.cin0 = (c.gx >= 0) & (c.gx < w);
     c.cin1 = (c.gx + 32 >= 0) & (c.gx + 32 < w);
-    c.out0 = c.cin0 & (c.gx >= x0) & (c.gx < x0 + p.owt);
-    c.out1 = c.cin1 & (c.gx + 32 >= x0) & (c.gx + 32 < x0 + p.owt);
+    c.out0 = c.cin0 & (c.gx >= x0) & (c.gx < x0 + owt);
+    c.out1 = c.cin1 & (c.gx + 32 >= x0) & (c.gx + 32 < x0 + owt);
     unsigned in_rows = 0;  // bit k: image row Y0 + ib + k exists
     c.out_rows = 0;
 #pragma unroll
@@ -359,17 +351,17 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
         const int gy = Y0 + c.ib + k;
         const bool rin = (gy >= 0) & (gy < h);
         in_rows |= (rin ? 1u : 0u) << k;
-        c.out_rows |= ((rin & (gy >= y0) & (gy < y0 + p.oht)) ? 1u : 0u) << k;
+        c.out_rows |= ((rin & (gy >= y0) & (gy < y0 + oht)) ? 1u : 0u) << k;
     }
     float2 g[kRY];
     {
-        const float2 cf = make_float2(c_f, c_f);
-        const S *fr = f + (int64_t)(Y0 + c.ib) * ld + c.gx;
+        const float2 cf = make_float2(jb.c_f, jb.c_f);
+        const S *fr = jb.f + (int64_t)(Y0 + c.ib) * jb.ld + c.gx;
 #pragma unroll
         for (int k = 0; k < kRY; ++k) {
             float a = 0.0f, b = 0.0f;
-            if (f != nullptr && ((in_rows >> k) & 1u)) {
-                const S *fk = fr + (int64_t)k * ld;
+            if (jb.f != nullptr && ((in_rows >> k) & 1u)) {
+                const S *fk = fr + (int64_t)k * jb.ld;
                 if (c.cin0) a = Store<S>::load(fk);
                 if (c.cin1) b = Store<S>::load(fk + 32);
             }
@@ -379,11 +371,11 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
 
     // ---- wait for the window: thread 0 waits on the barrier (its completion makes the copied
     // data visible to it), then the CTA barrier orders everyone else's reads after that
-    if (use_tma) {
-        const bool ok = (tid != 0) || mbar_wait_bounded(smem_u32(&bar), 0, kWaitLimitNs);
+    if (jb.use_tma) {
+        const bool ok = (tid != 0) || mbar_wait_bounded(smem_u32(bar), phase, kWaitLimitNs);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0 && p.status) atomicOr(p.status, 1u);
-            return;
+            if (tid == 0 && status) atomicOr(status, 1u);
+            return false;
         }
         if constexpr (sizeof(S) != 4) {  // widen the staged 16-bit box, 8 elements per 16-byte access
             static_assert((LH * LW) % 8 == 0, "the staged box is a whole number of 16-byte chunks");
@@ -425,20 +417,68 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
             }
         }
     }
-    // the output pointer is looked up again here (kernel parameters, or the image descriptor in
-    // L1) rather than kept in registers through the steps
-    S *out;
     int64_t ldo;
-    if (BATCH) {
-        const BatchImage &im = p.images[p.tiles[blockIdx.x].x];
-        out = static_cast<S *>(const_cast<void *>(im.buf[p.dst_role]));
-        ldo = im.ld;
-    } else {
-        out = static_cast<S *>(p.out);
-        ldo = p.ld;
-    }
+    S *out = out_of(&ldo);
     tile_step<WRITE_GLOBAL, S, BND>(((T - 1) & 1) ? buf1 : buf0, nullptr, c, g,
                                     out + (int64_t)(Y0 + c.ib) * ldo + c.gx, ldo);
+    return true;
+}
+
+template <int T, typename S, int BND, bool BATCH>
+__global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
+    tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const TileV2Params p) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    float *buf0 = reinterpret_cast<float *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float *buf1 = buf0 + Geom<S>::BUF;
+
+    // ---- this CTA's job: image, buffers, coefficients and output tile
+    TileJob<S> jb;
+    if (BATCH) {
+        const int4 t = p.tiles[blockIdx.x];
+        const BatchImage &im = p.images[t.x];
+        jb.u = static_cast<const S *>(im.buf[p.src_role]);
+        jb.f = static_cast<const S *>(im.buf[0]);
+        jb.ld = im.ld;
+        jb.h = im.h;
+        jb.w = im.w;
+        jb.c_keep = im.c_keep;
+        jb.c_h = im.c_h;
+        jb.c_f = im.c_f;
+        jb.map = &im.map[p.src_role];
+        jb.use_tma = im.use_tma[p.src_role] != 0;
+        jb.x0 = t.y;
+        jb.y0 = t.z;
+    } else {
+        jb.u = static_cast<const S *>(p.u);
+        jb.f = static_cast<const S *>(p.f);
+        jb.ld = p.ld;
+        jb.h = p.h;
+        jb.w = p.w;
+        jb.c_keep = p.c_keep;
+        jb.c_h = p.c_h;
+        jb.c_f = p.c_f;
+        jb.map = &tmap;
+        jb.use_tma = p.use_tma != 0;
+        const int ty = blockIdx.x / p.ntx, tx = blockIdx.x - ty * p.ntx;
+        jb.x0 = tx * p.owt;
+        jb.y0 = ty * p.oht;
+    }
+    // the next launch may be scheduled once every CTA of this one is running
+    griddep_launch_dependents();
+    if (jb.use_tma && threadIdx.x == 0) mbar_init(smem_u32(&bar), 1);
+    // the output pointer is looked up again after the steps (kernel parameters, or the image
+    // descriptor in L1) rather than kept in registers through them
+    tile_job<T, S, BND>(jb, p.owt, p.oht, p.status, buf0, buf1, &bar, 0u, [&](int64_t *ldo) -> S * {
+        if (BATCH) {
+            const BatchImage &im = p.images[p.tiles[blockIdx.x].x];
+            *ldo = im.ld;
+            return static_cast<S *>(const_cast<void *>(im.buf[p.dst_role]));
+        }
+        *ldo = p.ld;
+        return static_cast<S *>(p.out);
+    });
 }
 
 template <int T, typename S, int BND, bool BATCH>
@@ -472,8 +512,21 @@ cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, int64_t nbl
         memset(&dummy, 0, sizeof dummy);
         map = &dummy;
     }
-    tile_v2_kernel<T, S, BND, BATCH><<<(unsigned)nblocks, kTileThreadsV2, G::SMEM, st>>>(*map, p);
-    return cudaGetLastError();
+    if (!p.pdl) {
+        tile_v2_kernel<T, S, BND, BATCH><<<(unsigned)nblocks, kTileThreadsV2, G::SMEM, st>>>(*map, p);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3(kTileThreadsV2);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tile_v2_kernel<T, S, BND, BATCH>, *map, p);
 }
 
 template <typename S, int BND>
