@@ -824,10 +824,12 @@ wmc_status_t wmc_batch_run(const wmc_batch_t *plan, int32_t iters, wmc_stream_t 
         e = cudaGetLastError();
         return e == cudaSuccess ? WMC_OK : cuda_fail(e, "batch copy launch");
     }
+    int launches = 0;
     for_each_launch(iters, bp.steps, [&](int s, int src, int dst) {
         if (e != cudaSuccess) return;
         p.src_role = src;
         p.dst_role = dst;
+        p.pdl = launches++ > 0 ? 1 : 0;  // follows a tile launch: may overlap its tail
         e = launch_tile((wmc_dtype_t)bp.dtype, (wmc_boundary_t)bp.bnd, s, nullptr, p, bp.ntiles, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
