@@ -33,22 +33,13 @@ __constant__ float kH12Taps[8][9] = {
 
 // half_laplace12 with the index (0..7 for h1..h8) of the candidate it returns.  Same FP32
 // operations, hence the same value and the same piece as the forward kernels.
-__device__ __forceinline__ float half_laplace12_sel(float nw, float n, float ne, float w, float c,
-                                                    float e, float sw, float s, float se, int *m) {
-    const float p = n - s;
-    const float q = w - e;
-    const float A = nw - se;
-    const float B = ne - sw;
-    const float corners = (nw + se) + (ne + sw);
-    const float edges = (n + s) + (w + e);
-    const float L = fmaf(-12.0f, c, fmaf(2.0f, edges, corners));
-    const float a1 = fmaf(2.0f, q, A - B);
-    const float a2 = fmaf(2.0f, p, A + B);
-    const float a5 = fmaf(2.0f, p + q, A);
-    const float a6 = fmaf(2.0f, p - q, B);
+// select12 with the index (0..7 for h1..h8) of the candidate it returns: the same comparisons
+// in the same order, so the same value and the same piece as the forward kernels.
+__device__ __forceinline__ float select12_idx(float L, float a1, float a2, float a5, float a6,
+                                              int *m) {
     const float aL = fabsf(L);
-    // the same comparisons in the same order as select12; aj and jd track the winner's odd
-    // part and the kernel index of its "L + a_j" candidate (h1, h2, h5, h6)
+    // aj and jd track the winner's odd part and the kernel index of its "L + a_j" candidate
+    // (h1, h2, h5, h6)
     float t = aL - fabsf(a1), aj = a1;
     int jd = 0;
     const float t2 = aL - fabsf(a2), t5 = aL - fabsf(a5), t6 = aL - fabsf(a6);
@@ -61,6 +52,42 @@ __device__ __forceinline__ float half_laplace12_sel(float nw, float n, float ne,
     const bool use_direct = (aj == 0.0f) || (signbit(Ls) != signbit(aj));
     *m = use_direct ? jd : jd + 2;
     return __int_as_float(__float_as_int(t) ^ (__float_as_int(Ls) & 0x80000000));
+}
+
+// 12 H^w and the selected kernel index at the centre of a 3x3 neighbourhood.
+__device__ __forceinline__ float half_laplace12_sel(float nw, float n, float ne, float w, float c,
+                                                    float e, float sw, float s, float se, int *m) {
+    const float p = n - s;
+    const float q = w - e;
+    const float A = nw - se;
+    const float B = ne - sw;
+    const float corners = (nw + se) + (ne + sw);
+    const float edges = (n + s) + (w + e);
+    const float L = fmaf(-12.0f, c, fmaf(2.0f, edges, corners));
+    return select12_idx(L, fmaf(2.0f, q, A - B), fmaf(2.0f, p, A + B), fmaf(2.0f, p + q, A),
+                        fmaf(2.0f, p - q, B), m);
+}
+
+// The same for two cells at once (lane .x, lane .y): the linear part as packed FP32x2 operations,
+// each lane rounding exactly as the scalar form (a - b as fma(b, -1, a), exact in the product).
+__device__ __forceinline__ float2 half_laplace12_sel_x2(float2 nw, float2 n, float2 ne, float2 w,
+                                                        float2 c, float2 e, float2 sw, float2 s,
+                                                        float2 se, int *m0, int *m1) {
+    const float2 two = make_float2(2.0f, 2.0f);
+    const float2 m12 = make_float2(-12.0f, -12.0f);
+    const float2 p = sub2(n, s);
+    const float2 q = sub2(w, e);
+    const float2 A = sub2(nw, se);
+    const float2 B = sub2(ne, sw);
+    const float2 corners = __fadd2_rn(__fadd2_rn(nw, se), __fadd2_rn(ne, sw));
+    const float2 edges = __fadd2_rn(__fadd2_rn(n, s), __fadd2_rn(w, e));
+    const float2 L = __ffma2_rn(m12, c, __ffma2_rn(two, edges, corners));
+    const float2 a1 = __ffma2_rn(two, q, sub2(A, B));
+    const float2 a2 = __ffma2_rn(two, p, __fadd2_rn(A, B));
+    const float2 a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
+    const float2 a6 = __ffma2_rn(two, sub2(p, q), B);
+    return make_float2(select12_idx(L.x, a1.x, a2.x, a5.x, a6.x, m0),
+                       select12_idx(L.y, a1.y, a2.y, a5.y, a6.y, m1));
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -89,6 +116,14 @@ int64_t adjoint_blocks(int32_t h, int32_t w) {
     return (int64_t)((w + kTX - 1) / kTX) * ((h + kTY - 1) / kTY);
 }
 
+// The selection byte stores the kernel index times the byte size of a tap row, so that a tap is
+// one shared load at [index + constant] with no address arithmetic.
+constexpr int kTapRowBytes = 9 * sizeof(float);
+
+__device__ __forceinline__ float tap_at(const float (&taps)[8][9], int moff, int o) {
+    return *reinterpret_cast<const float *>(reinterpret_cast<const char *>(&taps[0][0]) + moff + 4 * o);
+}
+
 using AdjU = float[kTY + 4][kTX + 4];
 using AdjG = float[kTY + 2][kTX + 2];
 using AdjM = uint8_t[kTY + 2][kTX + 2];
@@ -110,7 +145,7 @@ __device__ __forceinline__ float adjoint_select_one(AdjU &us, AdjG &gs, AdjM &ms
     }
     int m;
     const float h12 = half_laplace12_sel(nw, n, ne, wv, ce, e, sw, sv, se, &m);
-    ms[r + 1][cc + 1] = (uint8_t)m;
+    ms[r + 1][cc + 1] = (uint8_t)(m * kTapRowBytes);
     if (ENERGY) {
         gs[r + 1][cc + 1] = h12 > 0.0f ? 1.0f : (h12 < 0.0f ? -1.0f : 0.0f);
         return 0.0f;
@@ -118,22 +153,49 @@ __device__ __forceinline__ float adjoint_select_one(AdjU &us, AdjG &gs, AdjM &ms
     return (r >= 0 && r < kTY && cc >= 0 && cc < kTX) ? gs[r + 1][cc + 1] * h12 : 0.0f;
 }
 
-// kRows selections down column c from row r0, a 3-row U window carried in registers.
+// Phase-2 selections of one thread: tile columns l and l + 32 (the two lanes of packed FP32x2
+// arithmetic), kSelRows rows down from r0, a 3-row window of operand pairs in registers.
+constexpr int kSelRows = kTY / (kAdjThreads / 32);  // rows per thread in phase 2
+
 template <int BND, bool ENERGY, bool CHECK>
-__device__ __forceinline__ float adjoint_select_rows(AdjU &us, AdjG &gs, AdjM &ms, int c, int r0,
-                                                     int x0, int y0, int h, int w) {
+__device__ __forceinline__ float adjoint_select_rows2(AdjU &us, AdjG &gs, AdjM &ms, int l, int r0,
+                                                      int x0, int y0, int h, int w) {
     float acc = 0.0f;
-    float a0 = us[r0 + 1][c + 1], a1 = us[r0 + 1][c + 2], a2 = us[r0 + 1][c + 3];
-    float b0 = us[r0 + 2][c + 1], b1 = us[r0 + 2][c + 2], b2 = us[r0 + 2][c + 3];
+    // operand pairs: column cc of the tile is us column cc + 2; its west/east are cc + 1 / cc + 3
+    auto row3 = [&](int ur, float2 &wv, float2 &cv, float2 &ev) {
+        wv = make_float2(us[ur][l + 1], us[ur][l + 33]);
+        cv = make_float2(us[ur][l + 2], us[ur][l + 34]);
+        ev = make_float2(us[ur][l + 3], us[ur][l + 35]);
+    };
+    float2 aw, ac, ae, bw, bc, be;
+    row3(r0 + 1, aw, ac, ae);
+    row3(r0 + 2, bw, bc, be);
 #pragma unroll
-    for (int k = 0; k < kRows; ++k) {
+    for (int k = 0; k < kSelRows; ++k) {
         const int r = r0 + k;
-        const float d0 = us[r + 3][c + 1], d1 = us[r + 3][c + 2], d2 = us[r + 3][c + 3];
-        const float t = adjoint_select_one<BND, ENERGY, CHECK>(us, gs, ms, r, c, x0, y0, h, w, a0, a1,
-                                                               a2, b0, b1, b2, d0, d1, d2);
-        if (!ENERGY) acc += t;
-        a0 = b0; a1 = b1; a2 = b2;
-        b0 = d0; b1 = d1; b2 = d2;
+        float2 dw, dc, de;
+        row3(r + 3, dw, dc, de);
+        int m0, m1;
+        const float2 h12 = half_laplace12_sel_x2(aw, ac, ae, bw, bc, be, dw, dc, de, &m0, &m1);
+        bool in0 = true, in1 = true;
+        if (CHECK) {
+            const int y = y0 + r;
+            const bool rin = (y >= 0) & (y < h);
+            in0 = rin & (x0 + l < w);
+            in1 = rin & (x0 + l + 32 < w);
+        }
+        ms[r + 1][l + 1] = in0 ? (uint8_t)(m0 * kTapRowBytes) : 0;
+        ms[r + 1][l + 33] = in1 ? (uint8_t)(m1 * kTapRowBytes) : 0;
+        if (ENERGY) {
+            gs[r + 1][l + 1] = in0 ? (h12.x > 0.0f ? 1.0f : (h12.x < 0.0f ? -1.0f : 0.0f)) : 0.0f;
+            gs[r + 1][l + 33] = in1 ? (h12.y > 0.0f ? 1.0f : (h12.y < 0.0f ? -1.0f : 0.0f)) : 0.0f;
+        } else {
+            // outside the image g = 0, so those cells add nothing
+            acc = fmaf(gs[r + 1][l + 1], h12.x, acc);
+            acc = fmaf(gs[r + 1][l + 33], h12.y, acc);
+        }
+        aw = bw; ac = bc; ae = be;
+        bw = dw; bc = dc; be = de;
     }
     return acc;
 }
@@ -180,9 +242,9 @@ __device__ __forceinline__ void adjoint_gather_rows(AdjG &gs, AdjM &ms, float (&
             float a = 0.0f;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                a = fmaf(taps[m0[k]][8 - k], g0[k], a);  // dy = -1
-                a = fmaf(taps[m1[k]][5 - k], g1[k], a);  // dy = 0
-                a = fmaf(taps[m2[k]][2 - k], g2[k], a);  // dy = +1
+                a = fmaf(tap_at(taps, m0[k], 8 - k), g0[k], a);  // dy = -1
+                a = fmaf(tap_at(taps, m1[k], 5 - k), g1[k], a);  // dy = 0
+                a = fmaf(tap_at(taps, m2[k], 2 - k), g2[k], a);  // dy = +1
             }
             if (BND == BND_REPLICATE && CHECK) {
                 // Taps that leave the image read the clamped pixel.  On the first row, the taps
@@ -191,23 +253,23 @@ __device__ __forceinline__ void adjoint_gather_rows(AdjG &gs, AdjM &ms, float (&
                 const bool top = qy == 0, bottom = qy == h - 1, left = qx == 0, right = qx == w - 1;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    if (top) a = fmaf(taps[m1[k]][2 - k], g1[k], a);
-                    if (bottom) a = fmaf(taps[m1[k]][8 - k], g1[k], a);
+                    if (top) a = fmaf(tap_at(taps, m1[k], 2 - k), g1[k], a);
+                    if (bottom) a = fmaf(tap_at(taps, m1[k], 8 - k), g1[k], a);
                 }
                 if (left) {
-                    a = fmaf(taps[m0[1]][6], g0[1], a);
-                    a = fmaf(taps[m1[1]][3], g1[1], a);
-                    a = fmaf(taps[m2[1]][0], g2[1], a);
+                    a = fmaf(tap_at(taps, m0[1], 6), g0[1], a);
+                    a = fmaf(tap_at(taps, m1[1], 3), g1[1], a);
+                    a = fmaf(tap_at(taps, m2[1], 0), g2[1], a);
                 }
                 if (right) {
-                    a = fmaf(taps[m0[1]][8], g0[1], a);
-                    a = fmaf(taps[m1[1]][5], g1[1], a);
-                    a = fmaf(taps[m2[1]][2], g2[1], a);
+                    a = fmaf(tap_at(taps, m0[1], 8), g0[1], a);
+                    a = fmaf(tap_at(taps, m1[1], 5), g1[1], a);
+                    a = fmaf(tap_at(taps, m2[1], 2), g2[1], a);
                 }
-                if (top && left) a = fmaf(taps[m1[1]][0], g1[1], a);
-                if (top && right) a = fmaf(taps[m1[1]][2], g1[1], a);
-                if (bottom && left) a = fmaf(taps[m1[1]][6], g1[1], a);
-                if (bottom && right) a = fmaf(taps[m1[1]][8], g1[1], a);
+                if (top && left) a = fmaf(tap_at(taps, m1[1], 0), g1[1], a);
+                if (top && right) a = fmaf(tap_at(taps, m1[1], 2), g1[1], a);
+                if (bottom && left) a = fmaf(tap_at(taps, m1[1], 6), g1[1], a);
+                if (bottom && right) a = fmaf(tap_at(taps, m1[1], 8), g1[1], a);
             }
             const float gq = g1[1];
             const float out = fmaf(c_nb, a, c_self * gq);
@@ -310,9 +372,9 @@ __global__ void __launch_bounds__(kAdjThreads, 4)
     const int c = tid % kTX, grp = tid / kTX;
     float acc = 0.0f;
     if (interior)
-        acc = adjoint_select_rows<BND, ENERGY, false>(us, gs, ms, c, grp * kRows, x0, y0, h, w);
+        acc = adjoint_select_rows2<BND, ENERGY, false>(us, gs, ms, lane, warp * kSelRows, x0, y0, h, w);
     else
-        acc = adjoint_select_rows<BND, ENERGY, true>(us, gs, ms, c, grp * kRows, x0, y0, h, w);
+        acc = adjoint_select_rows2<BND, ENERGY, true>(us, gs, ms, lane, warp * kSelRows, x0, y0, h, w);
     // the ring: rows -1 and kTY (all kTX + 2 columns), columns -1 and kTX (rows 0 .. kTY-1)
     for (int i = tid; i < 2 * GW + 2 * kTY; i += kAdjThreads) {
         int r, cc;
