@@ -560,3 +560,27 @@ def test_fd_flow_one_step_uses_fd_operator():
     u = synth.make_image(10, 12, seed=63, sigma=0.1, dtype=np.float64)
     out = oracle.fd_flow(None, 2.0, 0.1, 1, mu=0.0, u0=u)
     np.testing.assert_allclose(out, u + 0.2 * oracle.fd_eval(u), atol=1e-14)
+
+
+# ------------------------------------------------------------- worked 5x5 examples
+def test_ramp_zero_boundary_rows_by_hand():
+    """U = x + 2y on 5x5 with the Appendix's zero padding.  At (0,0) the only in-image
+    neighbours are E = 1, S = 2, SE = 3, and the north-west half window h5 (2nw + 4n + ne + 4w -
+    12c + sw)/12 reads none of them: d5 = 0, so H^w = 0.  The other entries follow the same way
+    (exact rationals from the eight printed kernels, ties by the canonical order)."""
+    y, x = np.mgrid[0:5, 0:5].astype(np.float64)
+    hw = oracle.wmc_eval(x + 2 * y, "zero")
+    np.testing.assert_allclose(hw[0], [0, 0, 1 / 2, 1 / 6, -1 / 6], atol=1e-15)
+    np.testing.assert_allclose(hw[4], [-11 / 6, -4 / 3, -4 / 3, -4 / 3, -7 / 2], atol=1e-15)
+    hr = oracle.wmc_eval(x + 2 * y, "replicate")
+    assert abs(hr[0, 0] - 1 / 4) < 1e-15 and abs(hr[4, 4] + 1 / 4) < 1e-15
+
+
+def test_one_step_on_a_mod7_image_by_hand():
+    """One denoising step, lambda = 1, step = 1/4, REPLICATE, f[y][x] = ((3x + 5y) mod 7) / 7,
+    U^0 = f, so U^1 = f + H^w(f)/4; the values were worked out in exact rationals."""
+    y, x = np.mgrid[0:5, 0:5].astype(np.float64)
+    f = ((3 * x + 5 * y) % 7) / 7
+    u1 = oracle.denoise(f, 1.0, 0.25, 1)
+    for (r, c), want in [((0, 0), 1 / 42), ((1, 1), 11 / 48), ((2, 2), 17 / 56), ((4, 4), 191 / 336)]:
+        assert abs(u1[r, c] - want) < 1e-15, (r, c, u1[r, c], want)
