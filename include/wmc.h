@@ -9,7 +9,10 @@
  *     L2 denoising U^{t+1} = U^t + step (lambda H^w(U^t) - (U^t - f)) (the gradient flow of
  *     Sec. V-B with A = I, where -dR_area/dU is replaced by H^w), and the mean-curvature flow
  *     U^{t+1} = U^t + step H^w(U^t) (Eq. MCF);
- *   - the energies of Eq. wmcr (q = 1) and Eq. 1 (L2 data term), reduced in FP64.
+ *   - the energies of Eq. wmcr (q = 1) and Eq. 1 (L2 data term), reduced in FP64;
+ *   - around them: batches of uneven images, the L1-fidelity primal-dual iteration of Sec. V-C,
+ *     the finite-difference discretisation of Eq. rhs that Sec. V-D compares against, and the
+ *     reverse mode of unrolled denoising steps and of the energy.
  *
  * Conventions shared by every entry point
  *   Images are single-channel, row-major, h rows by w columns, with a leading dimension
@@ -18,7 +21,9 @@
  *   Pointers documented as "device" must be CUDA device (or managed) memory readable by the
  *   current device; "host" pointers are ordinary host memory (pinned memory gives
  *   asynchronous copies).  The caller owns every buffer; the library never allocates or
- *   frees memory and keeps no state between calls other than the per-thread error string.
+ *   frees memory.  Between calls it keeps only the per-thread error string and, per device,
+ *   the kernel attributes it has set (once) and the fixed device array of
+ *   wmc_denoise_noalloc.
  *   Work is enqueued on `stream` (NULL = the legacy default stream) and runs asynchronously;
  *   argument errors are detected on the host and returned before anything is enqueued.
  *   No function throws; every failure is a status code, with a detail string available from
