@@ -303,3 +303,25 @@ def test_mcf_steps_per_launch_bitwise():
     ref = wmc().mcf(u0, step=0.3, iters=10, steps_per_launch=1)
     for T in (2, 4, 7):
         assert torch.equal(wmc().mcf(u0, step=0.3, iters=10, steps_per_launch=T), ref), T
+
+
+def test_denoise_graph_capture_replay():
+    """A single-image run (consecutive tile launches chained as programmatic dependents) captured
+    into a CUDA graph replays to the same bits as the direct call."""
+    f = to_gpu(synth.make_image(300, 260, seed=23, sigma=0.1))
+    out = torch.empty_like(f)
+    ws = torch.empty(wmc().load().wmc_denoise_workspace_size(300, 260, 260, 0), dtype=torch.uint8,
+                     device=DEV)
+    ref = wmc().denoise(f, 1.0, 0.25, 18, out=torch.empty_like(f), workspace=ws)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        wmc().denoise(f, 1.0, 0.25, 18, out=out, workspace=ws)  # warm-up off the capture
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        wmc().denoise(f, 1.0, 0.25, 18, out=out, workspace=ws)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
