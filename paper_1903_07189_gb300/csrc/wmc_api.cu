@@ -408,7 +408,8 @@ __global__ void batch_copy_kernel(const wmc::BatchImage *images, const int4 *til
     }
 }
 
-// Unrolled-flow workspace: [status | checkpoints | segment/temporary stacks | g ping-pong |
+// Unrolled-flow workspace: [256 reserved bytes (the status-word slot of the other workspaces;
+// these kernels have no bounded waits) | checkpoints | segment/temporary stacks | g ping-pong |
 // dlambda partials].
 struct UnrolledLayout {
     size_t slot, off_ckpt, off_seg, off_g, off_part, total;
@@ -1066,6 +1067,9 @@ wmc_status_t wmc_unrolled_backward(const float *f, const float *lambda, float st
         return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed", L.total);
     if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
         return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    if (overlap(workspace, L.total, f, nbytes) || overlap(workspace, L.total, grad_u, nbytes) ||
+        overlap(workspace, L.total, grad_f, nbytes))
+        return fail(WMC_ERR_ALIAS, "workspace overlaps f, grad_u or grad_f");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (K == 0) {

@@ -225,3 +225,14 @@ def test_batch_autotune_validation(lib):
     assert lib.wmc_batch_autotune(imgs, 1, 0, 0, good, 0, 8, ws, need, ctypes.byref(best), None, None) == INVALID
     assert lib.wmc_batch_autotune(imgs, 1, 0, 0, good, 1, 0, ws, need, ctypes.byref(best), None, None) == INVALID
     assert lib.wmc_batch_autotune(imgs, 1, 0, 0, good, 1, 8, ws, need, None, None, None) == INVALID
+
+
+def test_unrolled_backward_workspace_alias(lib):
+    f = ctypes.c_void_p(0x100000)
+    lam = ctypes.c_void_p(0x200000)
+    gu = ctypes.c_void_p(0x300000)
+    gf = ctypes.c_void_p(0x400000)
+    need = lib.wmc_unrolled_workspace_size(1, 8, 8, 8, 4, 2)
+    # a workspace starting inside grad_u
+    assert lib.wmc_unrolled_backward(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, gu, gf, lam, ctypes.c_void_p(0x300000),
+                                     need, None) == ALIAS
