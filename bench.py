@@ -374,6 +374,29 @@ def run_precision(args):
         r = {"gpix_iter_s": n * n * iters / (min(times) * 1e-3) / 1e9, "ms": min(times),
              "max_abs_err_vs_fp64": float(err.max()),
              "psnr_vs_fp64_db": 10 * np.log10(1.0 / mse) if mse > 0 else float("inf")}
+        if name == "f32":
+            # the single-pass kernels at this size: one evaluation (8 B per pixel) and one-step
+            # launches (12 B per pixel-iteration), against the measured copy bandwidth
+            peak, _ = peaks()
+            hw = torch.empty_like(f)
+
+            def best(fn, reps=5):
+                fn()
+                ts = []
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    fn()
+                    b.record()
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b))
+                return min(ts)
+            te = best(lambda: wmc.eval(f, out=hw))
+            t1 = best(lambda: wmc.denoise(f, LAM, STEP, 10, out=out, steps_per_launch=1, workspace=ws)) / 10
+            r["single_pass"] = {"eval_ms": te, "eval_hbm_frac": 8 * n * n / (te * 1e-3) / 1e9 / peak,
+                                "step_ms": t1, "step_hbm_frac": 12 * n * n / (t1 * 1e-3) / 1e9 / peak,
+                                "kernel": "wmc::stream4_kernel (4 cells per lane)"}
+            del hw
         if name in ref_bf:
             e2 = np.abs(got - ref_bf[name])
             r["max_abs_err_vs_emulated_storage"] = float(e2.max())
