@@ -400,7 +400,11 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
         __syncthreads();
     }
 
-    // ---- T steps: ping-pong buf0 -> buf1 -> buf0 ...; the last one writes the output tile
+    // ---- T steps: ping-pong buf0 -> buf1 -> buf0 ...; the last one writes the output tile.
+    // A warp whose cells all lie beyond the ring just outside the image (rows >= h + 1, or
+    // columns >= w + 1: tiles that overhang the image's bottom or right edge) has nothing that
+    // any in-image cell reads, so it skips the arithmetic (it still takes part in the barriers).
+    const bool idle = (Y0 + c.ib >= h + 1) | (X0 + 2 + 64 * (warp & 1) >= w + 1);
 #pragma unroll 1
     for (int s = 0; s < T - 1; ++s) {
         const float *src = (s & 1) ? buf1 : buf0;
@@ -409,7 +413,7 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
             tile_step<WRITE_INTERIOR, S, BND>(src, dst, c, g);
             __syncthreads();
         } else {
-            tile_step<WRITE_BORDER, S, BND>(src, dst, c, g);
+            if (!idle) tile_step<WRITE_BORDER, S, BND>(src, dst, c, g);
             __syncthreads();
             if (BND == BND_REPLICATE) {
                 refresh_ring<S>(dst, X0, Y0, h, w, tid);
@@ -417,6 +421,7 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
             }
         }
     }
+    if (idle) return true;  // none of its cells is an output cell inside the image
     int64_t ldo;
     S *out = out_of(&ldo);
     tile_step<WRITE_GLOBAL, S, BND>(((T - 1) & 1) ? buf1 : buf0, nullptr, c, g,
