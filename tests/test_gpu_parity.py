@@ -325,3 +325,18 @@ def test_denoise_graph_capture_replay():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+@pytest.mark.parametrize("shape", [(59, 117), (117, 233), (175, 65), (3, 130), (130, 3), (61, 61)])
+def test_overhanging_tiles_bitwise_invariant(bnd, shape):
+    """Images one cell past a whole number of output tiles (T = 4: 116 x 58, T = 8: 108 x 50),
+    where the last tile row or column overhangs the image and its outer warps skip work: every
+    T still gives the one-step-per-launch bits."""
+    f = to_gpu(synth.make_image(*shape, seed=sum(shape), sigma=0.1))
+    ref = wmc().denoise(f, 1.0, 0.25, 11, bnd, steps_per_launch=1)
+    for T in (2, 4, 5, 8):
+        assert torch.equal(wmc().denoise(f, 1.0, 0.25, 11, bnd, steps_per_launch=T), ref), T
+    bf = f.to(torch.bfloat16)
+    ref16 = wmc().denoise(bf, 1.0, 0.25, 11, bnd, steps_per_launch=1)
+    assert torch.equal(wmc().denoise(bf, 1.0, 0.25, 11, bnd, steps_per_launch=4), ref16)
