@@ -10,13 +10,14 @@
 //   loaded window  [X0, X0+LW) x [Y0, Y0+LH)       one 2-D TMA box, zero-filled outside the image
 //   updated cells  [X0+2, X0+2+CW) x [Y0+1, Y0+1+CH)    every step (CW = 128, CH = 64)
 //   exact after T  [X0+1+T, X0+3+CW-T) x [Y0+T, Y0+2+CH-T)
-//   written back   [x0, x0+OWt) x [y0, y0+OHt),  x0 = X0 + M, y0 = Y0 + T
-// M (>= T+1) is a multiple of the TMA alignment (16 bytes of elements).  The output tile size
+//   written back   [x0, x0+OWt) x [y0, y0+OHt),  X0 = x0 - (T+1) rounded down to the TMA
+//                  alignment (16 bytes of elements), y0 = Y0 + T
+// The output tile size
 // (OWt, OHt) is a launch parameter: a single-image launch uses the largest exact tile of its T
 // (Out<S,T>); a batch uses the tile of its deepest T for every launch, which any shallower
 // launch also covers exactly (its exact region is larger), so one tile table serves them all.
-// Output tile origins are multiples of the TMA alignment, which keeps every TMA x-coordinate
-// aligned.
+// Each tile rounds its own window origin down to the TMA alignment, which keeps every TMA
+// x-coordinate aligned without constraining where output tiles start.
 //
 // Threads: 16 warps as 2 (x) x 8 (y); lane l of warp (wx, wy) updates columns j = 2 + 64 wx + l
 // and j + 32 for rows i = 1 + 8 wy .. 8 + 8 wy.  The two columns are the two lanes of packed
@@ -74,13 +75,21 @@ template <typename S> struct Geom {
     static constexpr int SMEM = 2 * BUF * 4 + STAGE_BYTES + 128;  // + alignment slack
 };
 
-// Output tile of a T-step single-image launch: margin M (>= T+1, TMA-aligned), width OW, height OH.
+// Output tile of a T-step single-image launch, width OW and height OH.  After T steps the window
+// is exact on columns [X0 + T + 1, X0 + CW + 3 - T); the window origin is the output origin
+// x0 less T + 1, rounded down to the TMA alignment A (window_x0), so the output origin sits
+// T + 1 .. T + A columns into the window and OW = CW + 3 - 2T - A always fits.  Rows need no
+// alignment: y0 - T.
 template <typename S, int T> struct Out {
     static constexpr int A = Geom<S>::A;
-    static constexpr int M = A * ((T + 1 + A - 1) / A);
-    static constexpr int OW = A * ((kCW + 3 - T - M) / A);
+    static constexpr int OW = kCW + 3 - 2 * T - A;
     static constexpr int OH = kCH + 2 - 2 * T;
 };
+
+template <typename S, int T>
+__host__ __device__ __forceinline__ int window_x0(int x0) {
+    return (x0 - (T + 1)) & ~(Geom<S>::A - 1);  // floor to a multiple of A (also below 0)
+}
 
 // One image of a batch (device memory; 64-byte aligned for the tensor maps).
 struct alignas(64) BatchImage {
@@ -297,7 +306,6 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
                                          uint64_t *bar, uint32_t phase, OutFn out_of) {
     using G = Geom<S>;
     constexpr int LW = G::LW, LH = G::LH, BUF = G::BUF;
-    constexpr int M = Out<S, T>::M;
     TileCtx c;
     c.h = jb.h;
     c.w = jb.w;
@@ -305,7 +313,7 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     c.c_h = jb.c_h;
     const int h = c.h, w = c.w;
     const int x0 = jb.x0, y0 = jb.y0;
-    const int X0 = x0 - M, Y0 = y0 - T;
+    const int X0 = window_x0<S, T>(x0), Y0 = y0 - T;
     const int tid = threadIdx.x;
     const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
 
