@@ -305,8 +305,8 @@ static_assert(sizeof(BatchPlan) <= sizeof(wmc_batch_t), "plan does not fit wmc_b
 
 void out_tile(wmc_dtype_t dtype, int T, int *owt, int *oht) {
     // Out<S, T> for the storage type; computed like the device-side struct.
-    const int A = dtype == WMC_F32 ? 4 : 8;
-    *owt = wmc::kCW + 3 - 2 * T - A;
+    (void)dtype;
+    *owt = wmc::kCW + 2 - 2 * T;
     *oht = wmc::kCH + 2 - 2 * T;
 }
 

@@ -8,10 +8,10 @@
 //
 // Geometry (element coordinates; X0, Y0 = global position of shared cell (0,0)):
 //   loaded window  [X0, X0+LW) x [Y0, Y0+LH)       one 2-D TMA box, zero-filled outside the image
-//   updated cells  [X0+2, X0+2+CW) x [Y0+1, Y0+1+CH)    every step (CW = 128, CH = 64)
-//   exact after T  [X0+1+T, X0+3+CW-T) x [Y0+T, Y0+2+CH-T)
+//   updated cells  [X0+2+d, X0+2+d+CW) x [Y0+1, Y0+1+CH)    every step (CW = 128, CH = 64)
+//   exact after T  [X0+1+d+T, X0+3+d+CW-T) x [Y0+T, Y0+2+CH-T)
 //   written back   [x0, x0+OWt) x [y0, y0+OHt),  X0 = x0 - (T+1) rounded down to the TMA
-//                  alignment (16 bytes of elements), y0 = Y0 + T
+//                  alignment (16 bytes of elements), d = x0 - (T+1) - X0, y0 = Y0 + T
 // The output tile size
 // (OWt, OHt) is a launch parameter: a single-image launch uses the largest exact tile of its T
 // (Out<S,T>); a batch uses the tile of its deepest T for every launch, which any shallower
@@ -19,7 +19,7 @@
 // Each tile rounds its own window origin down to the TMA alignment, which keeps every TMA
 // x-coordinate aligned without constraining where output tiles start.
 //
-// Threads: 16 warps as 2 (x) x 8 (y); lane l of warp (wx, wy) updates columns j = 2 + 64 wx + l
+// Threads: 16 warps as 2 (x) x 8 (y); lane l of warp (wx, wy) updates columns j = 2 + d + 64 wx + l
 // and j + 32 for rows i = 1 + 8 wy .. 8 + 8 wy.  The two columns are the two lanes of packed
 // FP32x2 arithmetic: every operand pair (west, centre, east neighbours of both cells) is read
 // by two conflict-free 4-byte shared loads straight into an aligned register pair, so no
@@ -67,7 +67,9 @@ constexpr int kTileThreadsV2 = 32 * kTileWX * kTileWY;  // 512
 
 template <typename S> struct Geom {
     static constexpr int A = 16 / (int)sizeof(S);                 // TMA x alignment (elements)
-    static constexpr int LW = ((kCW + 3 + A - 1) / A) * A;        // loaded width
+    // loaded width: the updated columns start 2 + d into the window (d < A, below) and their
+    // east neighbours reach column 130 + d
+    static constexpr int LW = ((kCW + 2 + A + A - 1) / A) * A;
     static constexpr int LH = kCH + 2;                            // loaded height
     static constexpr int P = LW;                                  // shared pitch (floats)
     static constexpr int BUF = LH * P;                            // floats per buffer
@@ -75,14 +77,12 @@ template <typename S> struct Geom {
     static constexpr int SMEM = 2 * BUF * 4 + STAGE_BYTES + 128;  // + alignment slack
 };
 
-// Output tile of a T-step single-image launch, width OW and height OH.  After T steps the window
-// is exact on columns [X0 + T + 1, X0 + CW + 3 - T); the window origin is the output origin
-// x0 less T + 1, rounded down to the TMA alignment A (window_x0), so the output origin sits
-// T + 1 .. T + A columns into the window and OW = CW + 3 - 2T - A always fits.  Rows need no
-// alignment: y0 - T.
+// Output tile of a T-step single-image launch, width OW and height OH.  The window origin is the
+// output origin x0 less T + 1, rounded down to the TMA alignment A (window_x0); the d = 0..A-1
+// columns lost to the rounding shift the updated columns (2 + d .. 129 + d in the window), so
+// after T steps the window is exact on exactly [x0, x0 + CW + 2 - 2T).  Rows: y0 - T.
 template <typename S, int T> struct Out {
-    static constexpr int A = Geom<S>::A;
-    static constexpr int OW = kCW + 3 - 2 * T - A;
+    static constexpr int OW = kCW + 2 - 2 * T;
     static constexpr int OH = kCH + 2 - 2 * T;
 };
 
@@ -343,7 +343,7 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
 
     // ---- per-thread geometry and f (overlaps the load)
     const int lane = tid & 31, warp = tid >> 5;
-    c.j = 2 + 64 * (warp & 1) + lane;
+    c.j = 2 + (x0 - (T + 1) - X0) + 64 * (warp & 1) + lane;  // shifted by the rounding d
     c.ib = 1 + kRY * (warp >> 1);
     c.X0 = X0;
     c.Y0 = Y0;
@@ -412,7 +412,7 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     // A warp whose cells all lie beyond the ring just outside the image (rows >= h + 1, or
     // columns >= w + 1: tiles that overhang the image's bottom or right edge) has nothing that
     // any in-image cell reads, so it skips the arithmetic (it still takes part in the barriers).
-    const bool idle = (Y0 + c.ib >= h + 1) | (X0 + 2 + 64 * (warp & 1) >= w + 1);
+    const bool idle = (Y0 + c.ib >= h + 1) | (c.gx - lane >= w + 1);
 #pragma unroll 1
     for (int s = 0; s < T - 1; ++s) {
         const float *src = (s & 1) ? buf1 : buf0;
