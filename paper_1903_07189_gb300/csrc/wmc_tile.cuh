@@ -352,15 +352,16 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     c.cin1 = (c.gx + 32 >= 0) & (c.gx + 32 < w);
     c.out0 = c.cin0 & (c.gx >= x0) & (c.gx < x0 + owt);
     c.out1 = c.cin1 & (c.gx + 32 >= x0) & (c.gx + 32 < x0 + owt);
-    unsigned in_rows = 0;  // bit k: image row Y0 + ib + k exists
-    c.out_rows = 0;
-#pragma unroll
-    for (int k = 0; k < kRY; ++k) {
-        const int gy = Y0 + c.ib + k;
-        const bool rin = (gy >= 0) & (gy < h);
-        in_rows |= (rin ? 1u : 0u) << k;
-        c.out_rows |= ((rin & (gy >= y0) & (gy < y0 + oht)) ? 1u : 0u) << k;
-    }
+    // bit k of in_rows: image row Y0 + ib + k exists; of out_rows: it is also an output row.
+    // Both are contiguous ranges of the thread's kRY rows.
+    auto row_range = [](int lo, int hi) -> unsigned {  // bits [max(lo,0), min(hi,kRY))
+        lo = max(lo, 0);
+        hi = min(hi, kRY);
+        return hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
+    };
+    const int r0 = Y0 + c.ib;
+    const unsigned in_rows = row_range(-r0, h - r0);
+    c.out_rows = in_rows & row_range(y0 - r0, y0 + oht - r0);
     float2 g[kRY];
     {
         const float2 cf = make_float2(jb.c_f, jb.c_f);
