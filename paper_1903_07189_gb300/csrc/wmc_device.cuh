@@ -138,12 +138,15 @@ template <> struct Store<__nv_bfloat16> {
         return __bfloat162float(__float2bfloat16_rn(v));
     }
     // both lanes rounded by one paired conversion (each to nearest even, as round())
-    static __device__ __forceinline__ float2 round2(float2 v) {
-        return __bfloat1622float2(__floats2bfloat162_rn(v.x, v.y));
-    }
     // two elements packed in 32 bits (lower address in the low half) widened to FP32
     static __device__ __forceinline__ float2 unpack2(uint32_t bits) {
         return make_float2(__uint_as_float(bits << 16), __uint_as_float(bits & 0xffff0000u));
+    }
+    static __device__ __forceinline__ float2 round2(float2 v) {
+        const __nv_bfloat162 r = __floats2bfloat162_rn(v.x, v.y);
+        uint32_t bits;
+        memcpy(&bits, &r, sizeof bits);
+        return unpack2(bits);  // widening a bfloat16 is a shift
     }
     static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v) {
         *p = __float2bfloat16_rn(v);
