@@ -12,10 +12,10 @@
 //   exact after T  [X0+1+d+T, X0+3+d+CW-T) x [Y0+T, Y0+2+CH-T)
 //   written back   [x0, x0+OWt) x [y0, y0+OHt),  X0 = x0 - (T+1) rounded down to the TMA
 //                  alignment (16 bytes of elements), d = x0 - (T+1) - X0, y0 = Y0 + T
-// The output tile size
-// (OWt, OHt) is a launch parameter: a single-image launch uses the largest exact tile of its T
-// (Out<S,T>); a batch uses the tile of its deepest T for every launch, which any shallower
-// launch also covers exactly (its exact region is larger), so one tile table serves them all.
+// The output tile size (OWt, OHt) is a launch parameter: a single-image launch uses the largest
+// exact tile of its T (Out<S,T>); a batch uses the tile of its deepest T for every launch, which
+// any shallower launch also covers exactly (its exact region is larger), so one tile table
+// serves them all.
 // Each tile rounds its own window origin down to the TMA alignment, which keeps every TMA
 // x-coordinate aligned without constraining where output tiles start.
 //
@@ -31,7 +31,8 @@
 // outside the image are rewritten as 0 every step.  REPLICATE: the ring of cells just outside
 // the image is kept equal to its nearest in-image cell (refreshed after the load and after every
 // step, in tiles touching the border only), so in-image cells read their neighbours without any
-// clamping and produce exactly what clamped reads would.
+// clamping and produce exactly what clamped reads would.  Warps whose cells all lie beyond that
+// ring (tiles overhanging the image) skip the arithmetic: no in-image cell reads those cells.
 //
 // Shared memory always holds FP32; for BF16/FP16 storage the TMA box lands in a staging area
 // and is widened once, and every step rounds its result to the storage type, so the arithmetic
