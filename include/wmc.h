@@ -176,9 +176,10 @@ wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_h
  *   out[0] = sum_p |H^w(U)(p)|,  out[1] = 1/2 sum_p (U - f)^2,  out[2] = sum_p (U - clean)^2
  *   (out[1] = 0 when f is NULL, out[2] = 0 when clean is NULL).
  *   u, f, clean: device, h x w, pitch ld, type dtype (f, clean may be NULL).  out: DEVICE, 3 doubles, written (not
- *   accumulated).  Per-thread partial sums run in FP32 over at most 16 pixels and in FP64
- *   beyond; the summation order is fixed, so repeated calls give identical results.  The
- *   workspace size depends on h and w (one FP64 triple per CTA).
+ *   accumulated).  Sums run in FP32 over at most 16 pixels, then in double-float (an FP32
+ *   pair, about 44 bits) up to one warp's share, and in FP64 beyond; the summation order is
+ *   fixed by h and w alone, so repeated calls give identical results.  The workspace size
+ *   depends on h and w (one FP64 triple per CTA, at most 304 CTAs).
  *   workspace: device, >= wmc_energy_workspace_size() bytes, aligned as above.
  */
 size_t wmc_energy_workspace_size(int32_t h, int32_t w);

@@ -3,22 +3,54 @@
 //   E_data = 1/2 sum_p (U - f)^2        (the L2 data term of Eq. 1, A = I)
 //   SSE    = sum_p (U - clean)^2        (for PSNR against a known clean image)
 //
-// The image is streamed like the single-pass kernels (a warp owns 64 columns, lanes hold column
-// pairs, neighbours by warp shuffle, each thread a strip of kStreamRY rows with every load issued
-// up front).  Each thread sums its 16 cells in FP32; everything after that is FP64: a fixed
-// shuffle tree inside the CTA, one partial per CTA, and the last CTA to finish (ticket counter)
-// adds the partials in CTA order.  The assignment and the order never change, so the result is
-// bitwise reproducible.
+// The image is streamed like the single-pass kernels: lanes hold 2 adjacent cells (any type) or 4
+// (FP32 rows aligned to 16 bytes), neighbours come by warp shuffle, and each thread takes a strip
+// of rows with every load issued up front, summing its 16 cells in FP32.  A CTA walks a fixed run
+// of strips and adds each strip's sums into double-float (hi + lo) accumulators; a shuffle tree
+// of double-float adds per warp, then FP64: the warps in order, one partial per CTA, and the last
+// CTA to finish (ticket counter) adds the partials in CTA order.  The assignment and the order
+// never change, so the result is bitwise reproducible.
 #include "wmc_device.cuh"
 #include "wmc_internal.h"
 #include "wmc_stream.cuh"
 
 namespace wmc {
 
+// Pair layout: a unit of work is one strip, a CTA's 512 columns times kStreamRY rows.  The grid
+// is a pure function of the image size -- at most kEnergyCTAs CTAs (2 resident per SM on 152
+// SMs, one wave) -- and CTA b walks the units [b*U/N, (b+1)*U/N) in order.
+// Four cells per lane: a CTA owns 1024 columns and a band of rows (a multiple of 4), and its
+// threads march down the band.  Either way the summation order never changes.
+#ifndef WMC_ENERGY_MIN_BLOCKS
+#define WMC_ENERGY_MIN_BLOCKS 2
+#endif
+constexpr int kEnergyCTAs = WMC_ENERGY_MIN_BLOCKS * 152;
+
+static int64_t energy_grid(int32_t h, int32_t w) {
+    const int64_t u = (int64_t)((w + kStreamWarps * 64 - 1) / (kStreamWarps * 64)) *
+                      ((h + kStreamRY - 1) / kStreamRY);
+    return u < kEnergyCTAs ? u : kEnergyCTAs;
+}
+
+struct MarchGeom {
+    int nbx, band_rows, nbands;
+};
+
+__host__ __device__ __forceinline__ MarchGeom march_geom(int32_t h, int32_t w) {
+    MarchGeom g;
+    g.nbx = (int)(((int64_t)w + kStreamWarps * 128 - 1) / (kStreamWarps * 128));
+    int64_t nb = kEnergyCTAs / g.nbx;
+    if (nb < 1) nb = 1;
+    const int64_t br = (((int64_t)h + nb - 1) / nb + 3) & ~(int64_t)3;
+    g.band_rows = (int)br;
+    g.nbands = (int)(((int64_t)h + br - 1) / br);
+    return g;
+}
+
 int64_t energy_blocks(int32_t h, int32_t w) {
-    const int64_t nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
-    const int64_t nby = (h + kStreamRY - 1) / kStreamRY;
-    return nbx * nby;
+    const MarchGeom g = march_geom(h, w);
+    const int64_t a = energy_grid(h, w), b = (int64_t)g.nbx * g.nbands;
+    return a > b ? a : b;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -27,83 +59,68 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <typename S, int BND, bool VEC>
-__global__ void __launch_bounds__(kStreamWarps * 32)
-    energy_kernel(const S *__restrict__ u, const S *__restrict__ f, const S *__restrict__ clean,
-                  int h, int w, int64_t ld, double *__restrict__ out,
-                  double *__restrict__ partials, unsigned int *__restrict__ ticket) {
-    constexpr int R = kStreamRY;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
-    const int by = (int)(blockIdx.x / nbx), bx = (int)(blockIdx.x - (unsigned)by * nbx);
-    const int x = ((bx * kStreamWarps + warp) * 32 + lane) * 2;
-    const int y0 = by * R;
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
-    if ((x & ~63) < w) {  // warp-uniform
-        float2 v[R + 2];
-        float el[R + 2], er[R + 2];
+// Double-float accumulator: the unevaluated sum hi + lo.  Adding a float is exact in (s, e) by
+// Knuth's TwoSum; the rounding errors collect in lo.  All summands here are >= 0, so no
+// cancellation occurs and the accumulated value keeps about 44 bits.  GB300 issues FP64 at a
+// small fraction of its FP32 rate, so only the last steps of the reduction run in FP64.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void df_add(DF &a, float x) {
+    float s, e;
+    two_sum(a.hi, x, s, e);
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, e);
+}
+
+__device__ __forceinline__ DF df_merge(DF a, DF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+    const float hi = __fadd_rn(s, lo);  // renormalise (Fast2Sum: |s| >= |lo|)
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ DF df_warp_sum(DF v) {
 #pragma unroll
-        for (int k = 0; k < R + 2; ++k) {
-            bool ok;
-            const int y = row_index<BND>(y0 - 1 + k, h, &ok);
-            const S *row = u + (int64_t)y * ld;
-            v[k] = load_pair<S, BND, VEC>(row, x, w, ok);
-            el[k] = (lane == 0) ? load_one<S, BND>(row, x - 1, w, ok) : 0.0f;
-            er[k] = (lane == 31) ? load_one<S, BND>(row, x + 2, w, ok) : 0.0f;
-        }
-        float2 fv[R], cv[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const int y = min(y0 + k, h - 1);
-            fv[k] = f ? load_pair<S, BND_ZERO, VEC>(f + (int64_t)y * ld, x, w, true) : make_float2(0.f, 0.f);
-            cv[k] = clean ? load_pair<S, BND_ZERO, VEC>(clean + (int64_t)y * ld, x, w, true)
-                          : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            float lf = __shfl_up_sync(0xffffffffu, v[k].y, 1);
-            float rt = __shfl_down_sync(0xffffffffu, v[k].x, 1);
-            float lf1 = __shfl_up_sync(0xffffffffu, v[k + 1].y, 1);
-            float rt1 = __shfl_down_sync(0xffffffffu, v[k + 1].x, 1);
-            float lf2 = __shfl_up_sync(0xffffffffu, v[k + 2].y, 1);
-            float rt2 = __shfl_down_sync(0xffffffffu, v[k + 2].x, 1);
-            if (lane == 0) { lf = el[k]; lf1 = el[k + 1]; lf2 = el[k + 2]; }
-            if (lane == 31) { rt = er[k]; rt1 = er[k + 1]; rt2 = er[k + 2]; }
-            const int y = y0 + k;
-            if (y >= h) continue;
-            const float h0 = half_laplace12(lf, v[k].x, v[k].y, lf1, v[k + 1].x, v[k + 1].y, lf2,
-                                            v[k + 2].x, v[k + 2].y);
-            const float h1 = half_laplace12(v[k].x, v[k].y, rt, v[k + 1].x, v[k + 1].y, rt1,
-                                            v[k + 2].x, v[k + 2].y, rt2);
-            const bool in0 = x < w, in1 = x + 1 < w;
-            if (in0) s0 += fabsf(h0) * (1.0f / 12.0f);
-            if (in1) s0 += fabsf(h1) * (1.0f / 12.0f);
-            if (f) {
-                const float d0 = v[k + 1].x - fv[k].x, d1 = v[k + 1].y - fv[k].y;
-                if (in0) s1 = fmaf(d0, d0, s1);
-                if (in1) s1 = fmaf(d1, d1, s1);
-            }
-            if (clean) {
-                const float d0 = v[k + 1].x - cv[k].x, d1 = v[k + 1].y - cv[k].y;
-                if (in0) s2 = fmaf(d0, d0, s2);
-                if (in1) s2 = fmaf(d1, d1, s2);
-            }
-        }
+    for (int o = 16; o > 0; o >>= 1) {
+        DF t;
+        t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        // lanes l and l^o merge the same two operands in the same order
+        v = ((threadIdx.x & o) == 0) ? df_merge(v, t) : df_merge(t, v);
     }
-    double acc[3] = {(double)s0, 0.5 * (double)s1, (double)s2};
+    return v;
+}
+
+// Thread sums (12 |H^w|, the squared data residual, the squared error) as double-float pairs:
+// a fixed shuffle tree per warp, one FP64 value per warp (hi + lo), the 8 warps in order, one
+// partial per CTA, and the last CTA to finish (ticket counter) adds the partials in CTA order.
+__device__ __forceinline__ void energy_reduce(const DF (&acc)[3], double *__restrict__ out,
+                                              double *__restrict__ partials,
+                                              unsigned int *__restrict__ ticket) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ double red[3][kStreamWarps];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double t = warp_sum(acc[k]);
-        if (lane == 0) red[k][warp] = t;
+        const DF t = df_warp_sum(acc[k]);
+        if (lane == 0) red[k][warp] = (double)t.hi + (double)t.lo;
     }
     __syncthreads();
     __shared__ bool is_last;
     if (threadIdx.x < 3) {
         double t = 0.0;
         for (int i = 0; i < kStreamWarps; ++i) t += red[threadIdx.x][i];
-        partials[(int64_t)blockIdx.x * 3 + threadIdx.x] = t;
+        // the thread sums hold 12 |H^w| and (U - f)^2: scale once, in FP64
+        partials[(int64_t)blockIdx.x * 3 + threadIdx.x] =
+            threadIdx.x == 0 ? t / 12.0 : threadIdx.x == 1 ? 0.5 * t : t;
     }
     __threadfence();
     __syncthreads();
@@ -117,6 +134,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
     for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
 #pragma unroll
         for (int k = 0; k < 3; ++k) a[k] += __ldcg(partials + (int64_t)b * 3 + k);
+    __syncthreads();  // red[] is reused
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const double t = warp_sum(a[k]);
@@ -130,12 +148,203 @@ __global__ void __launch_bounds__(kStreamWarps * 32)
     }
 }
 
+// One strip in the pair layout: a lane holds 2 adjacent cells, a warp 64 columns, the thread
+// kStreamRY rows (16 cells, summed in FP32).  Loads are issued before any arithmetic.
+template <typename S, int BND, bool VEC>
+__device__ __forceinline__ void energy_strip_pair(const S *__restrict__ u, const S *__restrict__ f,
+                                                  const S *__restrict__ clean, int h, int w,
+                                                  int64_t ld, int bx, int by, float (&s)[3]) {
+    constexpr int R = kStreamRY;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int x = ((bx * kStreamWarps + warp) * 32 + lane) * 2;
+    const int y0 = by * R;
+    if ((x & ~63) >= w) return;  // warp-uniform
+    float2 v[R + 2];
+    float el[R + 2], er[R + 2];
+#pragma unroll
+    for (int k = 0; k < R + 2; ++k) {
+        bool ok;
+        const int y = row_index<BND>(y0 - 1 + k, h, &ok);
+        const S *row = u + (int64_t)y * ld;
+        v[k] = load_pair<S, BND, VEC>(row, x, w, ok);
+        el[k] = (lane == 0) ? load_one<S, BND>(row, x - 1, w, ok) : 0.0f;
+        er[k] = (lane == 31) ? load_one<S, BND>(row, x + 2, w, ok) : 0.0f;
+    }
+    float2 fv[R], cv[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int y = min(y0 + k, h - 1);
+        fv[k] = f ? load_pair<S, BND_ZERO, VEC>(f + (int64_t)y * ld, x, w, true) : make_float2(0.f, 0.f);
+        cv[k] = clean ? load_pair<S, BND_ZERO, VEC>(clean + (int64_t)y * ld, x, w, true)
+                      : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        float lf = __shfl_up_sync(0xffffffffu, v[k].y, 1);
+        float rt = __shfl_down_sync(0xffffffffu, v[k].x, 1);
+        float lf1 = __shfl_up_sync(0xffffffffu, v[k + 1].y, 1);
+        float rt1 = __shfl_down_sync(0xffffffffu, v[k + 1].x, 1);
+        float lf2 = __shfl_up_sync(0xffffffffu, v[k + 2].y, 1);
+        float rt2 = __shfl_down_sync(0xffffffffu, v[k + 2].x, 1);
+        if (lane == 0) { lf = el[k]; lf1 = el[k + 1]; lf2 = el[k + 2]; }
+        if (lane == 31) { rt = er[k]; rt1 = er[k + 1]; rt2 = er[k + 2]; }
+        if (y0 + k >= h) continue;
+        const float h0 = half_laplace12(lf, v[k].x, v[k].y, lf1, v[k + 1].x, v[k + 1].y, lf2,
+                                        v[k + 2].x, v[k + 2].y);
+        const float h1 = half_laplace12(v[k].x, v[k].y, rt, v[k + 1].x, v[k + 1].y, rt1,
+                                        v[k + 2].x, v[k + 2].y, rt2);
+        const bool in0 = x < w, in1 = x + 1 < w;
+        if (in0) s[0] += fabsf(h0);
+        if (in1) s[0] += fabsf(h1);
+        if (f) {
+            const float d0 = v[k + 1].x - fv[k].x, d1 = v[k + 1].y - fv[k].y;
+            if (in0) s[1] = fmaf(d0, d0, s[1]);
+            if (in1) s[1] = fmaf(d1, d1, s[1]);
+        }
+        if (clean) {
+            const float d0 = v[k + 1].x - cv[k].x, d1 = v[k + 1].y - cv[k].y;
+            if (in0) s[2] = fmaf(d0, d0, s[2]);
+            if (in1) s[2] = fmaf(d1, d1, s[2]);
+        }
+    }
+}
+
+// Four cells per lane (FP32, 16-byte aligned rows): a warp holds 128 columns and its threads
+// march down the CTA's band with a three-row window (rows y-1, y, y+1) in registers, loading
+// the next 4 rows of U (and of f, clean) before computing any of them.  Each group of 4 rows
+// (16 cells) is summed in FP32 and added into the double-float accumulators.  HF, HC: f, clean
+// given (the unused terms cost no registers).
+template <int BND, bool HF, bool HC>
+__global__ void __launch_bounds__(kStreamWarps * 32, WMC_ENERGY_MIN_BLOCKS)
+    energy_march_kernel(const float *__restrict__ u, const float *__restrict__ f,
+                        const float *__restrict__ clean, int h, int w, int64_t ld,
+                        double *__restrict__ out, double *__restrict__ partials,
+                        unsigned int *__restrict__ ticket) {
+    const MarchGeom g = march_geom(h, w);
+    const int band = (int)(blockIdx.x / g.nbx), bx = (int)(blockIdx.x - (unsigned)band * g.nbx);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int x = ((bx * kStreamWarps + warp) * 32 + lane) * 4;
+    const int yb = band * g.band_rows, ye = min(yb + g.band_rows, h);
+    DF acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    auto load_row = [&](int y, float4 &v, float &el, float &er) {
+        bool ok;
+        const int yy = row_index<BND>(y, h, &ok);
+        const float *row = u + (int64_t)yy * ld;
+        v = load_quad<BND>(row, x, w, ok);
+        el = (lane == 0) ? load_one<float, BND>(row, x - 1, w, ok) : 0.0f;
+        er = (lane == 31) ? load_one<float, BND>(row, x + 4, w, ok) : 0.0f;
+    };
+    // left neighbour of the lane's first cell, right neighbour of its last
+    auto sides = [&](const float4 &v, float el, float er, float &l, float &r) {
+        l = __shfl_up_sync(0xffffffffu, v.w, 1);
+        r = __shfl_down_sync(0xffffffffu, v.x, 1);
+        if (lane == 0) l = el;
+        if (lane == 31) r = er;
+    };
+    if ((x & ~127) < w) {  // warp-uniform
+        float4 top, mid;
+        float tl, tr, ml, mr;
+        {
+            float e0, e1;
+            load_row(yb - 1, top, e0, e1);
+            sides(top, e0, e1, tl, tr);
+            load_row(yb, mid, e0, e1);
+            sides(mid, e0, e1, ml, mr);
+        }
+        for (int y = yb; y < ye; y += 4) {
+            float4 nv[4], fv[4], cv[4];
+            float nel[4], ner[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) load_row(y + 1 + k, nv[k], nel[k], ner[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int yy = min(y + k, h - 1);
+                fv[k] = HF ? load_quad<BND_ZERO>(f + (int64_t)yy * ld, x, w, true) : make_float4(0.f, 0.f, 0.f, 0.f);
+                cv[k] = HC ? load_quad<BND_ZERO>(clean + (int64_t)yy * ld, x, w, true) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            float s[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float bl, br;
+                sides(nv[k], nel[k], ner[k], bl, br);
+                if (y + k < ye) {  // uniform over the CTA
+                    const float4 a = top, b = mid, c = nv[k];
+                    const float hs[4] = {half_laplace12(tl, a.x, a.y, ml, b.x, b.y, bl, c.x, c.y),
+                                         half_laplace12(a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z),
+                                         half_laplace12(a.y, a.z, a.w, b.y, b.z, b.w, c.y, c.z, c.w),
+                                         half_laplace12(a.z, a.w, tr, b.z, b.w, mr, c.z, c.w, br)};
+                    const float uu[4] = {b.x, b.y, b.z, b.w};
+                    const float ff[4] = {fv[k].x, fv[k].y, fv[k].z, fv[k].w};
+                    const float cc[4] = {cv[k].x, cv[k].y, cv[k].z, cv[k].w};
+                    if (x + 3 < w) {  // every lane but those at the right edge
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) s[0] += fabsf(hs[q]);
+                        if (HF) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float d = uu[q] - ff[q];
+                                s[1] = fmaf(d, d, s[1]);
+                            }
+                        }
+                        if (HC) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float d = uu[q] - cc[q];
+                                s[2] = fmaf(d, d, s[2]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (x + q >= w) continue;
+                            s[0] += fabsf(hs[q]);
+                            const float d1 = uu[q] - ff[q], d2 = uu[q] - cc[q];
+                            if (HF) s[1] = fmaf(d1, d1, s[1]);
+                            if (HC) s[2] = fmaf(d2, d2, s[2]);
+                        }
+                    }
+                }
+                top = mid;
+                tl = ml;
+                tr = mr;
+                mid = nv[k];
+                ml = bl;
+                mr = br;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) df_add(acc[k], s[k]);
+        }
+    }
+    energy_reduce(acc, out, partials, ticket);
+}
+
+// Pair layout (any storage type): each strip's FP32 sums enter the thread's double-float
+// accumulators.
+template <typename S, int BND, bool VEC>
+__global__ void __launch_bounds__(kStreamWarps * 32, 2)
+    energy_kernel(const S *__restrict__ u, const S *__restrict__ f, const S *__restrict__ clean,
+                  int h, int w, int64_t ld, double *__restrict__ out,
+                  double *__restrict__ partials, unsigned int *__restrict__ ticket) {
+    const int nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
+    const int64_t units = (int64_t)nbx * ((h + kStreamRY - 1) / kStreamRY);
+    const int64_t u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
+    DF acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int64_t un = u0; un < u1; ++un) {
+        const int by = (int)(un / nbx), bx = (int)(un - (int64_t)by * nbx);
+        float s[3] = {0.f, 0.f, 0.f};
+        energy_strip_pair<S, BND, VEC>(u, f, clean, h, w, ld, bx, by, s);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) df_add(acc[k], s[k]);
+    }
+    energy_reduce(acc, out, partials, ticket);
+}
+
 template <typename S>
 static cudaError_t launch_energy_t(const void *u, const void *f, const void *clean, int32_t h,
                                    int32_t w, int64_t ld, int bnd, double *out, void *ws,
                                    cudaStream_t st) {
-    const int64_t nb = energy_blocks(h, w);
-    if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     unsigned int *ticket = static_cast<unsigned int *>(ws);
     double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + 256);
     cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st);
@@ -147,7 +356,28 @@ static cudaError_t launch_energy_t(const void *u, const void *f, const void *cle
     const bool vec = al(u) && al(f) && al(clean);
     const S *U = static_cast<const S *>(u), *F = static_cast<const S *>(f),
             *C = static_cast<const S *>(clean);
-    const unsigned g = (unsigned)nb, b = kStreamWarps * 32;
+    const unsigned b = kStreamWarps * 32;
+    if constexpr (sizeof(S) == 4) {
+        auto al16 = [&](const void *q) { return q == nullptr || ((uintptr_t)q % 16 == 0 && ld % 4 == 0); };
+        if (al16(u) && al16(f) && al16(clean)) {
+            const MarchGeom mg = march_geom(h, w);
+            const unsigned g = (unsigned)((int64_t)mg.nbx * mg.nbands);
+            auto go = [&](auto kern) { kern<<<g, b, 0, st>>>(U, F, C, h, w, ld, out, partials, ticket); };
+            const int sel = (bnd == BND_ZERO ? 4 : 0) | (f ? 2 : 0) | (clean ? 1 : 0);
+            switch (sel) {
+                case 0: go(energy_march_kernel<BND_REPLICATE, false, false>); break;
+                case 1: go(energy_march_kernel<BND_REPLICATE, false, true>); break;
+                case 2: go(energy_march_kernel<BND_REPLICATE, true, false>); break;
+                case 3: go(energy_march_kernel<BND_REPLICATE, true, true>); break;
+                case 4: go(energy_march_kernel<BND_ZERO, false, false>); break;
+                case 5: go(energy_march_kernel<BND_ZERO, false, true>); break;
+                case 6: go(energy_march_kernel<BND_ZERO, true, false>); break;
+                default: go(energy_march_kernel<BND_ZERO, true, true>); break;
+            }
+            return cudaGetLastError();
+        }
+    }
+    const unsigned g = (unsigned)energy_grid(h, w);
     if (bnd == BND_ZERO) {
         if (vec) energy_kernel<S, BND_ZERO, true><<<g, b, 0, st>>>(U, F, C, h, w, ld, out, partials, ticket);
         else energy_kernel<S, BND_ZERO, false><<<g, b, 0, st>>>(U, F, C, h, w, ld, out, partials, ticket);

@@ -5,6 +5,8 @@
   half an ulp of the stored result on top);
 - batch: the 512 uneven images (sides 64..1536), one 4-step launch per round; sampled images must
   equal the single-image path bit for bit, and one image's step is checked against the oracle;
+- scale: the 4096 x 4096 image after 20 iterations; its FP64 energies (the last kernel of every
+  benchmark step) against the oracle's;
 - diff: 32 images of 512 x 512, K = 50, checkpoints every 7: the forward equals wmc_denoise bit
   for bit, the gradients do not depend on the checkpoint spacing, and dL/dlambda agrees with a
   central difference of the loss.
@@ -115,3 +117,12 @@ def test_diff_config_properties():
         e[i] = eps
         fd = (loss(lam + e) - loss(lam - e)) / (2 * eps)
         assert abs(fd - float(gl7[i])) <= 0.05 * abs(fd) + 1e-9, (i, fd, float(gl7[i]))
+
+
+def test_scale_config_energies():
+    f = torch.from_numpy(synth.make_image(4096, 4096, seed=1, n_bumps=64, n_shapes=32, sigma=0.02)).to(DEV)
+    u = wmc().denoise(f, 1.0, 0.25, 20)
+    e = wmc().energy(u, f).cpu().numpy()
+    want = oracle.energies(host(u), host(f))
+    np.testing.assert_allclose(e[:2], want[:2], rtol=1e-6)
+    assert e[2] == 0.0 and np.array_equal(e, wmc().energy(u, f).cpu().numpy())

@@ -237,6 +237,25 @@ def test_energy_parity():
     assert np.array_equal(e, e2)  # fixed summation order
 
 
+@pytest.mark.parametrize("shape,ld", [((301, 1300), None), ((70, 133), 136), ((5, 4), None), ((2, 2049), 2052),
+                                      ((33, 218), None), ((19, 131), 133)])
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_energy_layouts(shape, ld, bnd):
+    """FP32 rows that are 16-byte aligned take the 4-cells-per-lane energy kernel, the rest the
+    pair layout; ragged widths and heights, NaN-filled pitch padding (never read), and the
+    optional f / clean terms must all match the oracle and repeat bitwise."""
+    f, clean = synth.make_image(*shape, seed=23, sigma=0.1, return_clean=True)
+    fg, cg = to_gpu(f, ld=ld), to_gpu(clean, ld=ld)
+    ug = wmc().denoise(fg, 1.0, 0.25, 3, boundary=bnd)
+    U = host(ug)
+    for args, want in [((ug, fg, cg), oracle.energies(U, host(fg), host(cg), boundary=bnd)),
+                       ((ug, fg, None), oracle.energies(U, host(fg), None, boundary=bnd)),
+                       ((ug, None, None), oracle.energies(U, None, None, boundary=bnd))]:
+        e = wmc().energy(*args, boundary=bnd).cpu().numpy()
+        np.testing.assert_allclose(e, want, rtol=2e-6, atol=1e-300)
+        assert np.array_equal(e, wmc().energy(*args, boundary=bnd).cpu().numpy())
+
+
 def test_host_entry_point_matches_device():
     f = synth.make_image(129, 257, seed=19)
     fh = torch.from_numpy(f).pin_memory()
