@@ -444,8 +444,9 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
     tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const TileV2Params p) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    float *buf0 = reinterpret_cast<float *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // 128-byte aligned start of the buffers, formed as an offset into the __shared__ array (not
+    // through an integer cast) so that every access below stays a shared-memory access
+    float *buf0 = reinterpret_cast<float *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     float *buf1 = buf0 + Geom<S>::BUF;
 
     // ---- this CTA's job: image, buffers, coefficients and output tile
