@@ -244,11 +244,11 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
                 if (in1) d[32] = rv.y;
             }
         } else {
-            if ((c.out_rows >> k) & 1u) {
-                S *o = orow + (int64_t)k * ld;  // row Y0 + ib + k, column gx
-                if (c.out0) Store<S>::store(o, v.x);
-                if (c.out1) Store<S>::store(o + 32, v.y);
-            }
+            // predicated stores, no branch: row Y0 + ib + k, columns gx and gx + 32
+            const bool rk = (c.out_rows >> k) & 1u;
+            S *o = orow + (int64_t)k * ld;
+            if (rk & c.out0) Store<S>::store(o, v.x);
+            if (rk & c.out1) Store<S>::store(o + 32, v.y);
         }
         r0 = r1;
         r1 = r2;
@@ -368,13 +368,13 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
         const float2 cf = make_float2(jb.c_f, jb.c_f);
         const S *fr = jb.f + (int64_t)(Y0 + c.ib) * jb.ld + c.gx;
 #pragma unroll
+        const bool hasf = jb.f != nullptr;
         for (int k = 0; k < kRY; ++k) {
-            float a = 0.0f, b = 0.0f;
-            if (jb.f != nullptr && ((in_rows >> k) & 1u)) {
-                const S *fk = fr + (int64_t)k * jb.ld;
-                if (c.cin0) a = Store<S>::load(fk);
-                if (c.cin1) b = Store<S>::load(fk + 32);
-            }
+            // predicated loads, no branch
+            const bool rk = hasf & ((in_rows >> k) & 1u);
+            const S *fk = fr + (int64_t)k * jb.ld;
+            const float a = (rk & c.cin0) ? Store<S>::load(fk) : 0.0f;
+            const float b = (rk & c.cin1) ? Store<S>::load(fk + 32) : 0.0f;
             g[k] = __fmul2_rn(cf, make_float2(a, b));
         }
     }
