@@ -367,8 +367,8 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     {
         const float2 cf = make_float2(jb.c_f, jb.c_f);
         const S *fr = jb.f + (int64_t)(Y0 + c.ib) * jb.ld + c.gx;
-#pragma unroll
         const bool hasf = jb.f != nullptr;
+#pragma unroll
         for (int k = 0; k < kRY; ++k) {
             // predicated loads, no branch
             const bool rk = hasf & ((in_rows >> k) & 1u);
