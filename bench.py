@@ -52,6 +52,14 @@ DEFAULT_T = 4
 # this image, from an ncu capture of a warm-L2 launch (67.15 MB read + 20.91 MB written); valid
 # for the default 4 steps per launch only.
 TILE_T4_DRAM_BYTES = 88.06e6
+# GB300 HBM3e nominal bandwidth (GB/s); fractions are reported against it and against the
+# measured copy bandwidth
+NOMINAL_HBM_GBS = 8000.0
+# The paper's one throughput figure (the abstract and Sec. IV-D, support region and complexity):
+# WMC computed at 33.2 gigapixels/s on an NVIDIA TITAN X (Pascal); image size, precision and pass
+# not stated.  Another machine: context for the eval pass, not a target.
+PAPER_EVAL_CONTEXT = {"value": 33.2, "unit": "Gpix/s", "hardware": "NVIDIA TITAN X (Pascal)",
+                      "note": "paper figure; size, precision and pass not stated"}
 
 
 def parse():
@@ -291,9 +299,10 @@ def run_gpu(args):
                     "algorithmic_ops_per_px_iter": FMA_OPS_PER_PX_ITER, "launch_ms": launch_ms,
                     # the same iterations unblocked would move 12 B per pixel-iteration
                     "unblocked_equivalent": {"gbs": value * BYTES_PER_PX_LAUNCH,
-                                             "frac": value * BYTES_PER_PX_LAUNCH / peak},
+                                             "frac": value * BYTES_PER_PX_LAUNCH / peak,
+                                             "frac_of_nominal": value * BYTES_PER_PX_LAUNCH / NOMINAL_HBM_GBS},
                     "hbm": {"achieved": hbm_achieved, "peak": peak, "unit": "GB/s", "frac": hbm_achieved / peak,
-                            "peak_kind": peak_kind}}
+                            "peak_kind": peak_kind, "frac_of_nominal": hbm_achieved / NOMINAL_HBM_GBS}}
     else:
         roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": peak, "unit": "GB/s",
                     "frac": hbm_achieved / peak, "traffic": None, "kernel": "wmc::stream_kernel (flow step)",
@@ -323,7 +332,10 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = host_threads()
         rate, dt = cpu_oracle_rate(u_host, 2048, 32, threads)
+        rate1, dt1 = cpu_oracle_rate(u_host, 512, 32, 1)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": f"512x512 top-left crop, 32 iterations ({dt1:.1f} s)"},
                "sample": f"2048x2048 top-left crop, 32 iterations (FP64 oracle, {threads} threads, {dt:.1f} s wall, "
                          f"{dt * threads:.0f} core-s)"}
 
@@ -337,7 +349,9 @@ def run_gpu(args):
                 "eval": {"ms": eval_ms, "gpix_s": H * W / (eval_ms * 1e-3) / 1e9,
                          "hbm_gbs": 8 * H * W / (eval_ms * 1e-3) / 1e9,
                          "hbm_frac": 8 * H * W / (eval_ms * 1e-3) / 1e9 / peak,
-                         "kernel": "wmc::stream4_kernel (eval, 4 cells per lane), 8 B per pixel"},
+                         "hbm_frac_of_nominal": 8 * H * W / (eval_ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
+                         "kernel": "wmc::stream4_kernel (eval, 4 cells per lane), 8 B per pixel",
+                         "paper_context": PAPER_EVAL_CONTEXT},
                 # U was written by the last flow launch, so part of it is still in L2
                 "energy": {"ms": energy_ms, "hbm_gbs": 8 * H * W / (energy_ms * 1e-3) / 1e9,
                            "hbm_frac": 8 * H * W / (energy_ms * 1e-3) / 1e9 / peak,
@@ -436,18 +450,29 @@ def run_batch(args):
     """512 images, sides uniform in [64, 1536] (seeded), image i: seed 1000+i, 8 bumps + 4 shapes,
     sigma_i ~ U[0.01, 0.15], lambda_i ~ U[0.5, 2], step_i = 0.5/(1+lambda_i); 300 iterations.
     Aggregate pixel-iterations/s of (a) one batch plan run captured in a CUDA graph and replayed,
-    (b) the same run launched directly, (c) looping the single-image path over the images."""
+    (b) the same run launched directly, (c) looping the single-image path over the images.
+    Under torchrun the images are partitioned over the ranks by pixel count (wmc.shard_lpt; no
+    communication on the data path) and each rate is all ranks' pixel-iterations over the
+    slowest rank's time (strong scaling: the batch is fixed)."""
     import torch
     from paper_1903_07189_gb300 import synth, wmc
-    dev = torch.device("cuda", 0)
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     n, iters = 512, 300
     sizes = synth.batch_sizes(n)
     params = synth.batch_params(n)
-    fs = [torch.from_numpy(synth.make_image(h, w, seed=1000 + i, n_bumps=8, n_shapes=4, sigma=sg)).to(dev)
-          for i, ((h, w), (sg, _)) in enumerate(zip(sizes, params))]
-    lams = [l for _, l in params]
+    costs = [h * w for h, w in sizes]
+    owner, loads = wmc.shard_lpt(costs, world)
+    mine = [i for i in range(n) if owner[i] == rank]
+    fs = [torch.from_numpy(synth.make_image(sizes[i][0], sizes[i][1], seed=1000 + i, n_bumps=8,
+                                            n_shapes=4, sigma=params[i][0])).to(dev) for i in mine]
+    lams = [params[i][1] for i in mine]
     steps = [0.5 / (1 + l) for l in lams]
-    px = sum(h * w for h, w in sizes)
+    px = sum(costs)
     # steps per launch picked by the library's autotuner (times each candidate on this batch)
     if args.steps_per_launch:
         T, tune = args.steps_per_launch, {}
@@ -463,24 +488,30 @@ def run_batch(args):
     with torch.cuda.graph(graph):
         b.run(iters)
 
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
     def timed(fn, reps):
         ts = []
         for _ in range(reps):
+            barrier()
             a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             fn()
             e.record()
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(e))
-        return min(ts)
+        return max_over_ranks(min(ts), world, dev)
 
     graph.replay()
     t_graph = timed(graph.replay, max(1, min(args.steps, 5)))
     t_direct = timed(lambda: b.run(iters), max(1, min(args.steps, 3)))
     b.check_status()
     outs = [torch.empty_like(f) for f in fs]
-    ws = torch.empty(max(wmc.load().wmc_denoise_workspace_size(h, w, w, 0) for h, w in sizes),
-                     dtype=torch.uint8, device=dev)
+    ws = torch.empty(max([wmc.load().wmc_denoise_workspace_size(sizes[i][0], sizes[i][1], sizes[i][1], 0)
+                          for i in mine] or [256]), dtype=torch.uint8, device=dev)
 
     def loop():
         for f, l, st, o in zip(fs, lams, steps, outs):
@@ -489,16 +520,23 @@ def run_batch(args):
     loop()
     t_loop = timed(loop, 1)
     same = all(torch.equal(a, c) for a, c in zip(b.outs, outs))
-    line = {"workload": "batch", "metric": METRIC, "unit": UNIT, "config": {
-        "images": n, "pixels": px, "sides": "uniform [64, 1536] (seed 999)", "iters": iters,
-        "sigma": "U[0.01, 0.15]", "lambda": "U[0.5, 2]", "step": "0.5/(1+lambda)", "dtype": "f32",
-        "steps_per_launch": T, "autotune_ms_per_iter": tune},
-        "results": {"batched_graph": px * iters / (t_graph * 1e-3) / 1e9,
-                    "batched_direct": px * iters / (t_direct * 1e-3) / 1e9,
-                    "single_image_loop": px * iters / (t_loop * 1e-3) / 1e9,
-                    "ms": {"graph": t_graph, "direct": t_direct, "loop": t_loop},
-                    "batched_equals_loop_bitwise": same}}
-    print(json.dumps(line), flush=True)
+    same = max_over_ranks(0.0 if same else 1.0, world, dev) == 0.0
+    if rank == 0:
+        line = {"workload": "batch", "metric": METRIC, "unit": UNIT, "n_gpus": world,
+                "scaling": "strong", "config": {
+                    "images": n, "pixels": px, "sides": "uniform [64, 1536] (seed 999)", "iters": iters,
+                    "sigma": "U[0.01, 0.15]", "lambda": "U[0.5, 2]", "step": "0.5/(1+lambda)", "dtype": "f32",
+                    "steps_per_launch": T, "autotune_ms_per_iter": tune,
+                    "shard": {"rule": "longest first to the least-loaded rank, by pixel count",
+                              "pixels_per_rank": loads}},
+                "results": {"batched_graph": px * iters / (t_graph * 1e-3) / 1e9,
+                            "batched_direct": px * iters / (t_direct * 1e-3) / 1e9,
+                            "single_image_loop": px * iters / (t_loop * 1e-3) / 1e9,
+                            "ms": {"graph": t_graph, "direct": t_direct, "loop": t_loop},
+                            "batched_equals_loop_bitwise": same}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 

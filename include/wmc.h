@@ -342,6 +342,22 @@ wmc_status_t wmc_unrolled_backward(const float *f, const float *lambda, float st
 wmc_status_t wmc_energy_grad(const float *u, float *grad, int32_t h, int32_t w, int64_t ld,
                              wmc_boundary_t bnd, wmc_stream_t stream);
 
+/* ------------------------------------------------------------------------------------------
+ * wmc_shard_lpt: host-side partition of n independent images over `world` ranks (one GPU each),
+ * for running a batch of Sec. V-B denoisings on several GPUs with no communication: each image
+ * goes to one rank, balancing the ranks' total cost (cost[i]: the image's pixel count, or pixels
+ * x iterations).  Longest-processing-time-first (Graham): images in order of decreasing cost
+ * (equal costs: lower index first), each to the rank with the least cost so far (equal loads:
+ * lower rank).  The largest load is at most (4/3 - 1/(3 world)) of the best possible.  The
+ * result depends only on the arguments, so every rank computes the same partition by itself.
+ *   cost: host, n entries >= 0.  owner: host, n entries, written (rank of image i).
+ *   load: host, `world` entries, written (each rank's total cost), or NULL.
+ *   n >= 0 (0: nothing to do), world >= 1; cost and owner non-NULL when n > 0.
+ *   Runs on the calling thread, no CUDA call; WMC_ERR_INVALID_ARG on bad arguments.
+ */
+wmc_status_t wmc_shard_lpt(const int64_t *cost, int32_t n, int32_t world, int32_t *owner,
+                           int64_t *load);
+
 /* ------------------------------------------------------------------------------------------ */
 const char *wmc_status_string(wmc_status_t status); /* static string, never NULL */
 const char *wmc_last_error(void); /* detail of the last failure on this thread ("" if none) */

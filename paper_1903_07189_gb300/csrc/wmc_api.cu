@@ -500,6 +500,31 @@ wmc_status_t noalloc_scratch(void **out) {
 
 extern "C" {
 
+wmc_status_t wmc_shard_lpt(const int64_t *cost, int32_t n, int32_t world, int32_t *owner,
+                           int64_t *load) {
+    g_last_error[0] = 0;
+    if (n < 0) return fail(WMC_ERR_INVALID_ARG, "n = %d < 0", n);
+    if (world < 1) return fail(WMC_ERR_INVALID_ARG, "world = %d < 1", world);
+    if (n > 0 && (!cost || !owner)) return fail(WMC_ERR_INVALID_ARG, "cost or owner is NULL");
+    for (int32_t i = 0; i < n; ++i)
+        if (cost[i] < 0) return fail(WMC_ERR_INVALID_ARG, "cost[%d] < 0", i);
+    std::vector<int32_t> order((size_t)n);
+    for (int32_t i = 0; i < n; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    std::vector<int64_t> acc((size_t)world, 0);
+    for (int32_t i : order) {
+        int32_t best = 0;
+        for (int32_t r = 1; r < world; ++r)
+            if (acc[(size_t)r] < acc[(size_t)best]) best = r;
+        owner[i] = best;
+        acc[(size_t)best] += cost[i];
+    }
+    if (load)
+        for (int32_t r = 0; r < world; ++r) load[r] = acc[(size_t)r];
+    return WMC_OK;
+}
+
 const char *wmc_status_string(wmc_status_t s) {
     switch (s) {
         case WMC_OK: return "WMC_OK";

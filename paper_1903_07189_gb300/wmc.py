@@ -80,6 +80,7 @@ SIGNATURES = {
     "wmc_unrolled_backward": (_i32, [_vp, _vp, _f32, _i32, _i32, _i32, _i32, _i32, _i64, _i32, _vp, _vp, _vp,
                                      _vp, _sz, _vp]),
     "wmc_energy_grad": (_i32, [_vp, _vp, _i32, _i32, _i64, _i32, _vp]),
+    "wmc_shard_lpt": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     "wmc_status_string": (ctypes.c_char_p, [_i32]),
     "wmc_last_error": (ctypes.c_char_p, []),
     "wmc_version": (_i32, []),
@@ -504,6 +505,19 @@ def energy_grad(u: torch.Tensor, boundary: str = "replicate", out: torch.Tensor 
     _check(load().wmc_energy_grad(p, po, h, w, ld, BOUNDARY[boundary], _stream(u.device)),
            "wmc_energy_grad")
     return out
+
+
+def shard_lpt(costs, world: int):
+    """Partition images over `world` ranks by their costs (longest first, each to the least
+    loaded rank; the library's wmc_shard_lpt).  Returns (owner per image, total cost per rank).
+    Host only: no GPU is needed."""
+    n = len(costs)
+    c = (ctypes.c_int64 * max(n, 1))(*[int(x) for x in costs])
+    owner = (ctypes.c_int32 * max(n, 1))()
+    loads = (ctypes.c_int64 * max(int(world), 1))()
+    _check(load().wmc_shard_lpt(ctypes.cast(c, _vp), n, int(world), ctypes.cast(owner, _vp),
+                                ctypes.cast(loads, _vp)), "wmc_shard_lpt")
+    return [int(owner[i]) for i in range(n)], [int(loads[r]) for r in range(int(world))]
 
 
 def psnr(sse: float, n: int, peak: float = 1.0) -> float:
