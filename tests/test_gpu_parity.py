@@ -88,6 +88,23 @@ def test_eval_parity_structured_images():
         assert ok.all(), err
 
 
+@pytest.mark.parametrize("R", [16, 64])
+def test_smooth_disk_eval_and_energy(R):
+    """Smooth disks (edge width R/4; the gradient turns through every direction, so every
+    selection branch and the 8-direction axis bias are exercised): evaluation against the oracle
+    with tie excusal, and the FP64 energy sum |H^w| within 2e-6."""
+    n = int(2 * R * 1.75) + 8
+    c = (n - 1) / 2.0
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    u = (0.5 * (1 + np.tanh((R - np.hypot(y - c, x - c)) / (0.25 * R)))).astype(np.float32)
+    for bnd in ("replicate", "zero"):
+        ok, _, err = eval_parity(u, bnd)
+        assert ok.all(), (bnd, err)
+        e = float(wmc().energy(to_gpu(u), boundary=bnd)[0])
+        want = oracle.energies(u.astype(np.float64), boundary=bnd)[0]
+        assert abs(e - want) <= 2e-6 * abs(want), (bnd, e, want)
+
+
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
 def test_eval_parity_reduced_storage(dtype):
     u = synth.make_image(97, 131, seed=11, sigma=0.05)
