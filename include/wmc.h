@@ -129,6 +129,15 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
  * incomplete).  WMC_OK otherwise.  workspace: device pointer passed to that call. */
 wmc_status_t wmc_denoise_status(const void *workspace, wmc_stream_t stream);
 
+/* wmc_selftest_wait_timeout: exercises the failure path of those bounded waits without a fault.
+ * One CTA arms an mbarrier for a 16-byte transfer that is never issued and waits for it with the
+ * multi-step kernels' bounded wait, limited to limit_ns (1 .. 1e9 ns); the wait runs out and the
+ * CTA sets bit 0 of the status word at `workspace`, as a tile whose load timed out does, and
+ * returns.  wmc_denoise_status(workspace) then reports WMC_ERR_TIMEOUT; the next flow call on
+ * that workspace clears the word.  Nothing but the status word is written.
+ *   workspace: device, >= 4 bytes, WMC_WORKSPACE_ALIGN-aligned (a wmc_denoise workspace). */
+wmc_status_t wmc_selftest_wait_timeout(void *workspace, int64_t limit_ns, wmc_stream_t stream);
+
 /* ------------------------------------------------------------------------------------------
  * wmc_denoise_noalloc: wmc_denoise without a workspace argument and without allocating.  It is
  * for callers that cannot obtain device memory for scratch space: code running where a memory

@@ -706,6 +706,19 @@ wmc_status_t wmc_denoise_status(const void *workspace, wmc_stream_t stream) {
     return WMC_OK;
 }
 
+wmc_status_t wmc_selftest_wait_timeout(void *workspace, int64_t limit_ns, wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    if (!workspace) return fail(WMC_ERR_INVALID_ARG, "workspace is NULL");
+    if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
+        return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    if (limit_ns < 1 || limit_ns > 1000000000LL)
+        return fail(WMC_ERR_INVALID_ARG, "limit_ns = %lld outside 1 .. 1e9", (long long)limit_ns);
+    cudaError_t e = wmc::launch_selftest_wait(static_cast<unsigned int *>(workspace), (uint64_t)limit_ns,
+                                              (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test wait kernel launch");
+    return WMC_OK;
+}
+
 size_t wmc_energy_workspace_size(int32_t h, int32_t w) {
     if (h <= 0 || w <= 0) return WMC_WORKSPACE_ALIGN;
     return WMC_WORKSPACE_ALIGN +

@@ -33,6 +33,9 @@ void tile_box(int dtype, int *box_w, int *box_h);
 
 // FP64 energies; workspace: a 256-byte ticket block followed by 3 doubles per CTA.
 int64_t energy_blocks(int32_t h, int32_t w);
+// wmc_selftest.cu: one CTA waits (bounded) on a transfer that never comes and sets *status
+cudaError_t launch_selftest_wait(unsigned int *status, uint64_t limit_ns, cudaStream_t st);
+
 cudaError_t launch_energy(int dtype, const void *u, const void *f, const void *clean, int32_t h,
                           int32_t w, int64_t ld, int bnd, double *out, void *workspace,
                           cudaStream_t st);

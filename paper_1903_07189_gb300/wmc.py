@@ -81,6 +81,7 @@ SIGNATURES = {
                                      _vp, _sz, _vp]),
     "wmc_energy_grad": (_i32, [_vp, _vp, _i32, _i32, _i64, _i32, _vp]),
     "wmc_shard_lpt": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+    "wmc_selftest_wait_timeout": (_i32, [_vp, _i64, _vp]),
     "wmc_status_string": (ctypes.c_char_p, [_i32]),
     "wmc_last_error": (ctypes.c_char_p, []),
     "wmc_version": (_i32, []),
@@ -260,6 +261,13 @@ def check_status(workspace: torch.Tensor):
     """Raise WMCError(WMC_ERR_TIMEOUT) if a bounded device wait in the last flow call that used
     `workspace` gave up (synchronises the current stream)."""
     _check(load().wmc_denoise_status(workspace.data_ptr(), _stream(workspace.device)), "wmc_denoise_status")
+
+
+def selftest_wait_timeout(workspace: torch.Tensor, limit_ns: int = 10_000_000):
+    """Make one bounded device wait run out on purpose (wmc_selftest_wait_timeout): afterwards
+    check_status(workspace) raises WMCError(WMC_ERR_TIMEOUT)."""
+    _check(load().wmc_selftest_wait_timeout(workspace.data_ptr(), int(limit_ns), _stream(workspace.device)),
+           "wmc_selftest_wait_timeout")
 
 
 def denoise_host_workspace_size(h: int, w: int, dtype=torch.float32) -> int:

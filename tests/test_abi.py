@@ -189,6 +189,14 @@ def test_energy_grad_validation(lib):
     assert lib.wmc_energy_grad(u, g, 8, 8, 8, 5, None) == INVALID
 
 
+def test_selftest_wait_validation(lib):
+    ws = ctypes.c_void_p(0x100000)
+    assert lib.wmc_selftest_wait_timeout(None, 1000, None) == INVALID
+    assert lib.wmc_selftest_wait_timeout(ctypes.c_void_p(0x100004), 1000, None) == WORKSPACE
+    assert lib.wmc_selftest_wait_timeout(ws, 0, None) == INVALID
+    assert lib.wmc_selftest_wait_timeout(ws, 2_000_000_000, None) == INVALID
+
+
 def test_l1_validation(lib):
     f = ctypes.c_void_p(0x100000)
     u = ctypes.c_void_p(0x300000)

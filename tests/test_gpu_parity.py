@@ -334,6 +334,23 @@ def test_status_word_ok_after_runs():
     wmc().check_status(ws)  # raises on WMC_ERR_TIMEOUT
 
 
+def test_timed_out_wait_is_reported_and_the_context_stays_usable():
+    """A bounded wait that runs out (the self-test's mbarrier is armed for a transfer that is
+    never issued; 10 ms limit) sets the status word: check_status raises WMC_ERR_TIMEOUT.  The
+    next flow call on the workspace clears the word, and its result is still exact."""
+    f = to_gpu(synth.make_image(150, 170, seed=25))
+    ws = torch.empty(wmc().load().wmc_denoise_workspace_size(150, 170, 170, 0), dtype=torch.uint8, device=DEV)
+    ref = wmc().denoise(f, 1.0, 0.25, 8, steps_per_launch=4, workspace=ws)
+    wmc().check_status(ws)
+    wmc().selftest_wait_timeout(ws, 10_000_000)
+    with pytest.raises(wmc().WMCError) as err:
+        wmc().check_status(ws)
+    assert err.value.status == 5  # WMC_ERR_TIMEOUT
+    again = wmc().denoise(f, 1.0, 0.25, 8, steps_per_launch=4, workspace=ws)
+    wmc().check_status(ws)
+    assert torch.equal(again, ref)
+
+
 def test_mcf_steps_per_launch_bitwise():
     u0 = to_gpu(synth.make_image(200, 180, seed=24))
     ref = wmc().mcf(u0, step=0.3, iters=10, steps_per_launch=1)
