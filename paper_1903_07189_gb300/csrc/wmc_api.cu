@@ -209,6 +209,11 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
     const void *srcs[3] = {u0, bufs[0], bufs[1]};
     if (T > 1)
         for (int k = 0; k < 3; ++k) tma[k] = encode_window_map(&maps[k], srcs[k], dtype, h, w, ld);
+    // FP32: f's window is loaded by TMA with U's (same box)
+    alignas(64) CUtensorMap fmap;
+    memset(&fmap, 0, sizeof fmap);
+    const bool f_tma = T > 1 && dtype == WMC_F32 && f != nullptr &&
+                       encode_window_map(&fmap, f, dtype, h, w, ld);
 
     const void *src = u0;
     int src_id = 0;
@@ -244,7 +249,9 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
             tp.c_h = c_h;
             tp.status = status;
             tp.pdl = prev_tile ? 1 : 0;  // follows a tile launch: may overlap its tail
-            e = launch_tile(dtype, bnd, s, &maps[src_id], tp, -1, st);
+            tp.f_tma = (f_tma && tma[src_id]) ? 1 : 0;
+            alignas(64) CUtensorMap pair[2] = {maps[src_id], fmap};
+            e = launch_tile(dtype, bnd, s, pair, tp, -1, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "flow kernel launch");
         prev_tile = s > 1;

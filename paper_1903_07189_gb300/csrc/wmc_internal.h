@@ -21,6 +21,8 @@ cudaError_t launch_stream(int dtype, int mode, int bnd, const StreamParams &p, b
                           cudaStream_t st);
 
 // Temporally blocked flow kernels, steps = 2..kMaxSteps.
+// map: single-image launches pass two tensor maps, U's window then f's (read when p.f_tma);
+// batch launches (batch_tiles >= 0) pass nullptr and use the image descriptors' maps
 cudaError_t launch_tile_f32_rep(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
 cudaError_t launch_tile_f32_zero(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
 cudaError_t launch_tile_bf16_rep(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);

@@ -75,7 +75,11 @@ template <typename S> struct Geom {
     static constexpr int P = LW;                                  // shared pitch (floats)
     static constexpr int BUF = LH * P;                            // floats per buffer
     static constexpr int STAGE_BYTES = sizeof(S) == 4 ? 0 : LH * LW * (int)sizeof(S);
-    static constexpr int SMEM = 2 * BUF * 4 + STAGE_BYTES + 128;  // + alignment slack
+    // FP32 storage: the window of f arrives by TMA too, into a third buffer after the two
+    // ping-pong buffers (16-bit storage reads f with plain loads)
+    static constexpr int F_BYTES = sizeof(S) == 4 ? BUF * 4 : 0;
+    static constexpr int SMEM = 2 * BUF * 4 + STAGE_BYTES + F_BYTES + 128;  // + alignment slack
+    static_assert(sizeof(S) != 4 || (2 * BUF * 4) % 128 == 0, "the f window must start 128-byte aligned");
 };
 
 // Output tile of a T-step single-image launch, width OW and height OH.  The window origin is the
@@ -120,6 +124,7 @@ struct TileV2Params {
     int32_t owt, oht;     // output tile size
     unsigned int *status; // device status word (bit 0: a bounded wait gave up) or nullptr
     int32_t pdl;          // host side: launch as a programmatic dependent of the previous launch
+    int32_t f_tma;        // single image, FP32: f is read through the second tensor map
 };
 
 // Programmatic dependent launch: a launch made with the programmatic-serialization attribute may
@@ -290,6 +295,8 @@ template <typename S> struct TileJob {
     const S *u;                // U^t (read through `map` when use_tma)
     const S *f;                // f or nullptr
     const CUtensorMap *map;
+    const CUtensorMap *fmap;   // f's tensor map, used when f_tma
+    bool f_tma;                // FP32 and TMA: f's window is loaded with U's into fbuf
     int64_t ld;
     int h, w;
     float c_keep, c_h, c_f;
@@ -322,12 +329,18 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     // copy and later waits for it, so the other threads never poll it).  U^t is the previous
     // launch's output: wait for that launch first (every later access of this CTA to U^t or to
     // the output buffer comes after this thread's wait through the CTA barriers below).
+    // FP32 with TMA: f's window (same box and origin as U's) lands in the third buffer and
+    // completes the same barrier.  f is never written by a flow launch, so its copy goes out
+    // before the wait for the previous launch.
+    const bool ftma = sizeof(S) == 4 && jb.use_tma && jb.f_tma && jb.f != nullptr;
+    float *fbuf = buf1 + BUF;
     if (jb.use_tma) {
         if (tid == 0) {
+            mbar_expect_tx(smem_u32(bar), (uint32_t)(LW * LH * sizeof(S)) * (ftma ? 2u : 1u));
+            if (ftma) tma_load_2d(smem_u32(fbuf), jb.fmap, X0, Y0, smem_u32(bar));
             griddep_wait();
             void *dst = (sizeof(S) == 4) ? static_cast<void *>(buf0)
                                          : static_cast<void *>(buf1 + BUF);  // staging
-            mbar_expect_tx(smem_u32(bar), (uint32_t)(LW * LH * sizeof(S)));
             tma_load_2d(smem_u32(dst), jb.map, X0, Y0, smem_u32(bar));
         }
     } else {
@@ -364,8 +377,8 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     const unsigned in_rows = row_range(-r0, h - r0);
     c.out_rows = in_rows & row_range(y0 - r0, y0 + oht - r0);
     float2 g[kRY];
-    {
-        const float2 cf = make_float2(jb.c_f, jb.c_f);
+    const float2 cf = make_float2(jb.c_f, jb.c_f);
+    if (!ftma) {
         const S *fr = jb.f + (int64_t)(Y0 + c.ib) * jb.ld + c.gx;
         const bool hasf = jb.f != nullptr;
 #pragma unroll
@@ -402,6 +415,11 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
         }
     } else {
         __syncthreads();
+    }
+    if (ftma) {  // f as loaded by TMA: zero outside the image, like the plain loads' predicates
+        const float *fr = fbuf + c.ib * G::P + c.j;
+#pragma unroll
+        for (int k = 0; k < kRY; ++k) g[k] = __fmul2_rn(cf, make_float2(fr[k * G::P], fr[k * G::P + 32]));
     }
 
     // ---- REPLICATE: fill the ring just outside the image from its nearest in-image cell.
@@ -441,7 +459,8 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
 
 template <int T, typename S, int BND, bool BATCH>
 __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
-    tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const TileV2Params p) {
+    tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap fmap,
+                   const TileV2Params p) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // 128-byte aligned start of the buffers, formed as an offset into the __shared__ array (not
@@ -464,6 +483,8 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
         jb.c_f = im.c_f;
         jb.map = &im.map[p.src_role];
         jb.use_tma = im.use_tma[p.src_role] != 0;
+        jb.fmap = &im.map[0];
+        jb.f_tma = im.use_tma[0] != 0;
         jb.x0 = t.y;
         jb.y0 = t.z;
     } else {
@@ -477,6 +498,8 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
         jb.c_f = p.c_f;
         jb.map = &tmap;
         jb.use_tma = p.use_tma != 0;
+        jb.fmap = &fmap;
+        jb.f_tma = p.f_tma != 0;
         const int ty = blockIdx.x / p.ntx, tx = blockIdx.x - ty * p.ntx;
         jb.x0 = tx * p.owt;
         jb.y0 = ty * p.oht;
@@ -523,13 +546,15 @@ cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, int64_t nbl
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(bit, std::memory_order_release);
     }
-    CUtensorMap dummy;
+    // map: the tensor maps of U and of f (single image; f's is read only when p.f_tma)
+    alignas(64) CUtensorMap dummy[2];
     if (BATCH || !p.use_tma) {
-        memset(&dummy, 0, sizeof dummy);
-        map = &dummy;
+        memset(dummy, 0, sizeof dummy);
+        map = dummy;
+        p.f_tma = 0;
     }
     if (!p.pdl) {
-        tile_v2_kernel<T, S, BND, BATCH><<<(unsigned)nblocks, kTileThreadsV2, G::SMEM, st>>>(*map, p);
+        tile_v2_kernel<T, S, BND, BATCH><<<(unsigned)nblocks, kTileThreadsV2, G::SMEM, st>>>(map[0], map[1], p);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg{};
@@ -542,7 +567,7 @@ cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, int64_t nbl
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tile_v2_kernel<T, S, BND, BATCH>, *map, p);
+    return cudaLaunchKernelEx(&cfg, tile_v2_kernel<T, S, BND, BATCH>, map[0], map[1], p);
 }
 
 template <typename S, int BND>
