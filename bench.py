@@ -49,9 +49,9 @@ FMA_OPS_PER_PX_ITER = 27
 SMS, FP32_LANES_PER_SM = 152, 128
 DEFAULT_T = 4
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one 4-step tile-kernel launch on
-# this image, from an ncu capture of a warm-L2 launch (67.15 MB read + 20.91 MB written); valid
+# this image, from an ncu capture of a warm-L2 launch (67.15 MB read + 20.98 MB written); valid
 # for the default 4 steps per launch only.
-TILE_T4_DRAM_BYTES = 88.06e6
+TILE_T4_DRAM_BYTES = 88.13e6
 # GB300 HBM3e nominal bandwidth (GB/s); fractions are reported against it and against the
 # measured copy bandwidth
 NOMINAL_HBM_GBS = 8000.0
