@@ -34,6 +34,12 @@
 // clamping and produce exactly what clamped reads would.  Warps whose cells all lie beyond that
 // ring (tiles overhanging the image) skip the arithmetic: no in-image cell reads those cells.
 //
+// The update's f term (c_f f, constant over the T steps) sits in registers, 8 rows x 2 columns
+// per thread.  For FP32 storage f's window comes as a second TMA box with the same origin, into a
+// third shared buffer, completing the same mbarrier (f is never written by a flow launch, so its
+// copy is issued before the wait for the previous launch); 16-bit storage reads f with
+// predicated plain loads.
+//
 // Shared memory always holds FP32; for BF16/FP16 storage the TMA box lands in a staging area
 // and is widened once, and every step rounds its result to the storage type, so the arithmetic
 // is identical to the single-step streaming kernel.
