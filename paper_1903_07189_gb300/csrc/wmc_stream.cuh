@@ -157,14 +157,15 @@ __global__ void __launch_bounds__(kStreamWarps * 32, R <= 8 ? 3 : 2)
 // ---------------------------------------------------------------------------------------------
 // FP32 images whose rows start on 16-byte boundaries: a lane holds 4 adjacent cells (one 16-byte
 // access per row), a warp 128 columns, a CTA of kStream4Warps warps 512 columns, a thread a strip of
-// stream4_rows<MODE>() rows.  Four cells per lane halve the shuffles and the load/store instructions per cell
+// stream4_rows<MODE, STACK>() rows.  Four cells per lane halve the shuffles and the load/store instructions per cell
 // of the pair layout above; this is the form the FP32 single-pass operations take whenever the
 // alignment allows it.  Every load of a strip is issued before its arithmetic, so the strip
 // height sets the bytes a thread has in flight: these kernels are bound by that (evaluation moves
 // 4.9 TB/s, the one-step flow, with its f rows in flight too, 7.0 TB/s at 16384^2), and 8-row
 // strips (4 CTAs of 128 threads per SM, 128 registers) beat 4-row strips (6 CTAs per SM) by 3 %
-// (evaluation) and 5 % (one step) at that size.  The finite-difference modes keep 4-row strips:
-// their division per cell makes the 8-row form over twice as slow.
+// (evaluation) and 5 % (one step) at that size.  The finite-difference modes keep 4-row strips
+// (their division per cell makes the 8-row form over twice as slow), and so do stacks of small
+// images (32 x 512^2: 22.5 instead of 20.5 us per step with 8 rows, from the longer last wave).
 #ifndef WMC_STREAM4_RY
 #define WMC_STREAM4_RY 8
 #endif
@@ -177,10 +178,16 @@ __global__ void __launch_bounds__(kStreamWarps * 32, R <= 8 ? 3 : 2)
 constexpr int kStream4Warps = WMC_STREAM4_WARPS;
 template <int MODE>
 __host__ __device__ constexpr bool stream4_fd() { return MODE == MODE_FD_EVAL || MODE == MODE_FD_FLOW; }
-template <int MODE>
-__host__ __device__ constexpr int stream4_rows() { return stream4_fd<MODE>() ? 4 : WMC_STREAM4_RY; }
-template <int MODE>
-__host__ __device__ constexpr int stream4_min_blocks() { return stream4_fd<MODE>() ? 6 : WMC_STREAM4_MIN_BLOCKS; }
+// 4-row strips for the finite-difference modes and for stacks of images (small images: the
+// shorter strips give more CTAs and a smaller last wave)
+template <int MODE, bool STACK>
+__host__ __device__ constexpr bool stream4_short() { return stream4_fd<MODE>() || STACK; }
+template <int MODE, bool STACK>
+__host__ __device__ constexpr int stream4_rows() { return stream4_short<MODE, STACK>() ? 4 : WMC_STREAM4_RY; }
+template <int MODE, bool STACK>
+__host__ __device__ constexpr int stream4_min_blocks() {
+    return stream4_short<MODE, STACK>() ? 6 : WMC_STREAM4_MIN_BLOCKS;
+}
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
@@ -212,9 +219,9 @@ __device__ __forceinline__ float stencil4(float nw, float n, float ne, float w, 
 }
 
 template <int BND, int MODE, bool STACK = false>
-__global__ void __launch_bounds__(kStream4Warps * 32, stream4_min_blocks<MODE>())
+__global__ void __launch_bounds__(kStream4Warps * 32, stream4_min_blocks<MODE, STACK>())
     stream4_kernel(const StreamParams p) {
-    constexpr int R = stream4_rows<MODE>();
+    constexpr int R = stream4_rows<MODE, STACK>();
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int w = p.w, h = p.h;
@@ -300,7 +307,7 @@ __host__ __forceinline__ bool quad_aligned(const StreamParams &p) {
 template <int BND, int MODE, bool STACK>
 cudaError_t launch_stream4(const StreamParams &p, unsigned n_images, cudaStream_t st) {
     const int64_t nbx = (p.w + kStream4Warps * 128 - 1) / (kStream4Warps * 128);
-    const int64_t nby = (p.h + stream4_rows<MODE>() - 1) / stream4_rows<MODE>();
+    const int64_t nby = (p.h + stream4_rows<MODE, STACK>() - 1) / stream4_rows<MODE, STACK>();
     if (nbx * nby > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)(nbx * nby), n_images);
     stream4_kernel<BND, MODE, STACK><<<grid, kStream4Warps * 32, 0, st>>>(p);
