@@ -489,6 +489,10 @@ class UnrolledDenoise(torch.autograd.Function):
         return gf, gl, None, None, None, None
 
 
+# the same autograd node under the library's short name
+WMCDenoise = UnrolledDenoise
+
+
 def unrolled_denoise(f: torch.Tensor, lam: torch.Tensor, step: float, K: int, ckpt_every: int = 7,
                      boundary: str = "replicate") -> torch.Tensor:
     """Differentiable K-step denoising of an (n, h, w) stack (or one (h, w) image)."""

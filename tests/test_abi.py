@@ -46,6 +46,14 @@ def test_binding_covers_every_declared_symbol():
     assert set(declared_functions()) <= set(wmc.SIGNATURES)
 
 
+def test_python_layer_names():
+    """The user-facing calls: evaluation, denoising (single, batched), the autograd node."""
+    for name in ["eval", "denoise", "denoise_batched", "energy", "WMCDenoise", "unrolled_denoise",
+                 "denoise_l1", "eval_fd", "denoise_fd", "shard_lpt"]:
+        assert callable(getattr(wmc, name)), name
+    assert wmc.WMCDenoise is wmc.UnrolledDenoise
+
+
 def test_library_is_built_for_sm_103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
     assert os.path.exists(build.LIB)
