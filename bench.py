@@ -368,7 +368,7 @@ def run_gpu(args):
                          "hbm_gbs": 8 * H * W / (eval_ms * 1e-3) / 1e9,
                          "hbm_frac": 8 * H * W / (eval_ms * 1e-3) / 1e9 / peak,
                          "hbm_frac_of_nominal": 8 * H * W / (eval_ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
-                         "kernel": "wmc::stream4_kernel (eval, 4 cells per lane), 8 B per pixel",
+                         "kernel": "wmc::eval_tma_kernel (persistent, double-buffered TMA windows), 8 B per pixel",
                          "paper_context": PAPER_EVAL_CONTEXT},
                 # U was written by the last flow launch, so part of it is still in L2
                 "energy": {"ms": energy_ms, "hbm_gbs": 8 * H * W / (energy_ms * 1e-3) / 1e9,

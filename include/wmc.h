@@ -90,6 +90,13 @@ typedef struct {
 wmc_status_t wmc_eval(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_u, int64_t ld_hw,
                       wmc_dtype_t dtype, wmc_boundary_t bnd, wmc_stream_t stream);
 
+/* wmc_eval_status: synchronises `stream` and reads, then clears, the library's evaluation status
+ * word.  FP32 images that TMA can read (16-byte aligned base and pitch) are evaluated by a
+ * persistent kernel that waits for its TMA window loads with a time limit of 0.2 s; a wait that
+ * runs out makes that CTA stop (its remaining output is missing) and sets the word, and this
+ * returns WMC_ERR_TIMEOUT.  WMC_OK otherwise.  The word is per device and shared by all calls. */
+wmc_status_t wmc_eval_status(wmc_stream_t stream);
+
 /* ------------------------------------------------------------------------------------------
  * wmc_denoise: `iters` explicit Jacobi steps of the WMC flow
  *      U^{t+1} = U^t + step * (lambda * H^w(U^t) - mu * (U^t - f)),

@@ -570,6 +570,16 @@ static wmc_status_t eval_impl(int mode, float scale, const void *u, void *hw, in
     p.h = h;
     p.w = w;
     p.c_h = scale;
+    if (mode == wmc::MODE_EVAL && dtype == WMC_F32) {
+        // FP32 rows that TMA can read: the persistent kernel with double-buffered windows
+        alignas(64) CUtensorMap map;
+        if (encode_window_map(&map, u, dtype, h, w, ld_u)) {
+            cudaError_t e = wmc::launch_eval_tma(&map, static_cast<float *>(hw), ld_hw, h, w, (int)bnd, scale,
+                                                 (cudaStream_t)stream);
+            if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
+            return WMC_OK;
+        }
+    }
     const bool vec = pair_aligned(u, ld_u, es) && pair_aligned(hw, ld_hw, es);
     cudaError_t e = wmc::launch_stream((int)dtype, mode, (int)bnd, p, vec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "eval kernel launch");
@@ -580,6 +590,15 @@ wmc_status_t wmc_eval(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_
                       wmc_dtype_t dtype, wmc_boundary_t bnd, wmc_stream_t stream) {
     // the kernels carry 12 * H^w; the output scale brings it back
     return eval_impl(wmc::MODE_EVAL, 1.0f / 12.0f, u, hw, h, w, ld_u, ld_hw, dtype, bnd, stream);
+}
+
+wmc_status_t wmc_eval_status(wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    unsigned int word = 0;
+    cudaError_t e = wmc::eval_tma_status(&word, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "read the evaluation status word");
+    if (word & 1u) return fail(WMC_ERR_TIMEOUT, "an evaluation kernel gave up waiting for its TMA load");
+    return WMC_OK;
 }
 
 wmc_status_t wmc_eval_fd(const void *u, void *hw, int32_t h, int32_t w, int64_t ld_u,

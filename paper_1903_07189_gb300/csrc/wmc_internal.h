@@ -35,6 +35,12 @@ void tile_box(int dtype, int *box_w, int *box_h);
 
 // FP64 energies; workspace: a 256-byte ticket block followed by 3 doubles per CTA.
 int64_t energy_blocks(int32_t h, int32_t w);
+// wmc_eval_tma.cu: FP32 evaluation fed by TMA (map: U's window map, as the tile kernel's); the
+// status call reads and clears the word its bounded waits set
+cudaError_t launch_eval_tma(const CUtensorMap *map, float *out, int64_t ldo, int32_t h, int32_t w,
+                            int bnd, float scale, cudaStream_t st);
+cudaError_t eval_tma_status(unsigned int *word, cudaStream_t st);
+
 // wmc_selftest.cu: one CTA waits (bounded) on a transfer that never comes and sets *status
 cudaError_t launch_selftest_wait(unsigned int *status, uint64_t limit_ns, cudaStream_t st);
 

@@ -163,6 +163,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                  : "memory");
 }
 
+// Orders this thread's (and, after a CTA barrier, the CTA's) earlier shared-memory accesses of
+// the generic proxy before later async-proxy (TMA) accesses of the same memory: issued before a
+// TMA copy refills a buffer that threads have been reading.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
                                             uint32_t bar) {
     asm volatile(

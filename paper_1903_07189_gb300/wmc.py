@@ -82,6 +82,7 @@ SIGNATURES = {
     "wmc_energy_grad": (_i32, [_vp, _vp, _i32, _i32, _i64, _i32, _vp]),
     "wmc_shard_lpt": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     "wmc_selftest_wait_timeout": (_i32, [_vp, _i64, _vp]),
+    "wmc_eval_status": (_i32, [_vp]),
     "wmc_status_string": (ctypes.c_char_p, [_i32]),
     "wmc_last_error": (ctypes.c_char_p, []),
     "wmc_version": (_i32, []),
@@ -145,6 +146,13 @@ def eval(u: torch.Tensor, boundary: str = "replicate", out: torch.Tensor | None 
     _check(load().wmc_eval(p, po, h, w, ld, ldo, DTYPES[u.dtype], BOUNDARY[boundary], _stream(u.device)),
            "wmc_eval")
     return out
+
+
+def eval_status(device=None):
+    """Raise WMCError(WMC_ERR_TIMEOUT) if a bounded device wait of an evaluation since the last
+    check gave up (synchronises the current stream; clears the word)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    _check(load().wmc_eval_status(_stream(dev)), "wmc_eval_status")
 
 
 def eval_fd(u: torch.Tensor, boundary: str = "replicate", out: torch.Tensor | None = None) -> torch.Tensor:

@@ -88,6 +88,23 @@ def test_eval_parity_structured_images():
         assert ok.all(), err
 
 
+@pytest.mark.parametrize("shape", [(64, 128), (65, 129), (200, 517), (3, 700), (1000, 130), (7, 5)])
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_eval_tma_path_equals_streaming_path(shape, bnd):
+    """Dense FP32 rows (16-byte aligned) are evaluated by the persistent TMA kernel, an odd pitch
+    takes the streaming kernel: both must give the same bits (ragged boxes, both boundaries,
+    images smaller than one box), and the evaluation status word stays clear."""
+    u = synth.make_image(*shape, seed=26, sigma=0.07)
+    dense = to_gpu(u)
+    pitched = to_gpu(u, ld=shape[1] + 1)
+    a = wmc().eval(dense, bnd)
+    b = wmc().eval(pitched, bnd)
+    assert torch.equal(a, b)
+    ok, _, err = eval_parity(u, bnd)
+    assert ok.all(), err
+    wmc().eval_status()
+
+
 @pytest.mark.parametrize("R", [16, 64])
 def test_smooth_disk_eval_and_energy(R):
     """Smooth disks (edge width R/4; the gradient turns through every direction, so every
