@@ -444,7 +444,8 @@ def run_precision(args):
             t1 = best(lambda: wmc.denoise(f, LAM, STEP, 10, out=out, steps_per_launch=1, workspace=ws)) / 10
             r["single_pass"] = {"eval_ms": te, "eval_hbm_frac": 8 * n * n / (te * 1e-3) / 1e9 / peak,
                                 "step_ms": t1, "step_hbm_frac": 12 * n * n / (t1 * 1e-3) / 1e9 / peak,
-                                "kernel": "wmc::stream4_kernel (4 cells per lane)"}
+                                "kernel": {"eval": "wmc::eval_tma_kernel (persistent, double-buffered TMA windows)",
+                                           "step": "wmc::stream4_kernel (4 cells per lane)"}}
             del hw
         if name in ref_bf:
             e2 = np.abs(got - ref_bf[name])
