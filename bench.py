@@ -373,7 +373,7 @@ def run_gpu(args):
                 # U was written by the last flow launch, so part of it is still in L2
                 "energy": {"ms": energy_ms, "hbm_gbs": 8 * H * W / (energy_ms * 1e-3) / 1e9,
                            "hbm_frac": 8 * H * W / (energy_ms * 1e-3) / 1e9 / peak,
-                           "kernel": "wmc::energy_march_kernel (FP64 energies of U and f), 8 B per pixel"},
+                           "kernel": "wmc::energy_tma_kernel (FP64 energies of U and f; persistent, TMA windows), 8 B per pixel"},
                 "gpu_launches": args.steps * (2 + n_launch), "clocks": clocks,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)

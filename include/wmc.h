@@ -195,7 +195,9 @@ wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_h
  *   accumulated).  Sums run in FP32 over at most 16 pixels, then in double-float (an FP32
  *   pair, about 44 bits) up to one warp's share, and in FP64 beyond; the summation order is
  *   fixed by h and w alone, so repeated calls give identical results.  The workspace size
- *   depends on h and w (one FP64 triple per CTA, at most 304 CTAs).
+ *   depends on h and w (one FP64 triple per CTA, at most 304 CTAs).  FP32 images that TMA can
+ *   read are summed by a kernel fed by TMA copies; if one of its bounded waits (0.2 s) runs out,
+ *   out[] holds NaN.
  *   workspace: device, >= wmc_energy_workspace_size() bytes, aligned as above.
  */
 size_t wmc_energy_workspace_size(int32_t h, int32_t w);

@@ -107,17 +107,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     return g_encode;
 }
 
-// A 2-D tiled tensor map over an h x w image with pitch ld, box = the tile kernel's window.
-// Returns false when the image cannot be read through TMA (alignment, pitch, driver).
-bool encode_window_map(CUtensorMap *m, const void *base, wmc_dtype_t dtype, int32_t h, int32_t w,
-                       int64_t ld) {
+// A 2-D tiled tensor map over an h x w image with pitch ld and a bw x bh box.  Returns false
+// when the image cannot be read through TMA (alignment, pitch, driver).
+bool encode_box_map(CUtensorMap *m, const void *base, wmc_dtype_t dtype, int32_t h, int32_t w,
+                    int64_t ld, int bw, int bh) {
     const size_t es = elem_size(dtype);
     if (((uintptr_t)base % 16) != 0 || ((size_t)ld * es) % 16 != 0) return false;
     if ((size_t)ld * es >= (1ull << 40)) return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
     if (!enc) return false;
-    int bw, bh;
-    wmc::tile_box((int)dtype, &bw, &bh);
     const CUtensorMapDataType t = dtype == WMC_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                   : dtype == WMC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
@@ -129,6 +127,14 @@ bool encode_window_map(CUtensorMap *m, const void *base, wmc_dtype_t dtype, int3
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+// The same with the tile kernel's window as the box.
+bool encode_window_map(CUtensorMap *m, const void *base, wmc_dtype_t dtype, int32_t h, int32_t w,
+                       int64_t ld) {
+    int bw, bh;
+    wmc::tile_box((int)dtype, &bw, &bh);
+    return encode_box_map(m, base, dtype, h, w, ld, bw, bh);
 }
 
 bool pair_aligned(const void *p, int64_t ld, size_t es) {
@@ -770,6 +776,26 @@ wmc_status_t wmc_energy(const void *u, const void *f, const void *clean, int32_t
         return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed", need);
     if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
         return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+#ifndef WMC_ENERGY_TMA
+#define WMC_ENERGY_TMA 1  // 0: FP32 energies take the streaming kernels only
+#endif
+    if (WMC_ENERGY_TMA && dtype == WMC_F32) {
+        // FP32 rows that TMA can read: the persistent kernel fed by TMA windows (U) and boxes
+        // (f, clean)
+        alignas(64) CUtensorMap maps[3];
+        memset(maps, 0, sizeof maps);
+        int bw = 0, bh = 0;
+        wmc::energy_tma_box(&bw, &bh);
+        const bool ok = encode_window_map(&maps[0], u, dtype, h, w, ld) &&
+                        (!f || encode_box_map(&maps[1], f, dtype, h, w, ld, bw, bh)) &&
+                        (!clean || encode_box_map(&maps[2], clean, dtype, h, w, ld, bw, bh));
+        if (ok) {
+            cudaError_t e = wmc::launch_energy_tma(maps, f != nullptr, clean != nullptr, h, w, (int)bnd, out,
+                                                   workspace, st);
+            if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
+            return WMC_OK;
+        }
+    }
     cudaError_t e = wmc::launch_energy((int)dtype, u, f, clean, h, w, ld, (int)bnd, out, workspace, st);
     if (e != cudaSuccess) return cuda_fail(e, "energy kernel launch");
     return WMC_OK;

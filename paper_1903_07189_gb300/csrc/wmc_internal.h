@@ -44,6 +44,12 @@ cudaError_t eval_tma_status(unsigned int *word, cudaStream_t st);
 // wmc_selftest.cu: one CTA waits (bounded) on a transfer that never comes and sets *status
 cudaError_t launch_selftest_wait(unsigned int *status, uint64_t limit_ns, cudaStream_t st);
 
+// FP32 energies fed by TMA: maps[0] is U's window map, maps[1] / maps[2] f's / clean's box maps
+// (box size from energy_tma_box; read when has_f / has_clean)
+void energy_tma_box(int *bw, int *bh);
+cudaError_t launch_energy_tma(const CUtensorMap *maps, bool has_f, bool has_clean, int32_t h, int32_t w,
+                              int bnd, double *out, void *ws, cudaStream_t st);
+
 cudaError_t launch_energy(int dtype, const void *u, const void *f, const void *clean, int32_t h,
                           int32_t w, int64_t ld, int bnd, double *out, void *workspace,
                           cudaStream_t st);

@@ -10,9 +10,12 @@
 // of double-float adds per warp, then FP64: the warps in order, one partial per CTA, and the last
 // CTA to finish (ticket counter) adds the partials in CTA order.  The assignment and the order
 // never change, so the result is bitwise reproducible.
+#include <atomic>
+
 #include "wmc_device.cuh"
 #include "wmc_internal.h"
 #include "wmc_stream.cuh"
+#include "wmc_tile.cuh"
 
 namespace wmc {
 
@@ -47,9 +50,20 @@ __host__ __device__ __forceinline__ MarchGeom march_geom(int32_t h, int32_t w) {
     return g;
 }
 
+// TMA-fed kernel: boxes of 128 x 64 cells, at most kEnergyTmaCTAs persistent CTAs (one per SM on
+// 152 SMs); the grid is a pure function of the image size, so the summation order is too.
+constexpr int kEBoxW = 128, kEBoxH = 64, kEnergyTmaCTAs = 152;
+
+static int64_t energy_tma_grid(int32_t h, int32_t w) {
+    const int64_t nb = (((int64_t)w + kEBoxW - 1) / kEBoxW) * (((int64_t)h + kEBoxH - 1) / kEBoxH);
+    return nb < kEnergyTmaCTAs ? nb : kEnergyTmaCTAs;
+}
+
 int64_t energy_blocks(int32_t h, int32_t w) {
     const MarchGeom g = march_geom(h, w);
-    const int64_t a = energy_grid(h, w), b = (int64_t)g.nbx * g.nbands;
+    int64_t a = energy_grid(h, w), b = (int64_t)g.nbx * g.nbands;
+    if (b > a) a = b;
+    b = energy_tma_grid(h, w);
     return a > b ? a : b;
 }
 
@@ -103,11 +117,12 @@ __device__ __forceinline__ DF df_warp_sum(DF v) {
 // Thread sums (12 |H^w|, the squared data residual, the squared error) as double-float pairs:
 // a fixed shuffle tree per warp, one FP64 value per warp (hi + lo), the 8 warps in order, one
 // partial per CTA, and the last CTA to finish (ticket counter) adds the partials in CTA order.
+template <int NW = kStreamWarps>  // warps per CTA
 __device__ __forceinline__ void energy_reduce(const DF (&acc)[3], double *__restrict__ out,
                                               double *__restrict__ partials,
                                               unsigned int *__restrict__ ticket) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ double red[3][kStreamWarps];
+    __shared__ double red[3][NW];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const DF t = df_warp_sum(acc[k]);
@@ -117,7 +132,7 @@ __device__ __forceinline__ void energy_reduce(const DF (&acc)[3], double *__rest
     __shared__ bool is_last;
     if (threadIdx.x < 3) {
         double t = 0.0;
-        for (int i = 0; i < kStreamWarps; ++i) t += red[threadIdx.x][i];
+        for (int i = 0; i < NW; ++i) t += red[threadIdx.x][i];
         // the thread sums hold 12 |H^w| and (U - f)^2: scale once, in FP64
         partials[(int64_t)blockIdx.x * 3 + threadIdx.x] =
             threadIdx.x == 0 ? t / 12.0 : threadIdx.x == 1 ? 0.5 * t : t;
@@ -143,7 +158,7 @@ __device__ __forceinline__ void energy_reduce(const DF (&acc)[3], double *__rest
     __syncthreads();
     if (threadIdx.x < 3) {
         double t = 0.0;
-        for (int i = 0; i < kStreamWarps; ++i) t += red[threadIdx.x][i];
+        for (int i = 0; i < NW; ++i) t += red[threadIdx.x][i];
         out[threadIdx.x] = t;
     }
 }
@@ -339,6 +354,163 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 2)
         for (int k = 0; k < 3; ++k) df_add(acc[k], s[k]);
     }
     energy_reduce(acc, out, partials, ticket);
+}
+
+// FP32 images that TMA can read: persistent CTAs (one per SM, 512 threads) walk boxes of 128 x 64
+// cells.  A buffer holds U's 136 x 66 window (origin (x0 - 4, y0 - 1), the flow kernel's, ring
+// refreshed for REPLICATE border boxes) and dense 128 x 64 boxes of f and clean; two buffers per
+// CTA, so the next box's copies are in flight while the current box is summed.  A thread takes
+// columns j and j + 32 of 8 rows (the packed FP32x2 stencil), sums its 16 cells in FP32 per box
+// and adds those sums into its double-float accumulators.  A window wait that runs out turns the
+// CTA's partial sums into NaN (after a bounded wait for its copies in flight), so the energies come
+// out NaN instead of wrong.
+constexpr int kEUBuf = (Geom<float>::LH * Geom<float>::P + 31) / 32 * 32;  // U window, floats
+constexpr int kEFBuf = kEBoxW * kEBoxH;                                     // f or clean box
+static_assert((kEUBuf * 4) % 128 == 0 && (kEFBuf * 4) % 128 == 0, "TMA destinations 128-byte aligned");
+
+template <bool HF, bool HC>
+__host__ __device__ constexpr int energy_tma_buf() { return kEUBuf + (HF ? kEFBuf : 0) + (HC ? kEFBuf : 0); }
+
+template <int BND, bool HF, bool HC>
+__global__ void __launch_bounds__(kTileThreadsV2, 1)
+    energy_tma_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap fmap,
+                      const __grid_constant__ CUtensorMap cmap, int h, int w, double *__restrict__ out,
+                      double *__restrict__ partials, unsigned int *__restrict__ ticket) {
+    using G = Geom<float>;
+    constexpr int P = G::P, LW = G::LW, LH = G::LH, NB = energy_tma_buf<HF, HC>();
+    constexpr uint32_t BYTES = (uint32_t)(LW * LH + (HF ? kEFBuf : 0) + (HC ? kEFBuf : 0)) * 4u;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    float *buf0 = reinterpret_cast<float *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j = 4 + 64 * (warp & 1) + lane;  // window column of the thread's first cell
+    const int ib = 1 + kRY * (warp >> 1);       // window row of its first row
+    const int nbx = (w + kEBoxW - 1) / kEBoxW;
+    const int nboxes = nbx * ((h + kEBoxH - 1) / kEBoxH);
+    auto issue = [&](int b, int k) {  // thread 0: the copies of box b into buffer k
+        const int by = b / nbx, bx = b - by * nbx;
+        float *bk = buf0 + k * NB;
+        fence_proxy_async_smem();
+        mbar_expect_tx(smem_u32(&bar[k]), BYTES);
+        tma_load_2d(smem_u32(bk), &umap, bx * kEBoxW - 4, by * kEBoxH - 1, smem_u32(&bar[k]));
+        if (HF) tma_load_2d(smem_u32(bk + kEUBuf), &fmap, bx * kEBoxW, by * kEBoxH, smem_u32(&bar[k]));
+        if (HC)
+            tma_load_2d(smem_u32(bk + kEUBuf + (HF ? kEFBuf : 0)), &cmap, bx * kEBoxW, by * kEBoxH,
+                        smem_u32(&bar[k]));
+    };
+    if (tid == 0) {
+        mbar_init(smem_u32(&bar[0]), 1);
+        mbar_init(smem_u32(&bar[1]), 1);
+        if ((int)blockIdx.x < nboxes) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < nboxes) issue(blockIdx.x + gridDim.x, 1);
+    }
+    DF acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    int n = 0;
+    for (int b = blockIdx.x; b < nboxes; b += gridDim.x, ++n) {
+        const int k = n & 1;
+        const uint32_t phase = (uint32_t)(n >> 1) & 1u;
+        const float *bu = buf0 + k * NB;
+        const float *bf = bu + kEUBuf, *bc = bu + kEUBuf + (HF ? kEFBuf : 0);
+        const bool ok = (tid != 0) || mbar_wait_bounded(smem_u32(&bar[k]), phase, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {  // copies may still be in flight into either buffer
+                mbar_wait_bounded(smem_u32(&bar[k]), phase, kWaitLimitNs);
+                if ((int)(b + gridDim.x) < nboxes)
+                    mbar_wait_bounded(smem_u32(&bar[k ^ 1]), (uint32_t)((n + 1) >> 1) & 1u, kWaitLimitNs);
+            }
+            const float nan = __int_as_float(0x7fc00000);
+            for (int q = 0; q < 3; ++q) acc[q] = {nan, 0.f};
+            break;
+        }
+        const int by = b / nbx, bx = b - by * nbx;
+        const int X0 = bx * kEBoxW - 4, Y0 = by * kEBoxH - 1;
+        const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
+        if (BND == BND_REPLICATE && border) {
+            refresh_ring<float>(const_cast<float *>(bu), X0, Y0, h, w, tid);
+            __syncthreads();
+        }
+        const int gx = X0 + j;
+        const bool c0 = gx < w, c1 = gx + 32 < w;
+        const float *rp = bu + (ib - 1) * P + j;
+        const int fo = (ib - 1) * kEBoxW + (j - 4);  // box offset of the thread's first cell
+        Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
+        float s[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int r = 0; r < kRY; ++r) {
+            const Row3 r2 = load_row3(rp + (r + 2) * P);
+            const float2 h12 = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+            const bool rin = Y0 + ib + r < h;
+            const bool in0 = rin & c0, in1 = rin & c1;
+            if (in0) s[0] += fabsf(h12.x);
+            if (in1) s[0] += fabsf(h12.y);
+            if (HF) {
+                const float d0 = r1.c.x - bf[fo + r * kEBoxW], d1 = r1.c.y - bf[fo + r * kEBoxW + 32];
+                if (in0) s[1] = fmaf(d0, d0, s[1]);
+                if (in1) s[1] = fmaf(d1, d1, s[1]);
+            }
+            if (HC) {
+                const float d0 = r1.c.x - bc[fo + r * kEBoxW], d1 = r1.c.y - bc[fo + r * kEBoxW + 32];
+                if (in0) s[2] = fmaf(d0, d0, s[2]);
+                if (in1) s[2] = fmaf(d1, d1, s[2]);
+            }
+            r0 = r1;
+            r1 = r2;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) df_add(acc[q], s[q]);
+        __syncthreads();  // every thread is done with this buffer
+        if (tid == 0 && (int)(b + 2 * gridDim.x) < nboxes) issue(b + 2 * gridDim.x, k);
+    }
+    energy_reduce<kTileThreadsV2 / 32>(acc, out, partials, ticket);
+}
+
+void energy_tma_box(int *bw, int *bh) {
+    *bw = kEBoxW;
+    *bh = kEBoxH;
+}
+
+cudaError_t launch_energy_tma(const CUtensorMap *maps, bool has_f, bool has_clean, int32_t h, int32_t w,
+                              int bnd, double *out, void *ws, cudaStream_t st) {
+    unsigned int *ticket = static_cast<unsigned int *>(ws);
+    double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + 256);
+    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const unsigned g = (unsigned)energy_tma_grid(h, w), b = kTileThreadsV2;
+    // one shared-memory size for every instance: two buffers of the largest kind
+    const int smem = 2 * energy_tma_buf<true, true>() * 4 + 128;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::atomic<uint64_t> attr_set{0};
+    const uint64_t bit = 1ull << (dev & 63);
+    auto go = [&](auto kern) -> cudaError_t {
+        kern<<<g, b, smem, st>>>(maps[0], maps[1], maps[2], h, w, out, partials, ticket);
+        return cudaGetLastError();
+    };
+#define WMC_ENERGY_TMA_KERNELS(B)                                                                       \
+    energy_tma_kernel<B, false, false>, energy_tma_kernel<B, true, false>, energy_tma_kernel<B, false, true>, \
+        energy_tma_kernel<B, true, true>
+    if (!(attr_set.load(std::memory_order_acquire) & bit)) {
+        void (*ks[8])(CUtensorMap, CUtensorMap, CUtensorMap, int, int, double *, double *, unsigned int *) = {
+            WMC_ENERGY_TMA_KERNELS(BND_REPLICATE), WMC_ENERGY_TMA_KERNELS(BND_ZERO)};
+        for (auto kf : ks) {
+            e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+        }
+        attr_set.fetch_or(bit, std::memory_order_release);
+    }
+#undef WMC_ENERGY_TMA_KERNELS
+    const int sel = (bnd == BND_ZERO ? 4 : 0) | (has_f ? 1 : 0) | (has_clean ? 2 : 0);
+    switch (sel) {
+        case 0: return go(energy_tma_kernel<BND_REPLICATE, false, false>);
+        case 1: return go(energy_tma_kernel<BND_REPLICATE, true, false>);
+        case 2: return go(energy_tma_kernel<BND_REPLICATE, false, true>);
+        case 3: return go(energy_tma_kernel<BND_REPLICATE, true, true>);
+        case 4: return go(energy_tma_kernel<BND_ZERO, false, false>);
+        case 5: return go(energy_tma_kernel<BND_ZERO, true, false>);
+        case 6: return go(energy_tma_kernel<BND_ZERO, false, true>);
+        default: return go(energy_tma_kernel<BND_ZERO, true, true>);
+    }
 }
 
 template <typename S>
