@@ -620,3 +620,111 @@ def test_smooth_disk_sum_tends_to_the_axis_bias_term():
     for k in range(2):
         shrink = (1 - ratios[k + 1]) / (1 - ratios[k])
         assert 0.35 < shrink < 0.7, (ratios, shrink)  # about 1/2 per doubling of R
+
+
+# ------------------------------------------------------------ point-sampled forms of the oracle
+def _points_with_borders(h, w, n, seed):
+    """n random pixels plus every corner and a run along each of the four borders."""
+    rng = np.random.default_rng(seed)
+    ys = [rng.integers(0, h, n)]
+    xs = [rng.integers(0, w, n)]
+    for y, x in [(0, 0), (0, w - 1), (h - 1, 0), (h - 1, w - 1)]:
+        ys.append(np.array([y]))
+        xs.append(np.array([x]))
+    k = min(w, 17)
+    ys += [np.zeros(k, int), np.full(k, h - 1)]
+    xs += [rng.integers(0, w, k), rng.integers(0, w, k)]
+    k = min(h, 17)
+    ys += [rng.integers(0, h, k), rng.integers(0, h, k)]
+    xs += [np.zeros(k, int), np.full(k, w - 1)]
+    return np.concatenate(ys), np.concatenate(xs)
+
+
+@pytest.mark.parametrize("boundary", ["zero", "replicate"])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 9), (8, 1), (3, 4), (37, 53)])
+def test_eval_points_match_the_appendix_on_integer_images(boundary, shape):
+    """The point-sampled evaluation (the checker of every full-size GPU test) against the
+    Appendix restatement through scipy's conv2, bit for bit on integer images (exact on both
+    sides), at random pixels, all four corners and runs along all four borders."""
+    rng = np.random.default_rng(sum(shape) + len(boundary))
+    u = rng.integers(-40, 41, size=shape).astype(np.float64)
+    want, dist = _appendix_wmc(u, boundary)
+    ys, xs = _points_with_borders(*shape, 200, seed=sum(shape))
+    got, cand = oracle.eval_points(u, ys, xs, boundary, candidates=True)
+    assert np.array_equal(got, want[ys, xs])
+    assert np.array_equal(np.sort(cand, -1), np.sort(dist[ys, xs], -1))
+
+
+@pytest.mark.parametrize("boundary", ["zero", "replicate"])
+def test_eval_points_equal_the_whole_image_oracle(boundary):
+    """Real-valued image of non-square shape: the point-sampled values and candidates equal the
+    whole-image oracle's at the same pixels, bit for bit (a transposed index or a wrong pitch in
+    the sampled loop would move every value)."""
+    u = synth.make_image(61, 47, seed=40, sigma=0.07).astype(np.float64)
+    hw, cand, _ = oracle.wmc_eval(u, boundary, candidates=True)
+    ys, xs = _points_with_borders(61, 47, 500, seed=41)
+    got, c = oracle.eval_points(u, ys, xs, boundary, candidates=True)
+    assert np.array_equal(got, hw[ys, xs])
+    assert np.array_equal(c, cand[ys, xs])
+
+
+@pytest.mark.parametrize("boundary", ["zero", "replicate"])
+def test_step_points_equal_one_oracle_step(boundary):
+    """One Jacobi step at sampled pixels (Sec. V-B, A = I; and Eq. MCF with mu = 0) equals one
+    whole-image oracle step from the same U^t, bit for bit, at random pixels and on all borders."""
+    f = synth.make_image(43, 58, seed=42, sigma=0.1).astype(np.float64)
+    U = oracle.denoise(f, 1.3, 0.2, 3, boundary)
+    ys, xs = _points_with_borders(43, 58, 400, seed=43)
+    want = oracle.denoise(f, 1.3, 0.2, 1, boundary, u0=U)
+    got = oracle.step_points(U, f, 1.3, 0.2, ys, xs, boundary)
+    assert np.array_equal(got, want[ys, xs])
+    want = oracle.mcf(U, 0.3, 1, boundary)
+    got = oracle.step_points(U, None, 1.0, 0.3, ys, xs, boundary, mu=0.0)
+    assert np.array_equal(got, want[ys, xs])
+
+
+def test_step_points_by_hand():
+    """The one-step example worked by hand above (a single 1 in a 3 x 3 image, lambda 1, step
+    1/4): 0.75 at the centre, 0 elsewhere, here from the point-sampled step."""
+    f = np.zeros((3, 3))
+    f[1, 1] = 1
+    ys, xs = np.divmod(np.arange(9), 3)
+    got = oracle.step_points(f, f, 1.0, 0.25, ys, xs)
+    want = np.zeros(9)
+    want[4] = 0.75
+    assert np.array_equal(got, want)
+
+
+# ----------------------------------------------------------------- harmonic quadratics
+def _tangent_candidates(a, b):
+    """Candidates d_1..d_8 of the affine image U = a x + b y (x = column, y = row down), derived
+    by hand from the printed half windows: d1 = -2a/3, d2 = -2b/3, d3 = 2a/3, d4 = 2b/3,
+    d5 = -(a+b)/2, d6 = (a-b)/2, d7 = (a+b)/2, d8 = -(a-b)/2."""
+    return np.stack([-2 * a / 3, -2 * b / 3, 2 * a / 3, 2 * b / 3, -(a + b) / 2, (a - b) / 2,
+                     (a + b) / 2, -(a - b) / 2], -1)
+
+
+@pytest.mark.parametrize("which", ["xy", "x2-y2"])
+def test_harmonic_quadratics_reduce_to_their_tangent_plane(which):
+    """U = x y and U = x^2 - y^2 (harmonic, so the isotropic Laplacian of Eq. kernel3 is 0).
+    Worked by hand from the printed kernels: the second-order part (dx dy, resp. dx^2 - dy^2)
+    sums to zero over every one of the eight half windows, so at each interior pixel the eight
+    d_i are exactly those of the tangent plane, gradient (y, x) for x y and (2x, -2y) for
+    x^2 - y^2.  Hence |H^w| = min(2|a|/3, 2|b|/3, |a+b|/2, |a-b|/2) of that gradient, which is 0
+    exactly where the gradient lies along one of the 8 discrete normals (the axes and the
+    diagonals through the origin), and not 0 elsewhere."""
+    y, x = np.mgrid[-6:7, -7:8].astype(np.float64)
+    if which == "xy":
+        u, a, b = x * y, y, x
+    else:
+        u, a, b = x ** 2 - y ** 2, 2 * x, -2 * y
+    for boundary in ("replicate", "zero"):
+        hw, cand, _ = oracle.wmc_eval(u, boundary, candidates=True)
+        inner = (slice(1, -1), slice(1, -1))
+        want = _tangent_candidates(a, b)[inner]
+        assert np.array_equal(cand[inner] * 12, want * 12)  # all integers or halves: exact
+        mag = np.minimum.reduce([2 * np.abs(a) / 3, 2 * np.abs(b) / 3, np.abs(a + b) / 2,
+                                 np.abs(a - b) / 2])[inner]
+        np.testing.assert_allclose(np.abs(hw[inner]), mag, rtol=0, atol=1e-14)
+        zero = ((a == 0) | (b == 0) | (np.abs(a) == np.abs(b)))[inner]
+        assert np.all(hw[inner][zero] == 0) and np.all(hw[inner][~zero] != 0)
