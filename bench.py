@@ -311,7 +311,7 @@ def run_gpu(args):
         roofline = {"bound": "alu", "achieved": fp32_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": fp32_achieved / fp32_peak,
                     "traffic": TILE_T4_DRAM_BYTES if (T == 4 and iters == ITERS) else None,
-                    "kernel": f"wmc::tile_v2_kernel<T={T}> (flow, {T} Jacobi steps per launch)",
+                    "kernel": f"wmc::tile_flow_kernel<T={T}> (flow, {T} Jacobi steps per launch, 128 x 64 regions)",
                     "peak_kind": f"FP32 FMA pipe lane-operations (an FMA counts once): {SMS} SMs x {FP32_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz "
                                  "(unit counts and the sampled clock)",
                     "algorithmic_ops_per_px_iter": FMA_OPS_PER_PX_ITER, "launch_ms": launch_ms,
@@ -492,12 +492,13 @@ def run_batch(args):
     lams = [params[i][1] for i in mine]
     steps = [0.5 / (1 + l) for l in lams]
     px = sum(costs)
-    # steps per launch picked by the library's autotuner (times each candidate on this batch)
+    # steps per launch and tile shape picked by the library's autotuner (times each candidate on
+    # this batch)
     if args.steps_per_launch:
-        T, tune = args.steps_per_launch, {}
+        (T, tile), tune = (args.steps_per_launch, 0), {}
     else:
-        T, tune = wmc.batch_autotune(fs, lams, steps)
-    b = wmc.Batch(fs, lams, steps, steps_per_launch=T)
+        (T, tile), tune = wmc.batch_autotune(fs, lams, steps)
+    b = wmc.Batch(fs, lams, steps, steps_per_launch=T, tile=tile)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
@@ -534,7 +535,7 @@ def run_batch(args):
 
     def loop():
         for f, l, st, o in zip(fs, lams, steps, outs):
-            wmc.denoise(f, l, st, iters, out=o, steps_per_launch=T, workspace=ws)
+            wmc.denoise(f, l, st, iters, out=o, steps_per_launch=T, workspace=ws, tile=tile)
 
     loop()
     t_loop = timed(loop, 1)
@@ -545,7 +546,8 @@ def run_batch(args):
                 "scaling": "strong", "config": {
                     "images": n, "pixels": px, "sides": "uniform [64, 1536] (seed 999)", "iters": iters,
                     "sigma": "U[0.01, 0.15]", "lambda": "U[0.5, 2]", "step": "0.5/(1+lambda)", "dtype": "f32",
-                    "steps_per_launch": T, "autotune_ms_per_iter": tune,
+                    "steps_per_launch": T, "tile": tile,
+                    "autotune_ms_per_iter": {f"T{k[0]}_tile{k[1]}": v for k, v in tune.items()},
                     "shard": {"rule": "longest first to the least-loaded rank, by pixel count",
                               "pixels_per_rank": loads}},
                 "results": {"batched_graph": px * iters / (t_graph * 1e-3) / 1e9,

@@ -70,9 +70,11 @@ typedef enum { WMC_F32 = 0, WMC_BF16 = 1, WMC_F16 = 2 } wmc_dtype_t;
 /*
  * Kernel configuration for the flows.  steps_per_launch = T (1..8) Jacobi steps are taken in
  * on-chip memory per pass over the image (temporal blocking; legal because step t+1 of every
- * pixel reads only U^t, Eq. MCF / Sec. V-B); 0 = library default.  tile = 0 picks the default
- * tile shape.  Results do not depend on the configuration: every configuration performs the
- * same FP32 operations on every pixel, so outputs are bitwise identical.
+ * pixel reads only U^t, Eq. MCF / Sec. V-B); 0 = library default (4).  tile = the region one CTA
+ * updates per step: 1 = 128 x 64 cells (output tiles of 130 - 2T by 66 - 2T), 2 = 128 x 32
+ * (130 - 2T by 34 - 2T: less wasted work on small or short images); 0 = library default (1).
+ * Results do not depend on the configuration: every configuration performs the same FP32
+ * operations on every pixel, so outputs are bitwise identical.
  */
 typedef struct {
     int32_t steps_per_launch;
@@ -145,6 +147,17 @@ wmc_status_t wmc_denoise_status(const void *workspace, wmc_stream_t stream);
  *   workspace: device, >= 4 bytes, WMC_WORKSPACE_ALIGN-aligned (a wmc_denoise workspace). */
 wmc_status_t wmc_selftest_wait_timeout(void *workspace, int64_t limit_ns, wmc_stream_t stream);
 
+/* wmc_selftest_status_timeout: the same self-test aimed at a status word the library holds per
+ * device rather than one in a caller's workspace: target WMC_SELFTEST_EVAL sets the evaluation
+ * status word (wmc_eval_status then returns WMC_ERR_TIMEOUT once, and clears it), target
+ * WMC_SELFTEST_NOALLOC the word at the start of wmc_denoise_noalloc's fixed scratch array
+ * (wmc_denoise_noalloc_status then returns WMC_ERR_TIMEOUT until the next wmc_denoise_noalloc
+ * call clears it).  limit_ns as above.  Errors: WMC_ERR_INVALID_ARG (target, limit_ns),
+ * WMC_ERR_CUDA. */
+#define WMC_SELFTEST_EVAL 0
+#define WMC_SELFTEST_NOALLOC 1
+wmc_status_t wmc_selftest_status_timeout(int32_t target, int64_t limit_ns, wmc_stream_t stream);
+
 /* ------------------------------------------------------------------------------------------
  * wmc_denoise_noalloc: wmc_denoise without a workspace argument and without allocating.  It is
  * for callers that cannot obtain device memory for scratch space: code running where a memory
@@ -161,10 +174,20 @@ wmc_status_t wmc_selftest_wait_timeout(void *workspace, int64_t limit_ns, wmc_st
  *   All calls on a device share the one array and the array keeps the last call's contents:
  *   calls whose work overlaps on the GPU (different streams, or threads enqueueing at the same
  *   time) race and corrupt each other; serialise them (one stream, or events).  The status
- *   word at the start of the array is cleared by every call.  Other arguments, results and
- *   errors: as wmc_denoise.
+ *   word at the start of the array is cleared by every call; a timed-out tile load is reported
+ *   by wmc_denoise_noalloc_status() (the counterpart of wmc_denoise_status(), whose workspace
+ *   argument such callers do not have).  The array's address is looked up once per device and
+ *   kept: do not use the library across a cudaDeviceReset() of that device.  Other arguments,
+ *   results and errors: as wmc_denoise.
  */
 size_t wmc_denoise_noalloc_max_bytes(void);
+
+/* wmc_denoise_noalloc_status: synchronises `stream` and reads the status word at the start of
+ * wmc_denoise_noalloc's fixed scratch array on the current device (as wmc_denoise_status does for
+ * a caller's workspace): WMC_ERR_TIMEOUT if a multi-step kernel of the last wmc_denoise_noalloc
+ * call on this device gave up waiting for its tile load (its output is then incomplete), WMC_OK
+ * otherwise.  The word is cleared by the next wmc_denoise_noalloc call, not by this one. */
+wmc_status_t wmc_denoise_noalloc_status(wmc_stream_t stream);
 
 wmc_status_t wmc_denoise_noalloc(const void *f, const void *u0, void *u, int32_t h, int32_t w,
                                  int64_t ld, wmc_dtype_t dtype, float lambda, float step,
@@ -261,11 +284,27 @@ wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t
  * fastest per iteration.  ms_per_iter (optional, host, n_candidates floats) receives the timings.
  * The trials write the images' outputs (u) and synchronise `stream`; do not capture this call.
  *   workspace: device, >= wmc_batch_autotune_workspace_size() bytes (the largest plan).
- *   best: host, receives {steps_per_launch, tile = 0} for wmc_batch_plan.
+ *   best: host, receives {steps_per_launch, tile = 0 (the default shape)} for wmc_batch_plan.
  * Errors: as wmc_batch_plan; WMC_ERR_INVALID_ARG for candidates outside 1..8, n_candidates
  *         outside 1..64 or trial_iters < 1; WMC_ERR_TIMEOUT if a trial reported a timed-out load.
  */
 size_t wmc_batch_autotune_workspace_size(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype);
+
+/*
+ * wmc_batch_autotune_configs: the same search over whole configurations, tile shape included:
+ * candidates (host, n_candidates entries of {steps_per_launch 1..8, tile 0..2}; NULL = both tile
+ * shapes x steps {2, 3, 4, 5, 6, 8}, 12 candidates in that order, tile-major) are each planned,
+ * run once untimed and timed over about trial_iters iterations; `best` receives the fastest
+ * candidate as given, ms_per_iter (optional, host) one time per candidate.  The workspace size
+ * of wmc_batch_autotune_workspace_size() covers every candidate.  Writes the images' outputs and
+ * synchronises `stream`; do not capture this call.
+ * Errors: as wmc_batch_autotune; WMC_ERR_INVALID_ARG for a candidate outside those ranges.
+ */
+wmc_status_t wmc_batch_autotune_configs(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                                        wmc_boundary_t bnd, const wmc_config_t *candidates,
+                                        int32_t n_candidates, int32_t trial_iters, void *workspace,
+                                        size_t workspace_bytes, wmc_config_t *best, float *ms_per_iter,
+                                        wmc_stream_t stream);
 
 wmc_status_t wmc_batch_autotune(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
                                 wmc_boundary_t bnd, const int32_t *candidates, int32_t n_candidates,
@@ -353,6 +392,27 @@ wmc_status_t wmc_unrolled_backward(const float *f, const float *lambda, float st
                                    wmc_stream_t stream);
 
 /*
+ * wmc_backward: the reverse mode of K unrolled denoising steps in one call, with the arguments
+ * of the problem statement: f (device, n x h x ld stack), lambda (device, n floats), step, K,
+ * ckpt_every, and grad_u = dL/dU^K (device, n x h x ld) in; grad_f = dL/df (device, n x h x ld)
+ * and grad_lambda = dL/dlambda (device, n floats) out.  It runs wmc_unrolled_forward (keeping
+ * U^K and the checkpoints in the workspace) and then wmc_unrolled_backward; use those two calls
+ * instead when U^K itself is wanted, so that the forward is not run twice.  Selection held at its
+ * forward value, as above.
+ *   workspace: device, >= wmc_backward_workspace_size() bytes (the unrolled workspace plus one
+ *   stack for U^K), WMC_WORKSPACE_ALIGN-aligned, overlapping none of f, grad_u, grad_f.
+ * Errors: as wmc_unrolled_backward.
+ */
+size_t wmc_backward_workspace_size(int32_t n, int32_t h, int32_t w, int64_t ld, int32_t K,
+                                   int32_t ckpt_every);
+
+wmc_status_t wmc_backward(const float *f, const float *lambda, float step, int32_t K,
+                          int32_t ckpt_every, int32_t n, int32_t h, int32_t w, int64_t ld,
+                          wmc_boundary_t bnd, const float *grad_u, float *grad_f,
+                          float *grad_lambda, void *workspace, size_t workspace_bytes,
+                          wmc_stream_t stream);
+
+/*
  * wmc_energy_grad: grad = d/dU sum_p |H^w(U)(p)| (the Eq. wmcr regulariser, q = 1), selection
  * held fixed, sign(0) = 0.  u, grad: device FP32, h x w, pitch ld, must not overlap.  One kernel
  * launch, no workspace.
@@ -375,6 +435,18 @@ wmc_status_t wmc_energy_grad(const float *u, float *grad, int32_t h, int32_t w, 
  */
 wmc_status_t wmc_shard_lpt(const int64_t *cost, int32_t n, int32_t world, int32_t *owner,
                            int64_t *load);
+
+/* ------------------------------------------------------------------------------------------
+ * wmc_probe_fma: a measurement utility with no counterpart in the paper.  Enqueues `blocks` CTAs
+ * of wmc_probe_fma_threads() threads, each thread running `iters` iterations of 16 FP32 fused
+ * multiply-adds (8 independent packed FP32x2 chains), and writing one float per thread to `out`
+ * (device, blocks * wmc_probe_fma_threads() floats).  Timing it with events gives the FP32 FMA
+ * pipe's rate in lane-operations per second (an FMA counts once): the compute roofline of the
+ * temporally blocked flow kernel.  blocks 1 .. 2^20, iters >= 1.
+ * Errors: WMC_ERR_INVALID_ARG, WMC_ERR_CUDA (launch failure).
+ */
+int32_t wmc_probe_fma_threads(void);
+wmc_status_t wmc_probe_fma(float *out, int32_t blocks, int32_t iters, wmc_stream_t stream);
 
 /* ------------------------------------------------------------------------------------------ */
 const char *wmc_status_string(wmc_status_t status); /* static string, never NULL */

@@ -72,6 +72,7 @@ def _load():
                                                    _dp]
             lib.oracle_wmc_step_points.argtypes = [_dp, _dp, i32, i32, i64, d, d, d, ctypes.c_int, _ip,
                                                    _ip, i64, _dp, _dp]
+            lib.oracle_count_ties.argtypes = [_dp, i32, i32, i64, ctypes.c_int, d, ctypes.POINTER(i64)]
             _lib = lib
     return _lib
 
@@ -213,6 +214,18 @@ def eval_points(u, ys, xs, boundary="replicate", candidates: bool = False):
     if rc:
         raise ValueError(f"oracle_wmc_eval_points failed ({rc})")
     return (out, cand) if candidates else out
+
+
+def count_ties(u, tau: float, boundary="replicate") -> int:
+    """Pixels whose candidates within `tau` of the smallest magnitude hold both signs (the
+    opposite-sign near-ties of Eq. act)."""
+    u = _f64(u)
+    h, w = u.shape
+    n = ctypes.c_int64(0)
+    rc = _load().oracle_count_ties(_ptr(u), h, w, w, _bnd(boundary), float(tau), ctypes.byref(n))
+    if rc:
+        raise ValueError(f"oracle_count_ties failed ({rc})")
+    return int(n.value)
 
 
 def step_points(u, f, lam: float, step: float, ys, xs, boundary="replicate", mu: float = 1.0,

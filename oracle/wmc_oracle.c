@@ -292,6 +292,36 @@ int oracle_wmc_l1_primal_dual(const double *f, const double *u0, const double *d
 }
 
 /*
+ * Opposite-sign near-ties of Eq. act, the events the parity protocol excuses: pixels where the
+ * candidates d_i whose magnitude lies within `tau` of the smallest magnitude include both a
+ * positive and a negative value (so two valid choices of d_m differ by about 2 |d_m|).  Counts
+ * them over the whole image; returns 0, or 1 on bad arguments.
+ */
+int oracle_count_ties(const double *u, int32_t h, int32_t w, int64_t ld, int bnd, double tau,
+                      int64_t *count) {
+    if (check_dims(h, w, ld) || !(tau >= 0.0) || !count) return 1;
+    int64_t n = 0;
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(+ : n)
+    for (int32_t y = 0; y < h; ++y)
+        for (int32_t x = 0; x < w; ++x) {
+            double d[8];
+            distances(u, h, w, ld, y, x, bnd, d);
+            double mn = fabs(d[0]);
+            for (int i = 1; i < 8; ++i)
+                if (fabs(d[i]) < mn) mn = fabs(d[i]);
+            int pos = 0, neg = 0;
+            for (int i = 0; i < 8; ++i)
+                if (fabs(d[i]) <= mn + tau) {
+                    pos |= d[i] > 0.0;
+                    neg |= d[i] < 0.0;
+                }
+            n += pos & neg;
+        }
+    *count = n;
+    return 0;
+}
+
+/*
  * Point-sampled forms for checks at sizes where the whole-image oracle is too slow.
  * oracle_wmc_eval_points: H^w (Eq. conv + Eq. act) at n pixels (ys[k], xs[k]); cand (optional)
  * receives the eight d_i of each pixel (n*8 doubles).

@@ -20,14 +20,9 @@
 #include "wmc_tile.cuh"
 
 namespace wmc {
-void tile_box(int dtype, int *bw, int *bh) {
-    if (dtype == 0) {
-        *bw = Geom<float>::LW;
-        *bh = Geom<float>::LH;
-    } else {
-        *bw = Geom<__half>::LW;
-        *bh = Geom<__half>::LH;
-    }
+void tile_box(int dtype, int tile, int *bw, int *bh) {
+    *bw = dtype == 0 ? Geom<float>::LW : Geom<__half>::LW;
+    *bh = kQR * tile_warps(tile) + 2;
 }
 }  // namespace wmc
 
@@ -129,11 +124,12 @@ bool encode_box_map(CUtensorMap *m, const void *base, wmc_dtype_t dtype, int32_t
     return r == CUDA_SUCCESS;
 }
 
-// The same with the tile kernel's window as the box.
+// The same with the window of the flow kernel's tile shape `tile` as the box (tile 1: the 136 x 66
+// window of a 128 x 64 box, which the evaluation and energy kernels load too).
 bool encode_window_map(CUtensorMap *m, const void *base, wmc_dtype_t dtype, int32_t h, int32_t w,
-                       int64_t ld) {
+                       int64_t ld, int tile = 1) {
     int bw, bh;
-    wmc::tile_box((int)dtype, &bw, &bh);
+    wmc::tile_box((int)dtype, tile, &bw, &bh);
     return encode_box_map(m, base, dtype, h, w, ld, bw, bh);
 }
 
@@ -143,19 +139,23 @@ bool pair_aligned(const void *p, int64_t ld, size_t es) {
 
 // batch_tiles < 0: single-image launch (tiles from the grid); >= 0: batch launch over that
 // many tiles of the plan's table.
-cudaError_t launch_tile(wmc_dtype_t dtype, wmc_boundary_t bnd, int steps, const CUtensorMap *map,
-                        const wmc::TileV2Params &p, int64_t batch_tiles, cudaStream_t st) {
-    const bool z = bnd == WMC_BOUNDARY_ZERO;
+cudaError_t launch_tile(wmc_dtype_t dtype, wmc_boundary_t bnd, int tile, int steps, const CUtensorMap *map,
+                        const wmc::TileParams &p, int64_t batch_tiles, cudaStream_t st) {
+    const bool z = bnd == WMC_BOUNDARY_ZERO, s = tile == 2;
+#define WMC_TILE_PICK(dt)                                                                         \
+    (z ? (s ? wmc::launch_tile_##dt##_zero_w8 : wmc::launch_tile_##dt##_zero_w16)                 \
+       : (s ? wmc::launch_tile_##dt##_rep_w8 : wmc::launch_tile_##dt##_rep_w16))
     switch (dtype) {
-        case WMC_F32: return z ? wmc::launch_tile_f32_zero(steps, map, p, batch_tiles, st)
-                               : wmc::launch_tile_f32_rep(steps, map, p, batch_tiles, st);
-        case WMC_BF16: return z ? wmc::launch_tile_bf16_zero(steps, map, p, batch_tiles, st)
-                                : wmc::launch_tile_bf16_rep(steps, map, p, batch_tiles, st);
-        case WMC_F16: return z ? wmc::launch_tile_f16_zero(steps, map, p, batch_tiles, st)
-                               : wmc::launch_tile_f16_rep(steps, map, p, batch_tiles, st);
+        case WMC_F32: return WMC_TILE_PICK(f32)(steps, map, p, batch_tiles, st);
+        case WMC_BF16: return WMC_TILE_PICK(bf16)(steps, map, p, batch_tiles, st);
+        case WMC_F16: return WMC_TILE_PICK(f16)(steps, map, p, batch_tiles, st);
         default: return cudaErrorInvalidValue;
     }
+#undef WMC_TILE_PICK
 }
+
+constexpr int kDefaultTile = 1;
+constexpr int kTileShapes = 2;  // wmc_config_t.tile = 1 .. kTileShapes (0: kDefaultTile)
 
 constexpr int kDefaultSteps = 4;
 constexpr size_t kStatusBytes = WMC_WORKSPACE_ALIGN;
@@ -169,7 +169,7 @@ size_t image_bytes(int32_t h, int64_t ld, wmc_dtype_t dtype) {
 wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
                       wmc_dtype_t dtype, float lambda, float step, int32_t iters,
                       wmc_boundary_t bnd, int steps_per_launch, void *ws, cudaStream_t st,
-                      bool fd = false) {
+                      bool fd = false, int tile = kDefaultTile) {
     const size_t es = elem_size(dtype);
     if (!u0) u0 = f;
     if (h == 0 || w == 0) return WMC_OK;
@@ -214,12 +214,11 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
     bool tma[3] = {false, false, false};
     const void *srcs[3] = {u0, bufs[0], bufs[1]};
     if (T > 1)
-        for (int k = 0; k < 3; ++k) tma[k] = encode_window_map(&maps[k], srcs[k], dtype, h, w, ld);
-    // FP32: f's window is loaded by TMA with U's (same box)
+        for (int k = 0; k < 3; ++k) tma[k] = encode_window_map(&maps[k], srcs[k], dtype, h, w, ld, tile);
+    // f's window is loaded by TMA with U's (same box)
     alignas(64) CUtensorMap fmap;
     memset(&fmap, 0, sizeof fmap);
-    const bool f_tma = T > 1 && dtype == WMC_F32 && f != nullptr &&
-                       encode_window_map(&fmap, f, dtype, h, w, ld);
+    const bool f_tma = T > 1 && f != nullptr && encode_window_map(&fmap, f, dtype, h, w, ld, tile);
 
     const void *src = u0;
     int src_id = 0;
@@ -242,7 +241,7 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
             e = wmc::launch_stream((int)dtype, fd ? wmc::MODE_FD_FLOW : wmc::MODE_FLOW, (int)bnd, sp,
                                    vec, st);
         } else {
-            wmc::TileV2Params tp{};
+            wmc::TileParams tp{};
             tp.u = src;
             tp.f = f;
             tp.out = dst;
@@ -257,7 +256,7 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
             tp.pdl = prev_tile ? 1 : 0;  // follows a tile launch: may overlap its tail
             tp.f_tma = (f_tma && tma[src_id]) ? 1 : 0;
             alignas(64) CUtensorMap pair[2] = {maps[src_id], fmap};
-            e = launch_tile(dtype, bnd, s, pair, tp, -1, st);
+            e = launch_tile(dtype, bnd, tile, s, pair, tp, -1, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "flow kernel launch");
         prev_tile = s > 1;
@@ -275,7 +274,7 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
 wmc_status_t check_flow_args(const void *f, const void *u0, void *u, int32_t h, int32_t w,
                              int64_t ld, wmc_dtype_t dtype, float lambda, float step,
                              int32_t iters, wmc_boundary_t bnd, const wmc_config_t *cfg,
-                             int *steps_out) {
+                             int *steps_out, int *tile_out = nullptr) {
     wmc_status_t s;
     if ((s = check_enums(dtype, bnd)) != WMC_OK) return s;
     if ((s = check_image(h, w, ld, "image")) != WMC_OK) return s;
@@ -289,10 +288,12 @@ wmc_status_t check_flow_args(const void *f, const void *u0, void *u, int32_t h, 
         if (cfg->steps_per_launch < 0 || cfg->steps_per_launch > wmc::kMaxSteps)
             return fail(WMC_ERR_INVALID_ARG, "steps_per_launch must be 0..%d (got %d)",
                         wmc::kMaxSteps, cfg->steps_per_launch);
-        if (cfg->tile != 0) return fail(WMC_ERR_INVALID_ARG, "unknown tile %d", cfg->tile);
+        if (cfg->tile < 0 || cfg->tile > kTileShapes)
+            return fail(WMC_ERR_INVALID_ARG, "unknown tile %d (0 .. %d)", cfg->tile, kTileShapes);
         if (cfg->steps_per_launch > 0) T = cfg->steps_per_launch;
     }
     *steps_out = T;
+    if (tile_out) *tile_out = (cfg && cfg->tile > 0) ? cfg->tile : kDefaultTile;
     if (h > 0 && w > 0) {
         if (!u) return fail(WMC_ERR_INVALID_ARG, "u is NULL");
         if (!f && !u0) return fail(WMC_ERR_INVALID_ARG, "f and u0 are both NULL");
@@ -312,15 +313,16 @@ struct BatchPlan {
     int64_t off_images, off_tiles;
     int32_t n, dtype, bnd, steps;
     int32_t owt, oht;
+    int32_t tile;
     uint32_t magic;
 };
 static_assert(sizeof(BatchPlan) <= sizeof(wmc_batch_t), "plan does not fit wmc_batch_t");
 
-void out_tile(wmc_dtype_t dtype, int T, int *owt, int *oht) {
-    // Out<S, T> for the storage type; computed like the device-side struct.
-    (void)dtype;
+// Output tile of T steps per launch with tile shape `tile`: the region less T - 1 cells (plus the
+// region's own halo) on each side.
+void out_tile(int T, int tile, int *owt, int *oht) {
     *owt = wmc::kCW + 2 - 2 * T;
-    *oht = wmc::kCH + 2 - 2 * T;
+    *oht = wmc::kQR * wmc::tile_warps(tile) + 2 - 2 * T;
 }
 
 struct BatchLayout {
@@ -329,10 +331,10 @@ struct BatchLayout {
     std::vector<size_t> buf_off;
 };
 
-BatchLayout batch_layout(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype, int T) {
+BatchLayout batch_layout(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype, int T, int tile) {
     BatchLayout L{};
     int owt, oht;
-    out_tile(dtype, T, &owt, &oht);
+    out_tile(T, tile, &owt, &oht);
     L.off_images = kStatusBytes;
     L.off_tiles = round_up(L.off_images + (size_t)n * sizeof(wmc::BatchImage), WMC_WORKSPACE_ALIGN);
     L.ntiles = 0;
@@ -354,6 +356,8 @@ int batch_steps(const wmc_config_t *cfg) {
     return (cfg && cfg->steps_per_launch > 0) ? cfg->steps_per_launch : kDefaultSteps;
 }
 
+int batch_tile(const wmc_config_t *cfg) { return (cfg && cfg->tile > 0) ? cfg->tile : kDefaultTile; }
+
 wmc_status_t check_batch(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype, wmc_boundary_t bnd,
                          const wmc_config_t *cfg) {
     wmc_status_t s;
@@ -364,7 +368,8 @@ wmc_status_t check_batch(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype, 
         if (cfg->steps_per_launch < 0 || cfg->steps_per_launch > wmc::kMaxSteps)
             return fail(WMC_ERR_INVALID_ARG, "steps_per_launch must be 0..%d (got %d)",
                         wmc::kMaxSteps, cfg->steps_per_launch);
-        if (cfg->tile != 0) return fail(WMC_ERR_INVALID_ARG, "unknown tile %d", cfg->tile);
+        if (cfg->tile < 0 || cfg->tile > kTileShapes)
+            return fail(WMC_ERR_INVALID_ARG, "unknown tile %d (0 .. %d)", cfg->tile, kTileShapes);
     }
     const size_t es = elem_size(dtype);
     // every u must be disjoint from every other buffer; f buffers may overlap each other
@@ -623,9 +628,9 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
                             int32_t iters, wmc_boundary_t bnd, const wmc_config_t *config,
                             void *workspace, size_t workspace_bytes, wmc_stream_t stream) {
     g_last_error[0] = 0;
-    int T = 0;
+    int T = 0, tile = kDefaultTile;
     wmc_status_t s =
-        check_flow_args(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, config, &T);
+        check_flow_args(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, config, &T, &tile);
     if (s != WMC_OK) return s;
     if (h == 0 || w == 0) return WMC_OK;
     if (iters > 0) {
@@ -641,7 +646,7 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
             return fail(WMC_ERR_ALIAS, "workspace overlaps an image");
     }
     return run_flow(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, T, workspace,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, false, tile);
 }
 
 wmc_status_t wmc_denoise_fd(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
@@ -809,7 +814,9 @@ size_t wmc_batch_workspace_size(const wmc_image_t *imgs, int32_t n, wmc_dtype_t 
     for (int32_t i = 0; i < n; ++i)
         if (imgs[i].h < 0 || imgs[i].w < 0 || (imgs[i].h > 0 && imgs[i].w > 0 && imgs[i].ld < imgs[i].w))
             return 0;
-    return batch_layout(imgs, n, dtype, T).total;
+    const int tile = batch_tile(config);
+    if (tile < 1 || tile > kTileShapes) return 0;
+    return batch_layout(imgs, n, dtype, T, tile).total;
 }
 
 wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
@@ -821,7 +828,8 @@ wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtyp
     wmc_status_t s = check_batch(imgs, n, dtype, bnd, config);
     if (s != WMC_OK) return s;
     const int T = batch_steps(config);
-    const BatchLayout L = batch_layout(imgs, n, dtype, T);
+    const int tile = batch_tile(config);
+    const BatchLayout L = batch_layout(imgs, n, dtype, T, tile);
     if (!workspace || workspace_bytes < L.total)
         return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", L.total,
                     workspace ? workspace_bytes : (size_t)0);
@@ -835,7 +843,7 @@ wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtyp
             return fail(WMC_ERR_ALIAS, "workspace overlaps image %d", i);
     }
     int owt, oht;
-    out_tile(dtype, T, &owt, &oht);
+    out_tile(T, tile, &owt, &oht);
     char *base = static_cast<char *>(workspace);
     std::vector<wmc::BatchImage> desc((size_t)n);
     std::vector<int4> tiles;
@@ -855,7 +863,7 @@ wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtyp
         d.c_f = m.step;
         d.c_h = m.step * m.lambda / 12.0f;
         for (int r = 0; r < 3; ++r)
-            d.use_tma[r] = encode_window_map(&d.map[r], d.buf[r], dtype, m.h, m.w, m.ld) ? 1 : 0;
+            d.use_tma[r] = encode_window_map(&d.map[r], d.buf[r], dtype, m.h, m.w, m.ld, tile) ? 1 : 0;
         for (int y0 = 0; y0 < m.h; y0 += oht)
             for (int x0 = 0; x0 < m.w; x0 += owt) tiles.push_back(make_int4(i, x0, y0, 0));
     }
@@ -880,6 +888,7 @@ wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtyp
     bp.steps = T;
     bp.owt = owt;
     bp.oht = oht;
+    bp.tile = tile;
     bp.magic = kBatchMagic;
     memcpy(plan, &bp, sizeof bp);
     return WMC_OK;
@@ -898,7 +907,7 @@ wmc_status_t wmc_batch_run(const wmc_batch_t *plan, int32_t iters, wmc_stream_t 
     unsigned int *status = reinterpret_cast<unsigned int *>(base);
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return cuda_fail(e, "clear status");
-    wmc::TileV2Params p{};
+    wmc::TileParams p{};
     p.images = reinterpret_cast<const wmc::BatchImage *>(base + bp.off_images);
     p.tiles = reinterpret_cast<const int4 *>(base + bp.off_tiles);
     p.owt = bp.owt;
@@ -920,7 +929,7 @@ wmc_status_t wmc_batch_run(const wmc_batch_t *plan, int32_t iters, wmc_stream_t 
         p.src_role = src;
         p.dst_role = dst;
         p.pdl = launches++ > 0 ? 1 : 0;  // follows a tile launch: may overlap its tail
-        e = launch_tile((wmc_dtype_t)bp.dtype, (wmc_boundary_t)bp.bnd, s, nullptr, p, bp.ntiles, st);
+        e = launch_tile((wmc_dtype_t)bp.dtype, (wmc_boundary_t)bp.bnd, bp.tile, s, nullptr, p, bp.ntiles, st);
     });
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
     return WMC_OK;
@@ -938,13 +947,70 @@ wmc_status_t wmc_denoise_batched(const wmc_image_t *imgs, int32_t n, wmc_dtype_t
 
 size_t wmc_batch_autotune_workspace_size(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype) {
     size_t best = 0;
-    for (int T = 1; T <= wmc::kMaxSteps; ++T) {
-        wmc_config_t c{T, 0};
-        const size_t b = wmc_batch_workspace_size(imgs, n, dtype, &c);
-        if (b == 0) return 0;
-        best = b > best ? b : best;
-    }
+    for (int tile = 1; tile <= kTileShapes; ++tile)
+        for (int T = 1; T <= wmc::kMaxSteps; ++T) {
+            wmc_config_t c{T, tile};
+            const size_t b = wmc_batch_workspace_size(imgs, n, dtype, &c);
+            if (b == 0) return 0;
+            best = b > best ? b : best;
+        }
     return best;
+}
+
+// Times each candidate configuration on the caller's batch and keeps the fastest per iteration.
+static wmc_status_t autotune_configs(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                                     wmc_boundary_t bnd, const wmc_config_t *cands, int32_t nc,
+                                     int32_t trial_iters, void *workspace, size_t workspace_bytes,
+                                     wmc_config_t *best, float *ms_per_iter, wmc_stream_t stream) {
+    if (trial_iters < 1) return fail(WMC_ERR_INVALID_ARG, "trial_iters must be >= 1 (got %d)", trial_iters);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return cuda_fail(e, "event create");
+    }
+    float best_ms = 0.0f;
+    int best_k = -1;
+    wmc_status_t s = WMC_OK;
+    for (int32_t k = 0; k < nc && s == WMC_OK; ++k) {
+        const wmc_config_t c = cands[k];
+        const int T = batch_steps(&c);
+        wmc_batch_t plan;
+        s = wmc_batch_plan(imgs, n, dtype, bnd, &c, workspace, workspace_bytes, &plan, stream);
+        if (s != WMC_OK) break;
+        // one untimed run (first-launch costs), then the timed one; each covers whole launches
+        const int it = ((trial_iters + T - 1) / T) * T;
+        if ((s = wmc_batch_run(&plan, T, stream)) != WMC_OK) break;
+        if ((e = cudaEventRecord(a, st)) != cudaSuccess) { s = cuda_fail(e, "event record"); break; }
+        if ((s = wmc_batch_run(&plan, it, stream)) != WMC_OK) break;
+        if ((e = cudaEventRecord(b, st)) != cudaSuccess || (e = cudaEventSynchronize(b)) != cudaSuccess) {
+            s = cuda_fail(e, "event sync");
+            break;
+        }
+        float ms = 0.0f;
+        if ((e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) { s = cuda_fail(e, "event time"); break; }
+        const float per_iter = ms / (float)it;
+        if (ms_per_iter) ms_per_iter[k] = per_iter;
+        if (best_k < 0 || per_iter < best_ms) {
+            best_ms = per_iter;
+            best_k = k;
+        }
+        const unsigned int *status = static_cast<const unsigned int *>(workspace);
+        unsigned int hs = 0;
+        if ((e = cudaMemcpy(&hs, status, sizeof hs, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            s = cuda_fail(e, "read status");
+            break;
+        }
+        if (hs) s = fail(WMC_ERR_TIMEOUT, "a tile load timed out during the trial of tile %d, %d steps per launch",
+                         c.tile, T);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (s != WMC_OK) return s;
+    *best = cands[best_k];
+    return WMC_OK;
 }
 
 wmc_status_t wmc_batch_autotune(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
@@ -960,59 +1026,44 @@ wmc_status_t wmc_batch_autotune(const wmc_image_t *imgs, int32_t n, wmc_dtype_t 
     }
     if (n_candidates < 1 || n_candidates > 64)
         return fail(WMC_ERR_INVALID_ARG, "n_candidates must be 1..64 (got %d)", n_candidates);
-    for (int32_t k = 0; k < n_candidates; ++k)
+    wmc_config_t cands[64];
+    for (int32_t k = 0; k < n_candidates; ++k) {
         if (candidates[k] < 1 || candidates[k] > wmc::kMaxSteps)
             return fail(WMC_ERR_INVALID_ARG, "candidate %d: steps per launch must be 1..%d (got %d)", k,
                         wmc::kMaxSteps, candidates[k]);
-    if (trial_iters < 1) return fail(WMC_ERR_INVALID_ARG, "trial_iters must be >= 1 (got %d)", trial_iters);
-    cudaStream_t st = (cudaStream_t)stream;
-    cudaEvent_t a = nullptr, b = nullptr;
-    cudaError_t e = cudaEventCreate(&a);
-    if (e == cudaSuccess) e = cudaEventCreate(&b);
-    if (e != cudaSuccess) {
-        if (a) cudaEventDestroy(a);
-        return cuda_fail(e, "event create");
+        cands[k] = wmc_config_t{candidates[k], 0};
     }
-    float best_ms = 0.0f;
-    int best_T = 0;
-    wmc_status_t s = WMC_OK;
-    for (int32_t k = 0; k < n_candidates && s == WMC_OK; ++k) {
-        const wmc_config_t c{candidates[k], 0};
-        wmc_batch_t plan;
-        s = wmc_batch_plan(imgs, n, dtype, bnd, &c, workspace, workspace_bytes, &plan, stream);
-        if (s != WMC_OK) break;
-        // one untimed run (first-launch costs), then the timed one; each covers whole launches
-        const int it = ((trial_iters + c.steps_per_launch - 1) / c.steps_per_launch) * c.steps_per_launch;
-        if ((s = wmc_batch_run(&plan, c.steps_per_launch, stream)) != WMC_OK) break;
-        if ((e = cudaEventRecord(a, st)) != cudaSuccess) { s = cuda_fail(e, "event record"); break; }
-        if ((s = wmc_batch_run(&plan, it, stream)) != WMC_OK) break;
-        if ((e = cudaEventRecord(b, st)) != cudaSuccess || (e = cudaEventSynchronize(b)) != cudaSuccess) {
-            s = cuda_fail(e, "event sync");
-            break;
+    return autotune_configs(imgs, n, dtype, bnd, cands, n_candidates, trial_iters, workspace,
+                            workspace_bytes, best, ms_per_iter, stream);
+}
+
+wmc_status_t wmc_batch_autotune_configs(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype,
+                                        wmc_boundary_t bnd, const wmc_config_t *candidates,
+                                        int32_t n_candidates, int32_t trial_iters, void *workspace,
+                                        size_t workspace_bytes, wmc_config_t *best, float *ms_per_iter,
+                                        wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    if (!best) return fail(WMC_ERR_INVALID_ARG, "best is NULL");
+    wmc_config_t cands[64];
+    if (!candidates) {
+        static const int32_t kSteps[] = {2, 3, 4, 5, 6, 8};
+        n_candidates = 0;
+        for (int tile = 1; tile <= kTileShapes; ++tile)
+            for (int32_t T : kSteps) cands[n_candidates++] = wmc_config_t{T, tile};
+    } else {
+        if (n_candidates < 1 || n_candidates > 64)
+            return fail(WMC_ERR_INVALID_ARG, "n_candidates must be 1..64 (got %d)", n_candidates);
+        for (int32_t k = 0; k < n_candidates; ++k) {
+            const wmc_config_t &c = candidates[k];
+            if (c.steps_per_launch < 1 || c.steps_per_launch > wmc::kMaxSteps || c.tile < 0 ||
+                c.tile > kTileShapes)
+                return fail(WMC_ERR_INVALID_ARG, "candidate %d: {steps %d, tile %d} outside {1..%d, 0..%d}", k,
+                            c.steps_per_launch, c.tile, wmc::kMaxSteps, kTileShapes);
+            cands[k] = c;
         }
-        float ms = 0.0f;
-        if ((e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) { s = cuda_fail(e, "event time"); break; }
-        const float per_iter = ms / (float)it;
-        if (ms_per_iter) ms_per_iter[k] = per_iter;
-        if (best_T == 0 || per_iter < best_ms) {
-            best_ms = per_iter;
-            best_T = c.steps_per_launch;
-        }
-        const unsigned int *status = static_cast<const unsigned int *>(workspace);
-        unsigned int hs = 0;
-        if ((e = cudaMemcpy(&hs, status, sizeof hs, cudaMemcpyDeviceToHost)) != cudaSuccess) {
-            s = cuda_fail(e, "read status");
-            break;
-        }
-        if (hs) s = fail(WMC_ERR_TIMEOUT, "a tile load timed out during the trial of %d steps per launch",
-                         c.steps_per_launch);
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    if (s != WMC_OK) return s;
-    best->steps_per_launch = best_T;
-    best->tile = 0;
-    return WMC_OK;
+    return autotune_configs(imgs, n, dtype, bnd, cands, n_candidates, trial_iters, workspace,
+                            workspace_bytes, best, ms_per_iter, stream);
 }
 
 size_t wmc_denoise_l1_workspace_size(int32_t h, int32_t w, int64_t ld) {
@@ -1241,6 +1292,72 @@ wmc_status_t wmc_denoise_noalloc(const void *f, const void *u0, void *u, int32_t
     // needs a defined value (the ping-pong image is always written before it is read)
     return run_flow(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, T, scratch,
                     (cudaStream_t)stream);
+}
+
+wmc_status_t wmc_denoise_noalloc_status(wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    void *scratch = nullptr;
+    wmc_status_t s = noalloc_scratch(&scratch);
+    if (s != WMC_OK) return s;
+    return wmc_denoise_status(scratch, stream);
+}
+
+wmc_status_t wmc_selftest_status_timeout(int32_t target, int64_t limit_ns, wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    if (limit_ns < 1 || limit_ns > 1000000000LL)
+        return fail(WMC_ERR_INVALID_ARG, "limit_ns = %lld outside 1 .. 1e9", (long long)limit_ns);
+    unsigned int *word = nullptr;
+    if (target == WMC_SELFTEST_EVAL) {
+        cudaError_t e = wmc::eval_status_word(&word);
+        if (e != cudaSuccess) return cuda_fail(e, "evaluation status word");
+    } else if (target == WMC_SELFTEST_NOALLOC) {
+        void *scratch = nullptr;
+        wmc_status_t s = noalloc_scratch(&scratch);
+        if (s != WMC_OK) return s;
+        word = static_cast<unsigned int *>(scratch);
+    } else {
+        return fail(WMC_ERR_INVALID_ARG, "unknown self-test target %d", target);
+    }
+    cudaError_t e = wmc::launch_selftest_wait(word, (uint64_t)limit_ns, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "self-test wait kernel launch");
+    return WMC_OK;
+}
+
+size_t wmc_backward_workspace_size(int32_t n, int32_t h, int32_t w, int64_t ld, int32_t K,
+                                   int32_t ckpt_every) {
+    const size_t base = wmc_unrolled_workspace_size(n, h, w, ld, K, ckpt_every);
+    if (base == 0) return 0;
+    // the unrolled workspace, then U^K of the stack (the forward's output, not returned)
+    return round_up(base, WMC_WORKSPACE_ALIGN) +
+           round_up(span_bytes(n * h, w, ld, sizeof(float)), WMC_WORKSPACE_ALIGN);
+}
+
+wmc_status_t wmc_backward(const float *f, const float *lambda, float step, int32_t K,
+                          int32_t ckpt_every, int32_t n, int32_t h, int32_t w, int64_t ld,
+                          wmc_boundary_t bnd, const float *grad_u, float *grad_f,
+                          float *grad_lambda, void *workspace, size_t workspace_bytes,
+                          wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    wmc_status_t s = check_unrolled(f, lambda, step, K, ckpt_every, n, h, w, ld, bnd);
+    if (s != WMC_OK) return s;
+    if ((int64_t)n * h > 0x7fffffffLL) return fail(WMC_ERR_INVALID_ARG, "n * h beyond 2^31 - 1");
+    const size_t need = wmc_backward_workspace_size(n, h, w, ld, K, ckpt_every);
+    if (!workspace || workspace_bytes < need)
+        return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need,
+                    workspace ? workspace_bytes : (size_t)0);
+    if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
+        return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    const size_t nbytes = span_bytes(n * h, w, ld, sizeof(float));
+    if (overlap(workspace, need, f, nbytes) || overlap(workspace, need, grad_u, nbytes) ||
+        (grad_f && overlap(workspace, need, grad_f, nbytes)))
+        return fail(WMC_ERR_ALIAS, "workspace overlaps f, grad_u or grad_f");
+    const size_t inner = round_up(wmc_unrolled_workspace_size(n, h, w, ld, K, ckpt_every), WMC_WORKSPACE_ALIGN);
+    float *uK = reinterpret_cast<float *>(static_cast<char *>(workspace) + inner);
+    // the forward sweep stores the checkpoints in the inner workspace; the reverse sweep reads them
+    s = wmc_unrolled_forward(f, lambda, step, K, ckpt_every, n, h, w, ld, bnd, uK, workspace, inner, stream);
+    if (s != WMC_OK) return s;
+    return wmc_unrolled_backward(f, lambda, step, K, ckpt_every, n, h, w, ld, bnd, grad_u, grad_f,
+                                 grad_lambda, workspace, inner, stream);
 }
 
 }  // extern "C"

@@ -33,7 +33,8 @@ namespace wmc {
 // opposite-sign tie and RNE arithmetic gives L = +0 for U and for -U alike; taking the sign of
 // L + 2^-40 a_1 instead makes the choice odd in U (H^w(-U) = -H^w(U) bit for bit) and changes
 // nothing outside that tie band.
-__device__ __forceinline__ float select12(float L, float a1, float a2, float a5, float a6) {
+// Ls = L + 2^-40 a1 computed by the caller.
+__device__ __forceinline__ float select12_ls(float L, float a1, float a2, float a5, float a6, float Ls) {
     const float aL = fabsf(L);
     float t = aL - fabsf(a1);
     const float t2 = aL - fabsf(a2);
@@ -42,8 +43,11 @@ __device__ __forceinline__ float select12(float L, float a1, float a2, float a5,
     t = fabsf(t2) < fabsf(t) ? t2 : t;
     t = fabsf(t5) < fabsf(t) ? t5 : t;
     t = fabsf(t6) < fabsf(t) ? t6 : t;
-    const float Ls = fmaf(0x1p-40f, a1, L);
     return __int_as_float(__float_as_int(t) ^ (__float_as_int(Ls) & 0x80000000));
+}
+
+__device__ __forceinline__ float select12(float L, float a1, float a2, float a5, float a6) {
+    return select12_ls(L, a1, a2, a5, a6, fmaf(0x1p-40f, a1, L));
 }
 
 // 12 * H^w at the centre of a 3x3 neighbourhood (rows: n* above, s* below).
@@ -103,8 +107,9 @@ __device__ __forceinline__ float2 half_laplace12_x2(float2 nw, float2 n, float2 
     const float2 a2 = __ffma2_rn(two, p, __fadd2_rn(A, B));
     const float2 a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
     const float2 a6 = __ffma2_rn(two, sub2(p, q), B);
-    return make_float2(select12(L.x, a1.x, a2.x, a5.x, a6.x),
-                       select12(L.y, a1.y, a2.y, a5.y, a6.y));
+    // the sign guard of select12 stays a scalar FMA per lane: one packed FMA for both lanes makes
+    // each selection wait for the other lane's operands and measured 1.3 % slower
+    return make_float2(select12(L.x, a1.x, a2.x, a5.x, a6.x), select12(L.y, a1.y, a2.y, a5.y, a6.y));
 }
 
 // ---------------------------------------------------------------- storage types

@@ -12,7 +12,7 @@
 // Box b covers image columns x0 = 128 (b mod nbx) .. x0 + 127 and rows y0 = 64 (b div nbx) ..
 // y0 + 63; its window starts at (X0, Y0) = (x0 - 4, y0 - 1): x0 - 4 keeps the TMA x coordinate on
 // a 16-byte boundary, and output cell (y, x) is window cell (y - Y0, x - X0).
-#include "wmc_tile.cuh"
+#include "wmc_window.cuh"
 
 namespace wmc {
 
@@ -167,6 +167,10 @@ cudaError_t eval_tma_status(unsigned int *word, cudaStream_t st) {
     e = cudaMemcpyToSymbolAsync(g_eval_status, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
+}
+
+cudaError_t eval_status_word(unsigned int **word) {
+    return cudaGetSymbolAddress(reinterpret_cast<void **>(word), g_eval_status);
 }
 
 }  // namespace wmc

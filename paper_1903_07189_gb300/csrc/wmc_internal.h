@@ -13,25 +13,36 @@ enum Mode { MODE_EVAL = 0, MODE_FLOW = 1, MODE_FD_EVAL = 2, MODE_FD_FLOW = 3 };
 constexpr int kMaxSteps = 8;
 
 struct StreamParams;   // wmc_stream.cuh
-struct TileV2Params;   // wmc_tile.cuh
+struct TileParams;     // wmc_tile.cuh
 
 // Single-pass kernels (evaluation, one flow step).  dtype: 0 f32, 1 bf16, 2 f16.
 // vec: every row start of u, f and out is aligned to two elements (2-element accesses).
 cudaError_t launch_stream(int dtype, int mode, int bnd, const StreamParams &p, bool vec,
                           cudaStream_t st);
 
-// Temporally blocked flow kernels, steps = 2..kMaxSteps.
+// Temporally blocked flow kernels, steps = 1..kMaxSteps, one function per storage type, boundary
+// rule and tile shape (w16: 16 warps, a 128 x 64 region; w8: 8 warps, 128 x 32).
 // map: single-image launches pass two tensor maps, U's window then f's (read when p.f_tma);
 // batch launches (batch_tiles >= 0) pass nullptr and use the image descriptors' maps
-cudaError_t launch_tile_f32_rep(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
-cudaError_t launch_tile_f32_zero(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
-cudaError_t launch_tile_bf16_rep(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
-cudaError_t launch_tile_bf16_zero(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
-cudaError_t launch_tile_f16_rep(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
-cudaError_t launch_tile_f16_zero(int steps, const CUtensorMap *map, const TileV2Params &p, int64_t batch_tiles, cudaStream_t st);
+#define WMC_DECLARE_TILE(name) \
+    cudaError_t name(int steps, const CUtensorMap *map, const TileParams &p, int64_t batch_tiles, cudaStream_t st);
+WMC_DECLARE_TILE(launch_tile_f32_rep_w16)
+WMC_DECLARE_TILE(launch_tile_f32_zero_w16)
+WMC_DECLARE_TILE(launch_tile_bf16_rep_w16)
+WMC_DECLARE_TILE(launch_tile_bf16_zero_w16)
+WMC_DECLARE_TILE(launch_tile_f16_rep_w16)
+WMC_DECLARE_TILE(launch_tile_f16_zero_w16)
+WMC_DECLARE_TILE(launch_tile_f32_rep_w8)
+WMC_DECLARE_TILE(launch_tile_f32_zero_w8)
+WMC_DECLARE_TILE(launch_tile_bf16_rep_w8)
+WMC_DECLARE_TILE(launch_tile_bf16_zero_w8)
+WMC_DECLARE_TILE(launch_tile_f16_rep_w8)
+WMC_DECLARE_TILE(launch_tile_f16_zero_w8)
+#undef WMC_DECLARE_TILE
 
-// Shape of the TMA box the tile kernel loads, in elements of the storage type.
-void tile_box(int dtype, int *box_w, int *box_h);
+// Shape of the TMA box the flow kernel loads for tile shape `tile` (1 or 2), in elements of the
+// storage type.
+void tile_box(int dtype, int tile, int *box_w, int *box_h);
 
 // FP64 energies; workspace: a 256-byte ticket block followed by 3 doubles per CTA.
 int64_t energy_blocks(int32_t h, int32_t w);
@@ -40,6 +51,8 @@ int64_t energy_blocks(int32_t h, int32_t w);
 cudaError_t launch_eval_tma(const CUtensorMap *map, float *out, int64_t ldo, int32_t h, int32_t w,
                             int bnd, float scale, cudaStream_t st);
 cudaError_t eval_tma_status(unsigned int *word, cudaStream_t st);
+// device address of that word on the current device (for the timeout self-test)
+cudaError_t eval_status_word(unsigned int **word);
 
 // wmc_selftest.cu: one CTA waits (bounded) on a transfer that never comes and sets *status
 cudaError_t launch_selftest_wait(unsigned int *status, uint64_t limit_ns, cudaStream_t st);

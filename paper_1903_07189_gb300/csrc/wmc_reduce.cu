@@ -15,7 +15,7 @@
 #include "wmc_device.cuh"
 #include "wmc_internal.h"
 #include "wmc_stream.cuh"
-#include "wmc_tile.cuh"
+#include "wmc_window.cuh"
 
 namespace wmc {
 

@@ -1,6 +1,6 @@
 // wmc_selftest.cu -- a wait that nothing completes, for testing the timeout report of the
 // multi-step kernels' bounded mbarrier waits without faulting or hanging the GPU.
-#include "wmc_tile.cuh"
+#include "wmc_window.cuh"
 
 namespace wmc {
 

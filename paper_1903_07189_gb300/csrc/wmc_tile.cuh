@@ -6,26 +6,29 @@
 // take T steps on it without talking to anyone, and write back the part of the window that is
 // still exact: each step's stale border moves one cell inwards.
 //
-// Geometry (element coordinates; X0, Y0 = global position of shared cell (0,0)):
-//   loaded window  [X0, X0+LW) x [Y0, Y0+LH)       one 2-D TMA box, zero-filled outside the image
-//   updated cells  [X0+2+d, X0+2+d+CW) x [Y0+1, Y0+1+CH)    every step (CW = 128, CH = 64)
-//   exact after T  [X0+1+d+T, X0+3+d+CW-T) x [Y0+T, Y0+2+CH-T)
+// Geometry (element coordinates; X0, Y0 = global position of shared cell (0,0)).  A CTA of NW
+// warps updates 128 columns x CH = 4 NW rows every step (NW = 16: 128 x 64; NW = 8: 128 x 32,
+// the shape for small or short images):
+//   loaded window  [X0, X0+LW) x [Y0, Y0+CH+2)       one 2-D TMA box, zero-filled outside the image
+//   updated cells  [X0+2+d, X0+130+d) x [Y0+1, Y0+1+CH)    every step
+//   exact after T  [X0+1+d+T, X0+131+d-T) x [Y0+T, Y0+2+CH-T)
 //   written back   [x0, x0+OWt) x [y0, y0+OHt),  X0 = x0 - (T+1) rounded down to the TMA
 //                  alignment (16 bytes of elements), d = x0 - (T+1) - X0, y0 = Y0 + T
-// The output tile size (OWt, OHt) is a launch parameter: a single-image launch uses the largest
-// exact tile of its T (Out<S,T>); a batch uses the tile of its deepest T for every launch, which
-// any shallower launch also covers exactly (its exact region is larger), so one tile table
-// serves them all.
+// A single-image launch uses the largest exact output tile of its T (130 - 2T by CH + 2 - 2T); a
+// batch uses the tile of its deepest T for every launch, which any shallower launch also covers
+// exactly (its exact region is larger), so one tile table serves them all.
 // Each tile rounds its own window origin down to the TMA alignment, which keeps every TMA
 // x-coordinate aligned without constraining where output tiles start.
 //
-// Threads: 16 warps as 2 (x) x 8 (y); lane l of warp (wx, wy) updates columns j = 2 + d + 64 wx + l
+// Threads: warps as 2 (x) x NW/2 (y); lane l of warp (wx, wy) updates columns j = 2 + d + 64 wx + l
 // and j + 32 for rows i = 1 + 8 wy .. 8 + 8 wy.  The two columns are the two lanes of packed
 // FP32x2 arithmetic: every operand pair (west, centre, east neighbours of both cells) is read
 // by two conflict-free 4-byte shared loads straight into an aligned register pair, so no
-// register shuffling is needed (pairing the adjacent columns j, j+1 instead would make six of
-// the nine operands straddle register pairs).  Offsets are constants: the inner loop has no index
-// arithmetic and no per-cell predicates in tiles that lie inside the image.
+// register moves are needed (pairing the adjacent columns j, j+1 instead would make six of
+// the nine operands straddle register pairs; four adjacent columns per lane, read with one
+// 16-byte load, were measured slower: the register moves that form their pairs cost more than
+// the loads they save).  Offsets are constants: the inner loop has no index arithmetic and no
+// per-cell predicates in tiles that lie inside the image.
 //
 // Image boundary.  ZERO: the TMA fill supplies the zeros; in tiles touching the border, cells
 // outside the image are rewritten as 0 every step.  REPLICATE: the ring of cells just outside
@@ -35,14 +38,15 @@
 // ring (tiles overhanging the image) skip the arithmetic: no in-image cell reads those cells.
 //
 // The update's f term (c_f f, constant over the T steps) sits in registers, 8 rows x 2 columns
-// per thread.  For FP32 storage f's window comes as a second TMA box with the same origin, into a
-// third shared buffer, completing the same mbarrier (f is never written by a flow launch, so its
-// copy is issued before the wait for the previous launch); 16-bit storage reads f with
+// per thread.  f's window comes as a second TMA box with the same origin (FP32: into a third
+// shared buffer; 16-bit storage: into buffer 1, whose first write comes after f has been read),
+// completing the same mbarrier; f is never written by a flow launch, so its copy is issued before
+// the wait for the previous launch.  Without TMA (pitches TMA cannot describe) f is read with
 // predicated plain loads.
 //
-// Shared memory always holds FP32; for BF16/FP16 storage the TMA box lands in a staging area
-// and is widened once, and every step rounds its result to the storage type, so the arithmetic
-// is identical to the single-step streaming kernel.
+// Shared memory always holds FP32 for the steps; for BF16/FP16 storage the TMA box of U lands
+// in a staging area and is widened once, and every step rounds its result to the storage type,
+// so the arithmetic is identical to the single-step streaming kernel.
 //
 // Batches: a tile table lists (image, x0, y0) for every tile of every image; each image has a
 // descriptor with its buffers (f, u, workspace), pitch, size, update coefficients (its own
@@ -50,51 +54,31 @@
 // one role and writes the buffer of another, so all images advance T steps together.
 #pragma once
 
-#include <cuda.h>
-#include <string.h>
-
-#include <algorithm>
-#include <atomic>
-
-#include "wmc_device.cuh"
-#include "wmc_internal.h"
+#include "wmc_window.cuh"
 
 namespace wmc {
 
-constexpr int kCW = 128;   // updated columns per step
-constexpr int kCH = 64;    // updated rows per step
-constexpr int kRY = 8;     // rows per thread
-constexpr int kTileWX = 2; // warps across (64 columns each)
-constexpr int kTileWY = kCH / kRY;  // warps down
-constexpr int kTileThreadsV2 = 32 * kTileWX * kTileWY;  // 512
-#ifndef WMC_TILE_MIN_BLOCKS
-#define WMC_TILE_MIN_BLOCKS 2  // CTAs per SM the register allocation must allow (1 CTA/SM with
-                               // 82 registers measured 20% slower at 4096^2)
-#endif
+// Tile shapes (wmc_config_t.tile): 1 = 16 warps (128 x 64 region), 2 = 8 warps (128 x 32).
+__host__ __device__ constexpr int tile_warps(int tile) { return tile == 2 ? 8 : 16; }
+constexpr int kQR = 4;  // region rows per warp (CH = kQR * NW)
 
-template <typename S> struct Geom {
-    static constexpr int A = 16 / (int)sizeof(S);                 // TMA x alignment (elements)
-    // loaded width: the updated columns start 2 + d into the window (d < A, below) and their
-    // east neighbours reach column 130 + d
-    static constexpr int LW = ((kCW + 2 + A + A - 1) / A) * A;
-    static constexpr int LH = kCH + 2;                            // loaded height
-    static constexpr int P = LW;                                  // shared pitch (floats)
-    static constexpr int BUF = LH * P;                            // floats per buffer
-    static constexpr int STAGE_BYTES = sizeof(S) == 4 ? 0 : LH * LW * (int)sizeof(S);
-    // FP32 storage: the window of f arrives by TMA too, into a third buffer after the two
-    // ping-pong buffers (16-bit storage reads f with plain loads)
-    static constexpr int F_BYTES = sizeof(S) == 4 ? BUF * 4 : 0;
-    static constexpr int SMEM = 2 * BUF * 4 + STAGE_BYTES + F_BYTES + 128;  // + alignment slack
-    static_assert(sizeof(S) != 4 || (2 * BUF * 4) % 128 == 0, "the f window must start 128-byte aligned");
-};
-
-// Output tile of a T-step single-image launch, width OW and height OH.  The window origin is the
-// output origin x0 less T + 1, rounded down to the TMA alignment A (window_x0); the d = 0..A-1
-// columns lost to the rounding shift the updated columns (2 + d .. 129 + d in the window), so
-// after T steps the window is exact on exactly [x0, x0 + CW + 2 - 2T).  Rows: y0 - T.
-template <typename S, int T> struct Out {
-    static constexpr int OW = kCW + 2 - 2 * T;
-    static constexpr int OH = kCH + 2 - 2 * T;
+template <typename S, int NW> struct TGeom {
+    static constexpr int THREADS = 32 * NW;
+    static constexpr int WY = NW / 2;                 // warps down (2 across)
+    static constexpr int CH = kRY * WY;               // updated rows per step
+    static constexpr int LH = CH + 2;                 // loaded rows
+    static constexpr int LW = Geom<S>::LW;            // loaded columns (elements)
+    static constexpr int P = LW;                      // shared pitch (floats)
+    static constexpr int BUF = LH * P;                // floats per buffer
+    // FP32: f's window in a third buffer after the two ping-pong buffers.  16-bit: U's staged box
+    // after them (f's lands in buffer 1)
+    static constexpr int EXTRA = sizeof(S) == 4 ? BUF * 4 : LH * LW * (int)sizeof(S);
+    static constexpr int SMEM = 2 * BUF * 4 + EXTRA + 128;  // + alignment slack
+    static_assert(CH == kQR * NW, "a warp pair covers 8 rows");
+    // TMA destinations (buffer 0; FP32: the f window after buffer 1; 16-bit: buffer 1 and the
+    // staging area after it) start 128-byte aligned
+    static_assert(((sizeof(S) == 4 ? 2 : 1) * BUF * 4) % 128 == 0, "TMA destinations are 128-byte aligned");
+    static_assert(LH * LW * (int)sizeof(S) <= BUF * 4, "f's 16-bit window fits in buffer 1");
 };
 
 template <typename S, int T>
@@ -112,7 +96,7 @@ struct alignas(64) BatchImage {
     int32_t use_tma[3];
 };
 
-struct TileV2Params {
+struct TileParams {
     // single image (tiles from blockIdx)
     const void *u;    // U^t (device); read through the tensor map when use_tma
     const void *f;    // f or nullptr (mean-curvature flow)
@@ -130,73 +114,8 @@ struct TileV2Params {
     int32_t owt, oht;     // output tile size
     unsigned int *status; // device status word (bit 0: a bounded wait gave up) or nullptr
     int32_t pdl;          // host side: launch as a programmatic dependent of the previous launch
-    int32_t f_tma;        // single image, FP32: f is read through the second tensor map
+    int32_t f_tma;        // single image: f is read through the second tensor map
 };
-
-// Programmatic dependent launch: a launch made with the programmatic-serialization attribute may
-// start while the previous kernel in the stream finishes (its CTAs fill the SMs the last wave
-// leaves idle and do their set-up); griddep_wait() then blocks until that kernel has completed
-// and its writes are visible.  Both are no-ops for a launch made without the attribute.
-__device__ __forceinline__ void griddep_launch_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-// ------------------------------------------------------------------ TMA / mbarrier helpers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t global_timer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-// Orders this thread's (and, after a CTA barrier, the CTA's) earlier shared-memory accesses of
-// the generic proxy before later async-proxy (TMA) accesses of the same memory: issued before a
-// TMA copy refills a buffer that threads have been reading.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-// Wait for the barrier's phase; give up after `limit_ns` (returns false).  Each try_wait may
-// suspend the thread in hardware for up to 1 ms, so the loop spins very little.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, uint64_t limit_ns) {
-    const uint64_t t0 = global_timer_ns();
-    for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;"
-            " selp.u32 %0, 1, 0, p; }"
-            : "=r"(done)
-            : "r"(bar), "r"(phase), "r"(1000000u)
-            : "memory");
-        if (done) return true;
-        if (global_timer_ns() - t0 > limit_ns) return false;
-    }
-}
-
-constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;  // 0.2 s
 
 // ------------------------------------------------------------------------------- kernel
 // Per-thread constants of one tile.
@@ -212,26 +131,13 @@ struct TileCtx {
 
 enum StepWrite { WRITE_INTERIOR = 0, WRITE_BORDER = 1, WRITE_GLOBAL = 2 };
 
-// Columns j-1, j, j+1 of one shared row for both lanes (j and j+32) as aligned pairs.
-struct Row3 {
-    float2 w, c, e;
-};
-__device__ __forceinline__ Row3 load_row3(const float *r) {
-    Row3 o;
-    o.w = make_float2(r[-1], r[31]);
-    o.c = make_float2(r[0], r[32]);
-    o.e = make_float2(r[1], r[33]);
-    return o;
-}
-
 // One Jacobi step over the thread's kRY rows x 2 columns, reading `src`, writing `dst` (shared)
 // or the output image (last step).
-template <int WMODE, typename S, int BND>
+template <int WMODE, typename S, int BND, int NW>
 __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *__restrict__ dst,
                                           const TileCtx &c, const float2 (&g)[kRY],
                                           S *__restrict__ orow = nullptr, int64_t ld = 0) {
-    using G = Geom<S>;
-    constexpr int P = G::P, LH = G::LH, LW = G::LW;
+    constexpr int P = TGeom<S, NW>::P;
     const float2 ch = make_float2(c.c_h, c.c_h), ck = make_float2(c.c_keep, c.c_keep);
     const float *rp = src + (c.ib - 1) * P + c.j;
     Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
@@ -273,43 +179,13 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
     }
 }
 
-// REPLICATE: set the ring of cells just outside the image (image rows -1 and h, image columns -1
-// and w, where they cross the window) to the value of the nearest in-image cell, so that in-image
-// cells can read their neighbours without clamping.  Corner cells belong to two segments and get
-// the same value from both.
-template <typename S>
-__device__ __forceinline__ void refresh_ring(float *buf, int X0, int Y0, int h, int w, int tid) {
-    using G = Geom<S>;
-    constexpr int LW = G::LW, LH = G::LH, P = G::P;
-    const int ir0 = -1 - Y0, ir1 = h - Y0;  // shared rows of image rows -1 and h
-    const int jc0 = -1 - X0, jc1 = w - X0;  // shared columns of image columns -1 and w
-    const int jlo = max(jc0, 0), jhi = min(jc1, LW - 1);
-    const int ilo = max(ir0, 0), ihi = min(ir1, LH - 1);
-    for (int t = tid; t < 2 * (LW + LH); t += kTileThreadsV2) {
-        int i, j2;
-        if (t < 2 * LW) {
-            i = (t < LW) ? ir0 : ir1;
-            j2 = (t < LW) ? t : t - LW;
-            if (i < 0 || i >= LH || j2 < jlo || j2 > jhi) continue;
-        } else {
-            const int q = t - 2 * LW;
-            j2 = (q < LH) ? jc0 : jc1;
-            i = (q < LH) ? q : q - LH;
-            if (j2 < 0 || j2 >= LW || i < ilo || i > ihi) continue;
-        }
-        const int yy = Y0 + i, xx = X0 + j2;
-        const int ci = min(max(yy, 0), h - 1) - Y0, cj = min(max(xx, 0), w - 1) - X0;
-        buf[i * P + j2] = buf[ci * P + cj];
-    }
-}
-
 // One tile's job: which image buffers, coefficients and output tile.
 template <typename S> struct TileJob {
     const S *u;                // U^t (read through `map` when use_tma)
     const S *f;                // f or nullptr
     const CUtensorMap *map;
     const CUtensorMap *fmap;   // f's tensor map, used when f_tma
-    bool f_tma;                // FP32 and TMA: f's window is loaded with U's into fbuf
+    bool f_tma;                // f's window is loaded by TMA with U's
     int64_t ld;
     int h, w;
     float c_keep, c_h, c_f;
@@ -321,12 +197,12 @@ template <typename S> struct TileJob {
 // write the output tile through `out_of()` (called after the steps, so the output pointer is not
 // kept in registers through them).  `phase` is the mbarrier parity this tile's load completes.
 // Returns false if the window load timed out (the status word is set).
-template <int T, typename S, int BND, typename OutFn>
-__device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
-                                         unsigned int *status, float *buf0, float *buf1,
-                                         uint64_t *bar, uint32_t phase, OutFn out_of) {
-    using G = Geom<S>;
-    constexpr int LW = G::LW, LH = G::LH, BUF = G::BUF;
+template <int T, typename S, int BND, int NW, typename OutFn>
+__device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht, unsigned int *status,
+                                         float *buf0, float *buf1, uint64_t *bar, uint32_t phase,
+                                         OutFn out_of) {
+    using G = TGeom<S, NW>;
+    constexpr int LW = G::LW, LH = G::LH, BUF = G::BUF, P = G::P, NT = G::THREADS;
     TileCtx c;
     c.h = jb.h;
     c.w = jb.w;
@@ -342,24 +218,23 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     // copy and later waits for it, so the other threads never poll it).  U^t is the previous
     // launch's output: wait for that launch first (every later access of this CTA to U^t or to
     // the output buffer comes after this thread's wait through the CTA barriers below).
-    // FP32 with TMA: f's window (same box and origin as U's) lands in the third buffer and
-    // completes the same barrier.  f is never written by a flow launch, so its copy goes out
-    // before the wait for the previous launch.
-    const bool ftma = sizeof(S) == 4 && jb.use_tma && jb.f_tma && jb.f != nullptr;
-    float *fbuf = buf1 + BUF;
+    // f's window (same box and origin as U's) completes the same barrier: FP32 into the third
+    // buffer, 16-bit storage into buffer 1 (read into registers before the first step writes
+    // buffer 1).  f is never written by a flow launch, so its copy goes out before the wait for
+    // the previous launch.
+    const bool ftma = jb.use_tma && jb.f_tma && jb.f != nullptr;
+    void *fwin = (sizeof(S) == 4) ? static_cast<void *>(buf1 + BUF) : static_cast<void *>(buf1);
+    void *stage = (sizeof(S) == 4) ? static_cast<void *>(buf0) : static_cast<void *>(buf1 + BUF);
     if (jb.use_tma) {
         if (tid == 0) {
             mbar_expect_tx(smem_u32(bar), (uint32_t)(LW * LH * sizeof(S)) * (ftma ? 2u : 1u));
-            if (ftma) tma_load_2d(smem_u32(fbuf), jb.fmap, X0, Y0, smem_u32(bar));
+            if (ftma) tma_load_2d(smem_u32(fwin), jb.fmap, X0, Y0, smem_u32(bar));
             griddep_wait();
-            void *dst = (sizeof(S) == 4) ? static_cast<void *>(buf0)
-                                         : static_cast<void *>(buf1 + BUF);  // staging
-            tma_load_2d(smem_u32(dst), jb.map, X0, Y0, smem_u32(bar));
+            tma_load_2d(smem_u32(stage), jb.map, X0, Y0, smem_u32(bar));
         }
     } else {
-        constexpr int P = G::P;
         griddep_wait();
-        for (int idx = tid; idx < LH * LW; idx += kTileThreadsV2) {
+        for (int idx = tid; idx < LH * LW; idx += NT) {
             const int i = idx / LW, j = idx - (idx / LW) * LW;
             const int gy = Y0 + i, gx = X0 + j;
             float v = 0.0f;
@@ -410,34 +285,41 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     if (jb.use_tma) {
         const bool ok = (tid != 0) || mbar_wait_bounded(smem_u32(bar), phase, kWaitLimitNs);
         if (__syncthreads_or(!ok)) {
-            if (tid == 0 && status) atomicOr(status, 1u);
+            if (tid == 0) {
+                if (status) atomicOr(status, 1u);
+                // the copies may still land: wait for them (bounded) before the CTA's shared
+                // memory is released
+                mbar_wait_bounded(smem_u32(bar), phase, kWaitLimitNs);
+            }
             return false;
+        }
+        if (ftma) {  // f as loaded by TMA: zero outside the image, like the plain loads' predicates
+            const S *fr = static_cast<const S *>(fwin) + c.ib * LW + c.j;
+#pragma unroll
+            for (int k = 0; k < kRY; ++k)
+                g[k] = __fmul2_rn(cf, make_float2(Store<S>::to_float(fr[k * LW]), Store<S>::to_float(fr[k * LW + 32])));
         }
         if constexpr (sizeof(S) != 4) {  // widen the staged 16-bit box, 8 elements per 16-byte access
             static_assert((LH * LW) % 8 == 0, "the staged box is a whole number of 16-byte chunks");
-            const uint4 *stage = reinterpret_cast<const uint4 *>(buf1 + BUF);
+            const uint4 *st4 = static_cast<const uint4 *>(stage);
             float4 *dst4 = reinterpret_cast<float4 *>(buf0);
-            for (int q = tid; q < LH * LW / 8; q += kTileThreadsV2) {
-                const uint4 raw = stage[q];
+            for (int q = tid; q < LH * LW / 8; q += NT) {
+                const uint4 raw = st4[q];
                 const float2 a = Store<S>::unpack2(raw.x), b = Store<S>::unpack2(raw.y);
                 const float2 c2 = Store<S>::unpack2(raw.z), d2 = Store<S>::unpack2(raw.w);
                 dst4[2 * q] = make_float4(a.x, a.y, b.x, b.y);
                 dst4[2 * q + 1] = make_float4(c2.x, c2.y, d2.x, d2.y);
             }
+            // the widened window is complete, and every thread has read f from buffer 1
             __syncthreads();
         }
     } else {
         __syncthreads();
     }
-    if (ftma) {  // f as loaded by TMA: zero outside the image, like the plain loads' predicates
-        const float *fr = fbuf + c.ib * G::P + c.j;
-#pragma unroll
-        for (int k = 0; k < kRY; ++k) g[k] = __fmul2_rn(cf, make_float2(fr[k * G::P], fr[k * G::P + 32]));
-    }
 
     // ---- REPLICATE: fill the ring just outside the image from its nearest in-image cell.
     if (BND == BND_REPLICATE && border) {
-        refresh_ring<S>(buf0, X0, Y0, h, w, tid);
+        refresh_ring<S, LH, NT>(buf0, X0, Y0, h, w, tid);
         __syncthreads();
     }
 
@@ -445,19 +327,20 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     // A warp whose cells all lie beyond the ring just outside the image (rows >= h + 1, or
     // columns >= w + 1: tiles that overhang the image's bottom or right edge) has nothing that
     // any in-image cell reads, so it skips the arithmetic (it still takes part in the barriers).
-    const bool idle = (Y0 + c.ib >= h + 1) | (c.gx - lane >= w + 1);
+    const int lane0 = c.gx - lane;
+    const bool idle = (Y0 + c.ib >= h + 1) | (lane0 >= w + 1);
 #pragma unroll 1
     for (int s = 0; s < T - 1; ++s) {
         const float *src = (s & 1) ? buf1 : buf0;
         float *dst = (s & 1) ? buf0 : buf1;
         if (!border) {
-            tile_step<WRITE_INTERIOR, S, BND>(src, dst, c, g);
+            tile_step<WRITE_INTERIOR, S, BND, NW>(src, dst, c, g);
             __syncthreads();
         } else {
-            if (!idle) tile_step<WRITE_BORDER, S, BND>(src, dst, c, g);
+            if (!idle) tile_step<WRITE_BORDER, S, BND, NW>(src, dst, c, g);
             __syncthreads();
             if (BND == BND_REPLICATE) {
-                refresh_ring<S>(dst, X0, Y0, h, w, tid);
+                refresh_ring<S, LH, NT>(dst, X0, Y0, h, w, tid);
                 __syncthreads();
             }
         }
@@ -465,21 +348,22 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     if (idle) return true;  // none of its cells is an output cell inside the image
     int64_t ldo;
     S *out = out_of(&ldo);
-    tile_step<WRITE_GLOBAL, S, BND>(((T - 1) & 1) ? buf1 : buf0, nullptr, c, g,
-                                    out + (int64_t)(Y0 + c.ib) * ldo + c.gx, ldo);
+    tile_step<WRITE_GLOBAL, S, BND, NW>(((T - 1) & 1) ? buf1 : buf0, nullptr, c, g,
+                                        out + (int64_t)(Y0 + c.ib) * ldo + c.gx, ldo);
     return true;
 }
 
-template <int T, typename S, int BND, bool BATCH>
-__global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
-    tile_v2_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap fmap,
-                   const TileV2Params p) {
+template <int T, typename S, int BND, bool BATCH, int NW>
+__global__ void __launch_bounds__(32 * NW, 32 / NW)
+    tile_flow_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap fmap,
+                     const TileParams p) {
+    using G = TGeom<S, NW>;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     // 128-byte aligned start of the buffers, formed as an offset into the __shared__ array (not
     // through an integer cast) so that every access below stays a shared-memory access
     float *buf0 = reinterpret_cast<float *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
-    float *buf1 = buf0 + Geom<S>::BUF;
+    float *buf1 = buf0 + G::BUF;
 
     // ---- this CTA's job: image, buffers, coefficients and output tile
     TileJob<S> jb;
@@ -522,7 +406,7 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
     if (jb.use_tma && threadIdx.x == 0) mbar_init(smem_u32(&bar), 1);
     // the output pointer is looked up again after the steps (kernel parameters, or the image
     // descriptor in L1) rather than kept in registers through them
-    tile_job<T, S, BND>(jb, p.owt, p.oht, p.status, buf0, buf1, &bar, 0u, [&](int64_t *ldo) -> S * {
+    tile_job<T, S, BND, NW>(jb, p.owt, p.oht, p.status, buf0, buf1, &bar, 0u, [&](int64_t *ldo) -> S * {
         if (BATCH) {
             const BatchImage &im = p.images[p.tiles[blockIdx.x].x];
             *ldo = im.ld;
@@ -533,13 +417,12 @@ __global__ void __launch_bounds__(kTileThreadsV2, WMC_TILE_MIN_BLOCKS)
     });
 }
 
-template <int T, typename S, int BND, bool BATCH>
-cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, int64_t nblocks,
-                             cudaStream_t st) {
-    using G = Geom<S>;
+template <int T, typename S, int BND, bool BATCH, int NW>
+cudaError_t launch_tile_t(const CUtensorMap *map, TileParams p, int64_t nblocks, cudaStream_t st) {
+    using G = TGeom<S, NW>;
     if (!BATCH) {
-        p.owt = Out<S, T>::OW;
-        p.oht = Out<S, T>::OH;
+        p.owt = kCW + 2 - 2 * T;
+        p.oht = G::CH + 2 - 2 * T;
         const int64_t ntx = (p.w + p.owt - 1) / p.owt, nty = (p.h + p.oht - 1) / p.oht;
         nblocks = ntx * nty;
         p.ntx = (int32_t)ntx;
@@ -554,7 +437,7 @@ cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, int64_t nbl
     if (e != cudaSuccess) return e;
     const uint64_t bit = 1ull << (dev & 63);
     if (!(attr_set.load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(tile_v2_kernel<T, S, BND, BATCH>,
+        e = cudaFuncSetAttribute(tile_flow_kernel<T, S, BND, BATCH, NW>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(bit, std::memory_order_release);
@@ -567,12 +450,12 @@ cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, int64_t nbl
         p.f_tma = 0;
     }
     if (!p.pdl) {
-        tile_v2_kernel<T, S, BND, BATCH><<<(unsigned)nblocks, kTileThreadsV2, G::SMEM, st>>>(map[0], map[1], p);
+        tile_flow_kernel<T, S, BND, BATCH, NW><<<(unsigned)nblocks, G::THREADS, G::SMEM, st>>>(map[0], map[1], p);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)nblocks);
-    cfg.blockDim = dim3(kTileThreadsV2);
+    cfg.blockDim = dim3(G::THREADS);
     cfg.dynamicSmemBytes = G::SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -580,17 +463,19 @@ cudaError_t launch_tile_v2_t(const CUtensorMap *map, TileV2Params p, int64_t nbl
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tile_v2_kernel<T, S, BND, BATCH>, map[0], map[1], p);
+    return cudaLaunchKernelEx(&cfg, tile_flow_kernel<T, S, BND, BATCH, NW>, map[0], map[1], p);
 }
 
-template <typename S, int BND>
-cudaError_t launch_tile_v2_steps(int steps, const CUtensorMap *map, const TileV2Params &p,
+// steps = T (1..8), tile = 1 or 2 (tile_warps); batch_tiles >= 0: a batch launch over that many
+// tiles of the plan's table, < 0: a single-image launch
+template <typename S, int BND, int NW>
+cudaError_t launch_tile_steps_nw(int steps, const CUtensorMap *map, const TileParams &p,
                                  int64_t batch_tiles, cudaStream_t st) {
     const bool b = batch_tiles >= 0;
 #define WMC_TILE_CASE(T)                                                                        \
     case T:                                                                                     \
-        return b ? launch_tile_v2_t<T, S, BND, true>(map, p, batch_tiles, st)                   \
-                 : launch_tile_v2_t<T, S, BND, false>(map, p, 0, st);
+        return b ? launch_tile_t<T, S, BND, true, NW>(map, p, batch_tiles, st)                  \
+                 : launch_tile_t<T, S, BND, false, NW>(map, p, 0, st);
     switch (steps) {
         WMC_TILE_CASE(1)
         WMC_TILE_CASE(2)

@@ -58,6 +58,8 @@ SIGNATURES = {
     "wmc_denoise_status": (_i32, [_vp, _vp]),
     "wmc_denoise_noalloc_max_bytes": (_sz, []),
     "wmc_denoise_noalloc": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp]),
+    "wmc_denoise_noalloc_status": (_i32, [_vp]),
+    "wmc_selftest_status_timeout": (_i32, [_i32, _i64, _vp]),
     "wmc_denoise_host_workspace_size": (_sz, [_i32, _i32, _i64, _i32]),
     "wmc_denoise_host": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp, _sz,
                                 _vp]),
@@ -71,6 +73,9 @@ SIGNATURES = {
     "wmc_batch_autotune_workspace_size": (_sz, [ctypes.POINTER(Image), _i32, _i32]),
     "wmc_batch_autotune": (_i32, [ctypes.POINTER(Image), _i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32), _i32,
                                   _i32, _vp, _sz, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_float), _vp]),
+    "wmc_batch_autotune_configs": (_i32, [ctypes.POINTER(Image), _i32, _i32, _i32, ctypes.POINTER(Config), _i32,
+                                          _i32, _vp, _sz, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_float),
+                                          _vp]),
     "wmc_denoise_l1_workspace_size": (_sz, [_i32, _i32, _i64]),
     "wmc_denoise_l1": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i64, _f32, _f32, _f32, _i32, _i32, _vp, _sz,
                               _vp]),
@@ -79,10 +84,15 @@ SIGNATURES = {
                                     _vp]),
     "wmc_unrolled_backward": (_i32, [_vp, _vp, _f32, _i32, _i32, _i32, _i32, _i32, _i64, _i32, _vp, _vp, _vp,
                                      _vp, _sz, _vp]),
+    "wmc_backward_workspace_size": (_sz, [_i32, _i32, _i32, _i64, _i32, _i32]),
+    "wmc_backward": (_i32, [_vp, _vp, _f32, _i32, _i32, _i32, _i32, _i32, _i64, _i32, _vp, _vp, _vp, _vp, _sz,
+                            _vp]),
     "wmc_energy_grad": (_i32, [_vp, _vp, _i32, _i32, _i64, _i32, _vp]),
     "wmc_shard_lpt": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     "wmc_selftest_wait_timeout": (_i32, [_vp, _i64, _vp]),
     "wmc_eval_status": (_i32, [_vp]),
+    "wmc_probe_fma_threads": (_i32, []),
+    "wmc_probe_fma": (_i32, [_vp, _i32, _i32, _vp]),
     "wmc_status_string": (ctypes.c_char_p, [_i32]),
     "wmc_last_error": (ctypes.c_char_p, []),
     "wmc_version": (_i32, []),
@@ -201,10 +211,12 @@ def default_step(lam: float) -> float:
 
 def denoise(f: torch.Tensor | None, lam: float = 1.0, step: float | None = None, iters: int = 100,
             boundary: str = "replicate", u0: torch.Tensor | None = None, out: torch.Tensor | None = None,
-            steps_per_launch: int = 0, workspace: torch.Tensor | None = None) -> torch.Tensor:
+            steps_per_launch: int = 0, workspace: torch.Tensor | None = None, tile: int = 0) -> torch.Tensor:
     """`iters` Jacobi steps of U <- U + step*(lam*H^w(U) - (U - f)) (Sec. V-B, A = I).
 
     f = None gives the mean-curvature flow U <- U + step*lam*H^w(U) (Eq. MCF) from u0.
+    steps_per_launch and tile pick the kernel configuration (0: defaults; tile 1: 128 x 64
+    regions, 2: 128 x 32); the result does not depend on them.
     """
     ref = f if f is not None else u0
     if ref is None:
@@ -228,7 +240,7 @@ def denoise(f: torch.Tensor | None, lam: float = 1.0, step: float | None = None,
     need = lib.wmc_denoise_workspace_size(h, w, ld, dt)
     if workspace is None:
         workspace = _workspace(need, ref.device)
-    cfg = Config(int(steps_per_launch), 0)
+    cfg = Config(int(steps_per_launch), int(tile))
     _check(lib.wmc_denoise_ex(pf, pu0, po, h, w, ld, dt, float(lam), float(step), int(iters),
                               BOUNDARY[boundary], ctypes.byref(cfg), workspace.data_ptr(),
                               workspace.numel(), _stream(ref.device)), "wmc_denoise")
@@ -278,6 +290,18 @@ def selftest_wait_timeout(workspace: torch.Tensor, limit_ns: int = 10_000_000):
            "wmc_selftest_wait_timeout")
 
 
+SELFTEST_TARGETS = {"eval": 0, "noalloc": 1}
+
+
+def selftest_status_timeout(target: str, limit_ns: int = 10_000_000, device=None):
+    """Make one bounded device wait run out on purpose against a status word the library holds
+    per device ("eval": the word eval_status reads; "noalloc": the word at the start of the fixed
+    scratch of wmc_denoise_noalloc)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    _check(load().wmc_selftest_status_timeout(SELFTEST_TARGETS[target], int(limit_ns), _stream(dev)),
+           "wmc_selftest_status_timeout")
+
+
 def denoise_host_workspace_size(h: int, w: int, dtype=torch.float32) -> int:
     return load().wmc_denoise_host_workspace_size(h, w, w, DTYPES[dtype])
 
@@ -314,7 +338,7 @@ class Batch:
     """
 
     def __init__(self, fs, lams, steps=None, outs=None, boundary: str = "replicate",
-                 steps_per_launch: int = 0):
+                 steps_per_launch: int = 0, tile: int = 0):
         if not fs:
             raise ValueError("empty batch")
         dt = fs[0].dtype
@@ -333,7 +357,7 @@ class Batch:
                 raise ValueError(f"image {i}: f and out must share shape, pitch and dtype")
             imgs[i] = Image(pf, pu, h, w, ld, float(l), float(st))
         lib = load()
-        self.cfg = Config(int(steps_per_launch), 0)
+        self.cfg = Config(int(steps_per_launch), int(tile))
         self.dtype = DTYPES[dt]
         size = lib.wmc_batch_workspace_size(imgs, n, self.dtype, ctypes.byref(self.cfg))
         if size == 0:
@@ -354,10 +378,11 @@ class Batch:
         check_status(self.workspace)
 
 
-def batch_autotune(fs, lams, steps=None, outs=None, boundary: str = "replicate", candidates=(2, 3, 4, 5, 6, 8),
+def batch_autotune(fs, lams, steps=None, outs=None, boundary: str = "replicate", candidates=None,
                    trial_iters: int = 24):
-    """Time the batch at each candidate steps-per-launch (wmc_batch_autotune); returns
-    (best steps per launch, {candidate: ms per iteration}).  Writes the outputs."""
+    """Time the batch at each candidate configuration (wmc_batch_autotune_configs): candidates are
+    (steps_per_launch, tile) pairs, None = both tile shapes x steps {2, 3, 4, 5, 6, 8}.  Returns
+    ((best steps per launch, best tile), {(steps, tile): ms per iteration}).  Writes the outputs."""
     if not fs:
         raise ValueError("empty batch")
     dt = fs[0].dtype
@@ -378,19 +403,21 @@ def batch_autotune(fs, lams, steps=None, outs=None, boundary: str = "replicate",
     if size == 0:
         raise WMCError(1, "wmc_batch_autotune_workspace_size", "invalid batch")
     ws = _workspace(size, fs[0].device)
-    cand = (ctypes.c_int32 * len(candidates))(*candidates)
+    if candidates is None:
+        candidates = [(T, tile) for tile in (1, 2) for T in (2, 3, 4, 5, 6, 8)]
+    cand = (Config * len(candidates))(*[Config(int(T), int(tile)) for T, tile in candidates])
     times = (ctypes.c_float * len(candidates))()
     best = Config(0, 0)
-    _check(lib.wmc_batch_autotune(imgs, n, DTYPES[dt], BOUNDARY[boundary], cand, len(candidates), int(trial_iters),
-                                  ws.data_ptr(), ws.numel(), ctypes.byref(best), times, _stream(fs[0].device)),
-           "wmc_batch_autotune")
-    return best.steps_per_launch, {c: float(t) for c, t in zip(candidates, times)}
+    _check(lib.wmc_batch_autotune_configs(imgs, n, DTYPES[dt], BOUNDARY[boundary], cand, len(candidates),
+                                          int(trial_iters), ws.data_ptr(), ws.numel(), ctypes.byref(best), times,
+                                          _stream(fs[0].device)), "wmc_batch_autotune_configs")
+    return (best.steps_per_launch, best.tile), {tuple(c): float(t) for c, t in zip(candidates, times)}
 
 
 def denoise_batched(fs, lams, steps=None, iters: int = 100, boundary: str = "replicate", outs=None,
-                    steps_per_launch: int = 0):
+                    steps_per_launch: int = 0, tile: int = 0):
     """Plan and run one batch; returns the output tensors."""
-    return Batch(fs, lams, steps, outs, boundary, steps_per_launch).run(iters)
+    return Batch(fs, lams, steps, outs, boundary, steps_per_launch, tile).run(iters)
 
 
 def denoise_l1(f: torch.Tensor, lam: float = 1.0, step: float = 0.1, alpha: float = 0.1,
@@ -475,6 +502,27 @@ def unrolled_backward(f: torch.Tensor, lam: torch.Tensor, step: float, K: int, g
     return grad_f, grad_lam
 
 
+def backward(f: torch.Tensor, lam: torch.Tensor, step: float, K: int, grad_u: torch.Tensor, ckpt_every: int = 7,
+             boundary: str = "replicate", workspace: torch.Tensor | None = None):
+    """(dL/df, dL/dlambda) of K unrolled denoising steps from dL/dU^K in one call (wmc_backward:
+    the forward sweep that stores the checkpoints, then the reverse sweep)."""
+    pf, n, h, w, ld = _stack(f, "f")
+    if lam.dtype != torch.float32 or lam.numel() != n or not lam.is_cuda or not lam.is_contiguous():
+        raise ValueError("lam must be a contiguous float32 CUDA tensor with one value per image")
+    pg, n2, h2, w2, ld2 = _stack(grad_u, "grad_u")
+    if (n2, h2, w2, ld2) != (n, h, w, ld):
+        raise ValueError("grad_u must match f in shape and pitch")
+    lib = load()
+    if workspace is None:
+        workspace = _workspace(lib.wmc_backward_workspace_size(n, h, w, ld, K, ckpt_every), f.device)
+    grad_f = torch.empty_strided(f.shape, f.stride(), dtype=f.dtype, device=f.device)
+    grad_lam = torch.empty(n, dtype=torch.float32, device=f.device)
+    _check(lib.wmc_backward(pf, lam.data_ptr(), float(step), int(K), int(ckpt_every), n, h, w, ld,
+                            BOUNDARY[boundary], pg, grad_f.data_ptr(), grad_lam.data_ptr(), workspace.data_ptr(),
+                            workspace.numel(), _stream(f.device)), "wmc_backward")
+    return grad_f, grad_lam
+
+
 class UnrolledDenoise(torch.autograd.Function):
     """Autograd node of K unrolled denoising steps: apply(f, lam, step, K, ckpt_every, boundary).
 
@@ -538,6 +586,30 @@ def shard_lpt(costs, world: int):
     _check(load().wmc_shard_lpt(ctypes.cast(c, _vp), n, int(world), ctypes.cast(owner, _vp),
                                 ctypes.cast(loads, _vp)), "wmc_shard_lpt")
     return [int(owner[i]) for i in range(n)], [int(loads[r]) for r in range(int(world))]
+
+
+def measure_fma_rate(device=None, iters: int = 4096, reps: int = 5) -> float:
+    """FP32 FMA lane-operations per second of the current GPU (wmc_probe_fma; an FMA counts once),
+    best of `reps` timed launches of 8 CTAs per SM."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    lib = load()
+    blocks = 8 * torch.cuda.get_device_properties(dev).multi_processor_count
+    threads = lib.wmc_probe_fma_threads()
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    st = _stream(dev)
+    _check(lib.wmc_probe_fma(out.data_ptr(), blocks, iters, st), "wmc_probe_fma")  # warm-up
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _check(lib.wmc_probe_fma(out.data_ptr(), blocks, iters, st), "wmc_probe_fma")
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    if not bool(torch.isfinite(out).all()):
+        raise WMCError(4, "wmc_probe_fma", "non-finite probe output")
+    return blocks * threads * iters * 16 / (best * 1e-3)
 
 
 def psnr(sse: float, n: int, peak: float = 1.0) -> float:

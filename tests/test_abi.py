@@ -118,7 +118,10 @@ def test_denoise_config_validation(lib):
     cfg = wmc.Config(9, 0)
     assert lib.wmc_denoise_ex(A, None, B, 4, 4, 4, 0, 1.0, 0.25, 3, 0, ctypes.byref(cfg), 0x30000000, 4096,
                               None) == INVALID
-    cfg = wmc.Config(2, 3)
+    cfg = wmc.Config(2, 3)  # tile shapes are 0 (default), 1 and 2
+    assert lib.wmc_denoise_ex(A, None, B, 4, 4, 4, 0, 1.0, 0.25, 3, 0, ctypes.byref(cfg), 0x30000000, 4096,
+                              None) == INVALID
+    cfg = wmc.Config(2, -1)
     assert lib.wmc_denoise_ex(A, None, B, 4, 4, 4, 0, 1.0, 0.25, 3, 0, ctypes.byref(cfg), 0x30000000, 4096,
                               None) == INVALID
 
@@ -155,6 +158,14 @@ def test_batch_validation(lib):
     need = lib.wmc_batch_workspace_size(imgs, 1, 0, ctypes.byref(cfg))
     assert need > 0 and need % 256 == 0
     assert lib.wmc_batch_workspace_size(_images([(A, B, 8, 8, 7, 1.0, 0.25)]), 1, 0, None) == 0
+    # the 128 x 32 tile shape needs more tiles (a longer tile table) than the 128 x 64 one
+    tall = _images([(A, B, 1000, 300, 300, 1.0, 0.25)])
+    assert (lib.wmc_batch_workspace_size(tall, 1, 0, ctypes.byref(wmc.Config(4, 2))) >
+            lib.wmc_batch_workspace_size(tall, 1, 0, ctypes.byref(wmc.Config(4, 1))) ==
+            lib.wmc_batch_workspace_size(tall, 1, 0, ctypes.byref(wmc.Config(4, 0))))
+    assert lib.wmc_batch_workspace_size(imgs, 1, 0, ctypes.byref(wmc.Config(4, 3))) == 0
+    assert lib.wmc_batch_plan(imgs, 1, 0, 0, ctypes.byref(wmc.Config(4, 3)), 0x30000000, 1 << 20,
+                              ctypes.byref(plan), None) == INVALID
     assert lib.wmc_batch_run(ctypes.byref(wmc.BatchPlan()), 5, None) == INVALID  # not planned
 
 
@@ -205,6 +216,32 @@ def test_selftest_wait_validation(lib):
     assert lib.wmc_selftest_wait_timeout(ws, 2_000_000_000, None) == INVALID
 
 
+def test_selftest_status_validation(lib):
+    assert lib.wmc_selftest_status_timeout(0, 0, None) == INVALID
+    assert lib.wmc_selftest_status_timeout(1, 2_000_000_000, None) == INVALID
+    assert lib.wmc_selftest_status_timeout(2, 1000, None) == INVALID  # unknown target
+    assert lib.wmc_selftest_status_timeout(-1, 1000, None) == INVALID
+
+
+def test_backward_validation(lib):
+    f = ctypes.c_void_p(0x100000)
+    lam = ctypes.c_void_p(0x200000)
+    g = ctypes.c_void_p(0x300000)
+    gf = ctypes.c_void_p(0x400000)
+    ws = ctypes.c_void_p(0x10000000)
+    big = 1 << 40
+    need = lib.wmc_backward_workspace_size(2, 8, 8, 8, 9, 3)
+    assert need > lib.wmc_unrolled_workspace_size(2, 8, 8, 8, 9, 3) and need % 256 == 0
+    assert lib.wmc_backward_workspace_size(0, 8, 8, 8, 9, 3) == 0
+    bwd = lib.wmc_backward
+    assert bwd(f, lam, 0.25, 4, 0, 1, 8, 8, 8, 0, g, gf, lam, ws, big, None) == INVALID  # ckpt_every
+    assert bwd(f, lam, 0.0, 4, 2, 1, 8, 8, 8, 0, g, gf, lam, ws, big, None) == INVALID  # step
+    assert bwd(None, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, g, gf, lam, ws, big, None) == INVALID
+    assert bwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, g, gf, lam, ws, 16, None) == WORKSPACE
+    assert bwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, g, gf, lam, ctypes.c_void_p(0x10000010), big, None) == WORKSPACE
+    assert bwd(f, lam, 0.25, 4, 2, 1, 8, 8, 8, 0, g, gf, lam, ctypes.c_void_p(0x100000 - 256), big, None) == ALIAS
+
+
 def test_l1_validation(lib):
     f = ctypes.c_void_p(0x100000)
     u = ctypes.c_void_p(0x300000)
@@ -241,6 +278,15 @@ def test_batch_autotune_validation(lib):
     assert lib.wmc_batch_autotune(imgs, 1, 0, 0, good, 0, 8, ws, need, ctypes.byref(best), None, None) == INVALID
     assert lib.wmc_batch_autotune(imgs, 1, 0, 0, good, 1, 0, ws, need, ctypes.byref(best), None, None) == INVALID
     assert lib.wmc_batch_autotune(imgs, 1, 0, 0, good, 1, 8, ws, need, None, None, None) == INVALID
+    cfgs = (wmc.Config * 2)(wmc.Config(4, 1), wmc.Config(4, 3))
+    tune = lib.wmc_batch_autotune_configs
+    assert tune(imgs, 1, 0, 0, cfgs, 2, 8, ws, need, ctypes.byref(best), None, None) == INVALID  # tile 3
+    cfgs = (wmc.Config * 1)(wmc.Config(0, 1))
+    assert tune(imgs, 1, 0, 0, cfgs, 1, 8, ws, need, ctypes.byref(best), None, None) == INVALID  # 0 steps
+    cfgs = (wmc.Config * 1)(wmc.Config(4, 2))
+    assert tune(imgs, 1, 0, 0, cfgs, 0, 8, ws, need, ctypes.byref(best), None, None) == INVALID
+    assert tune(imgs, 1, 0, 0, cfgs, 1, 0, ws, need, ctypes.byref(best), None, None) == INVALID
+    assert tune(imgs, 1, 0, 0, cfgs, 1, 8, ws, need, None, None, None) == INVALID
 
 
 def test_unrolled_backward_workspace_alias(lib):

@@ -258,3 +258,17 @@ def test_energy_grad_pitched_rows():
     got = wmc().energy_grad(base[:, :50]).cpu().double().numpy()
     dense = wmc().energy_grad(torch.from_numpy(u_np).to(DEV)).cpu().double().numpy()
     assert np.array_equal(got, dense)
+
+
+@pytest.mark.parametrize("bnd", ["replicate", "zero"])
+def test_one_call_backward_equals_the_two_unrolled_calls(bnd):
+    """wmc_backward (forward sweep with checkpoints, then the reverse sweep, in one call) gives the
+    bits of wmc_unrolled_forward followed by wmc_unrolled_backward."""
+    h, w, step, K, c = 45, 131, 0.2, 11, 4
+    f = torch.from_numpy(np.stack([image(h, w, seed=s) for s in (31, 32, 33)])).to(DEV)
+    lam = torch.tensor([0.6, 1.1, 1.9], device=DEV)
+    g = torch.from_numpy(np.random.default_rng(12).normal(size=(3, h, w)).astype(np.float32)).to(DEV)
+    _, ws = wmc().unrolled_forward(f, lam, step, K, c, bnd)
+    gf, gl = wmc().unrolled_backward(f, lam, step, K, g, ws, c, bnd)
+    gf1, gl1 = wmc().backward(f, lam, step, K, g, c, bnd)
+    assert torch.equal(gf1, gf) and torch.equal(gl1, gl)

@@ -29,22 +29,26 @@ def batch_inputs(dtype=torch.float32, shapes=SHAPES, seed=0):
     return fs, lams, steps
 
 
+@pytest.mark.parametrize("tile", [1, 2])
 @pytest.mark.parametrize("T", [1, 2, 3, 5, 8])
-def test_batch_matches_single_images(T):
+def test_batch_matches_single_images(T, tile):
+    """Both tile shapes (128 x 64 and 128 x 32 regions), every image against itself run alone with
+    one step per launch."""
     fs, lams, steps = batch_inputs()
-    outs = wmc().denoise_batched(fs, lams, steps, iters=7, steps_per_launch=T)
+    outs = wmc().denoise_batched(fs, lams, steps, iters=7, steps_per_launch=T, tile=tile)
     for f, l, st, o in zip(fs, lams, steps, outs):
-        ref = wmc().denoise(f, l, st, 7, steps_per_launch=T)
-        assert torch.equal(o, ref), (f.shape, T)
+        ref = wmc().denoise(f, l, st, 7, steps_per_launch=1)
+        assert torch.equal(o, ref), (f.shape, T, tile)
 
 
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
 @pytest.mark.parametrize("bnd", ["replicate", "zero"])
 def test_batch_reduced_storage_and_zero_boundary(dtype, bnd):
     fs, lams, steps = batch_inputs(dtype, seed=1)
-    outs = wmc().denoise_batched(fs, lams, steps, iters=10, boundary=bnd, steps_per_launch=4)
-    for f, l, st, o in zip(fs, lams, steps, outs):
-        assert torch.equal(o, wmc().denoise(f, l, st, 10, bnd, steps_per_launch=4)), f.shape
+    for tile in (1, 2):
+        outs = wmc().denoise_batched(fs, lams, steps, iters=10, boundary=bnd, steps_per_launch=4, tile=tile)
+        for f, l, st, o in zip(fs, lams, steps, outs):
+            assert torch.equal(o, wmc().denoise(f, l, st, 10, bnd, steps_per_launch=1)), (f.shape, tile)
 
 
 def test_batch_zero_iterations_copies():
@@ -99,10 +103,16 @@ def test_batch_alias_rejected():
 
 
 def test_autotune_picks_a_candidate_and_the_plan_matches_single_images():
+    """The autotuner times (steps per launch, tile shape) pairs on the caller's batch and returns
+    the fastest; a plan with that configuration still gives every image's own bits."""
     fs, lams, steps = batch_inputs(seed=4)
-    T, times = wmc().batch_autotune(fs, lams, steps, candidates=(2, 4, 8), trial_iters=8)
-    assert T in (2, 4, 8)
-    assert all(t > 0 for t in times.values()) and times[T] == min(times.values())
-    outs = wmc().denoise_batched(fs, lams, steps, iters=9, steps_per_launch=T)
+    cands = [(2, 1), (4, 1), (8, 1), (4, 2), (6, 2)]
+    best, times = wmc().batch_autotune(fs, lams, steps, candidates=cands, trial_iters=8)
+    assert best in cands
+    assert all(t > 0 for t in times.values()) and times[best] == min(times.values())
+    T, tile = best
+    outs = wmc().denoise_batched(fs, lams, steps, iters=9, steps_per_launch=T, tile=tile)
     for f, l, st, o in zip(fs, lams, steps, outs):
-        assert torch.equal(o, wmc().denoise(f, l, st, 9, steps_per_launch=T))
+        assert torch.equal(o, wmc().denoise(f, l, st, 9, steps_per_launch=T, tile=tile))
+    best, times = wmc().batch_autotune(fs, lams, steps, trial_iters=4)  # every default candidate
+    assert len(times) == 12 and best in times

@@ -188,9 +188,10 @@ def test_steps_per_launch_bitwise_invariant(bnd):
     (every configuration performs the same FP32 operations per pixel)."""
     f = to_gpu(synth.make_image(150, 173, seed=15, sigma=0.1))
     ref = wmc().denoise(f, 1.0, 0.25, 17, bnd, steps_per_launch=1)
-    for T in range(2, 9):
-        got = wmc().denoise(f, 1.0, 0.25, 17, bnd, steps_per_launch=T)
-        assert torch.equal(got, ref), T
+    for tile in (1, 2):
+        for T in range(2, 9):
+            got = wmc().denoise(f, 1.0, 0.25, 17, bnd, steps_per_launch=T, tile=tile)
+            assert torch.equal(got, ref), (T, tile)
 
 
 def test_pr1_trajectory_vs_oracle():
@@ -275,15 +276,17 @@ def test_energy_parity():
                                       ((33, 218), None), ((19, 131), 133)])
 @pytest.mark.parametrize("bnd", ["replicate", "zero"])
 def test_energy_layouts(shape, ld, bnd):
-    """FP32 rows that are 16-byte aligned take the 4-cells-per-lane energy kernel, the rest the
-    pair layout; ragged widths and heights, NaN-filled pitch padding (never read), and the
-    optional f / clean terms must all match the oracle and repeat bitwise."""
+    """FP32 rows that are 16-byte aligned take the TMA-fed energy kernel, the rest the streaming
+    kernels; ragged widths and heights, NaN-filled pitch padding (never read), and every
+    combination of the optional f / clean terms (each a separate kernel instance with its own
+    box offsets) must match the oracle and repeat bitwise."""
     f, clean = synth.make_image(*shape, seed=23, sigma=0.1, return_clean=True)
     fg, cg = to_gpu(f, ld=ld), to_gpu(clean, ld=ld)
     ug = wmc().denoise(fg, 1.0, 0.25, 3, boundary=bnd)
     U = host(ug)
     for args, want in [((ug, fg, cg), oracle.energies(U, host(fg), host(cg), boundary=bnd)),
                        ((ug, fg, None), oracle.energies(U, host(fg), None, boundary=bnd)),
+                       ((ug, None, cg), oracle.energies(U, None, host(cg), boundary=bnd)),
                        ((ug, None, None), oracle.energies(U, None, None, boundary=bnd))]:
         e = wmc().energy(*args, boundary=bnd).cpu().numpy()
         np.testing.assert_allclose(e, want, rtol=2e-6, atol=1e-300)
@@ -368,6 +371,23 @@ def test_timed_out_wait_is_reported_and_the_context_stays_usable():
     assert torch.equal(again, ref)
 
 
+def test_eval_timeout_is_reported_once_and_cleared():
+    """The evaluation status word (set when a bounded TMA wait of the persistent evaluation
+    kernel runs out) is made to read WMC_ERR_TIMEOUT by the self-test's wait that nothing
+    completes (10 ms); wmc_eval_status reports it once and clears it, and evaluation still gives
+    the exact result afterwards."""
+    u = to_gpu(synth.make_image(130, 260, seed=27))
+    ref = wmc().eval(u)
+    wmc().eval_status()
+    wmc().selftest_status_timeout("eval", 10_000_000)
+    with pytest.raises(wmc().WMCError) as err:
+        wmc().eval_status()
+    assert err.value.status == 5  # WMC_ERR_TIMEOUT
+    wmc().eval_status()  # cleared by the previous read
+    assert torch.equal(wmc().eval(u), ref)
+    wmc().eval_status()
+
+
 def test_mcf_steps_per_launch_bitwise():
     u0 = to_gpu(synth.make_image(200, 180, seed=24))
     ref = wmc().mcf(u0, step=0.3, iters=10, steps_per_launch=1)
@@ -398,15 +418,19 @@ def test_denoise_graph_capture_replay():
 
 
 @pytest.mark.parametrize("bnd", ["replicate", "zero"])
-@pytest.mark.parametrize("shape", [(59, 117), (117, 233), (175, 65), (3, 130), (130, 3), (61, 61)])
+@pytest.mark.parametrize("shape", [(59, 123), (117, 245), (51, 115), (27, 123), (53, 245), (175, 65),
+                                   (3, 130), (130, 3), (61, 61)])
 def test_overhanging_tiles_bitwise_invariant(bnd, shape):
-    """Images one cell past a whole number of output tiles (T = 4: 116 x 58, T = 8: 108 x 50),
-    where the last tile row or column overhangs the image and its outer warps skip work: every
-    T still gives the one-step-per-launch bits."""
+    """Images one cell past a whole number of output tiles (128 x 64 regions: 122 x 58 at T = 4,
+    114 x 50 at T = 8; 128 x 32 regions: 122 x 26 at T = 4), where the last tile row or column
+    overhangs the image and its outer warps skip work: every T and tile shape still gives the
+    one-step-per-launch bits."""
     f = to_gpu(synth.make_image(*shape, seed=sum(shape), sigma=0.1))
     ref = wmc().denoise(f, 1.0, 0.25, 11, bnd, steps_per_launch=1)
-    for T in (2, 4, 5, 8):
-        assert torch.equal(wmc().denoise(f, 1.0, 0.25, 11, bnd, steps_per_launch=T), ref), T
+    for tile in (1, 2):
+        for T in (2, 4, 5, 8):
+            assert torch.equal(wmc().denoise(f, 1.0, 0.25, 11, bnd, steps_per_launch=T, tile=tile), ref), (T, tile)
     bf = f.to(torch.bfloat16)
     ref16 = wmc().denoise(bf, 1.0, 0.25, 11, bnd, steps_per_launch=1)
-    assert torch.equal(wmc().denoise(bf, 1.0, 0.25, 11, bnd, steps_per_launch=4), ref16)
+    for tile in (1, 2):
+        assert torch.equal(wmc().denoise(bf, 1.0, 0.25, 11, bnd, steps_per_launch=4, tile=tile), ref16)

@@ -728,3 +728,28 @@ def test_harmonic_quadratics_reduce_to_their_tangent_plane(which):
         np.testing.assert_allclose(np.abs(hw[inner]), mag, rtol=0, atol=1e-14)
         zero = ((a == 0) | (b == 0) | (np.abs(a) == np.abs(b)))[inner]
         assert np.all(hw[inner][zero] == 0) and np.all(hw[inner][~zero] != 0)
+
+
+# ------------------------------------------------------------------ tie events of Eq. act
+def test_tie_count_on_ramps_impulses_and_steps():
+    """Worked by hand from the printed kernels.  On the ramp x + 2y every interior pixel's
+    candidates are +-1/2, +-1, +-2/3, +-4/3 (the closed form above with a = 1, b = 2): the least
+    magnitude 1/2 comes with both signs, an opposite-sign tie; the border rows and columns under
+    REPLICATE are not (e.g. 1/4 alone at the top-left corner, or a zero).  An impulse has no
+    tie anywhere (every candidate at the centre is -1, and around it the least magnitude is a
+    single 0), nor has a straight step edge (least magnitude 0)."""
+    y, x = np.mgrid[0:9, 0:11].astype(np.float64)
+    ramp = x + 2 * y
+    _, cand, _ = oracle.wmc_eval(ramp, "replicate", candidates=True)
+    mags = np.abs(cand)
+    in_set = mags <= mags.min(-1, keepdims=True)
+    both = (in_set & (cand > 0)).any(-1) & (in_set & (cand < 0)).any(-1)
+    assert both[1:-1, 1:-1].all()
+    assert oracle.count_ties(ramp, 0.0) == int(both.sum()) >= 7 * 9
+    imp = np.zeros((7, 7))
+    imp[3, 3] = 1.0
+    assert oracle.count_ties(imp, 0.0) == 0
+    assert oracle.count_ties((x >= 5) * 1.0, 0.0) == 0
+    # the band widens with tau: candidates 1/2 and -2/3 of the ramp are within 1/6
+    assert oracle.count_ties(ramp, 0.2) >= oracle.count_ties(ramp, 0.0)
+    assert oracle.count_ties(-ramp, 0.0) == oracle.count_ties(ramp, 0.0)
