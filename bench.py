@@ -8,7 +8,15 @@ energies (wmc_energy).  value = H*W*500 / step time (the evaluation pass and the
 are inside the timed step but not counted as work).  L2 is flushed before every timed step,
 outside the events (a 256 MiB write, then a 256 MiB read of another buffer, which leaves L2 clean).
 
+The same JSON line carries, under "secondary", compact measurements of the other workloads
+(each a few seconds of GPU time; --no-secondary skips them): the 4096^2 sigma 0.1 image, the
+256^2 PR1 run (plain launches and a CUDA graph replay), the 16384^2 FP32/BF16/FP16 rates, the
+512-image batch against looping the single-image path, and the 32 x 512^2 unrolled
+forward + backward.  The CPU-baseline leg times the FP64 oracle on the host cores and compares
+its result with the GPU's on the same crop ("parity").
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload scale|pr1|precision|batch|diff|l1|fd]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded crop of the same
 workload.  Under torchrun (N > 1) every rank denoises its own image (independent replicas:
@@ -46,12 +54,12 @@ BYTES_PER_PX_LAUNCH = 12  # read U, read f, write U (FP32): algorithmic bytes of
 # kernels compute it (L and the four odd parts: 20, |L|-|a_j|: 4, sign guard: 1, update: 2);
 # compare/select/sign logic (7 more) runs on the separate ALU pipe and is not counted.
 FMA_OPS_PER_PX_ITER = 27
-SMS, FP32_LANES_PER_SM = 152, 128
 DEFAULT_T = 4
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one 4-step tile-kernel launch on
-# this image, from an ncu capture of a warm-L2 launch (67.15 MB read + 20.98 MB written); valid
-# for the default 4 steps per launch only.
-TILE_T4_DRAM_BYTES = 88.13e6
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one 4-step flow launch on this
+# image, from the ncu capture of one warm-L2 launch of the current kernel summarised in
+# profiles/flow_tile_t4_4096x4096_full.md; reported as roofline.traffic for the default 4 steps
+# per launch and the full 500 iterations only
+TILE_T4_DRAM_BYTES = 87.84e6  # 67.15 MB read + 20.69 MB written
 # GB300 HBM3e nominal bandwidth (GB/s); fractions are reported against it and against the
 # measured copy bandwidth
 NOMINAL_HBM_GBS = 8000.0
@@ -70,12 +78,13 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--steps-per-launch", type=int, default=0)
     ap.add_argument("--iters", type=int, default=ITERS, help="override (profiling runs only)")
-    ap.add_argument("--workload", default="scale", choices=["scale", "precision", "batch", "diff", "l1", "fd"],
-                    help="scale: the headline 4096^2 run; precision / batch / diff: the reduced-"
-                         "storage, uneven-batch and reverse-mode measurements (one JSON line "
+    ap.add_argument("--workload", default="scale", choices=["scale", "pr1", "precision", "batch", "diff", "l1", "fd"],
+                    help="scale: the headline 4096^2 run; pr1 / precision / batch / diff: the 256^2, "
+                         "reduced-storage, uneven-batch and reverse-mode measurements (one JSON line "
                          "each, not the headline)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the secondary workloads")
     return ap.parse_args()
 
 
@@ -195,6 +204,35 @@ def cpu_oracle_rate(u, crop: int, iters: int, threads: int):
     return crop * crop * iters / dt / 1e9, dt
 
 
+def oracle_parity(u, gpu_result, crop: int, iters: int, threads: int):
+    """The CPU-baseline leg's comparison of the GPU with the FP64 oracle: `iters` oracle steps on
+    the crop x crop corner of the input (run step by step, counting the opposite-sign near-ties of
+    Eq. act that each step meets), against `gpu_result` (the GPU's U^iters of the whole image, on
+    the host).  The oracle's crop has a false edge, whose influence travels one pixel per step,
+    so the two are compared on the top-left (crop - iters)^2 window, where the crop's result is
+    the whole image's."""
+    import oracle
+    F = np.ascontiguousarray(u[:crop, :crop], dtype=np.float64)
+    R = float(u.max() - u.min())
+    tau = 2.0 ** -18 * R  # the tie band of the parity protocol
+    oracle.set_threads(threads)
+    U, ties = F.copy(), 0
+    for _ in range(iters):
+        ties += oracle.count_ties(U[:crop - iters + 1, :crop - iters + 1], tau)
+        U = oracle.denoise(F, LAM, STEP, 1, u0=U)
+    n = crop - iters
+    d = np.abs(np.asarray(gpu_result[:n, :n], dtype=np.float64) - U[:n, :n])
+    mse = float((d ** 2).mean())
+    return {"window": f"top-left {n}x{n} of the image (oracle on the {crop}x{crop} crop, {iters} iterations)",
+            "max_abs_err_over_range": float(d.max()) / R, "tol_over_range": 1e-5,
+            "pixels_beyond_tol": int((d > 1e-5 * R).sum()), "pixels": n * n,
+            "tie_events": ties, "tie_band_over_range": 2.0 ** -18,
+            "psnr_db_vs_oracle": 10 * math.log10(R * R / mse) if mse > 0 else None,
+            "note": "tie events: opposite-sign near-ties of Eq. act met by the oracle's trajectory "
+                    "(each step, on the region that reaches the window); a different choice there "
+                    "is valid and moves the pixel by about 2 step lambda |H^w|"}
+
+
 def host_threads() -> int:
     return os.cpu_count() or 1
 
@@ -226,6 +264,229 @@ def run_reference(args):
     return 0
 
 
+def fma_peak(wmc, dev):
+    """The compute roofline's denominator: FP32 FMA lane-operations per second of this GPU,
+    measured by the library's probe (8 independent packed FP32x2 FMA chains per thread, 8 CTAs
+    per SM, best of 5 launches of about 20 ms), with the device's SM count beside it."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    rate = wmc.measure_fma_rate(dev, iters=200_000, reps=5)
+    return {"tops": rate / 1e12, "sms": props.multi_processor_count,
+            "how": "wmc_probe_fma: 8 packed FP32x2 FMA chains per thread, 8 CTAs per SM, best of 5 "
+                   "(an FMA counts as one lane-operation)"}
+
+
+def event_ms(fn, reps, flush=None):
+    """Median device time (CUDA events on the current stream) of fn() over `reps` runs."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def measure_scale_image(wmc, dev, u_host, iters, T, reps, flush):
+    """The headline step (eval + `iters` flow iterations + energies) on another image of the
+    4096^2 recipe: Gpix-iter/s over the median step time, L2 flushed before each step."""
+    import torch
+    f = torch.from_numpy(u_host).to(dev)
+    hw, out = torch.empty_like(f), torch.empty_like(f)
+    h, w = f.shape
+    ws = torch.empty(wmc.load().wmc_denoise_workspace_size(h, w, w, 0), dtype=torch.uint8, device=dev)
+    ews = torch.empty(wmc.load().wmc_energy_workspace_size(h, w), dtype=torch.uint8, device=dev)
+    en = torch.empty(3, dtype=torch.float64, device=dev)
+
+    def step():
+        wmc.eval(f, out=hw)
+        wmc.denoise(f, LAM, STEP, iters, out=out, steps_per_launch=T, workspace=ws)
+        wmc.energy(out, f, None, out=en, workspace=ews)
+    for _ in range(3):
+        step()
+    ms = event_ms(step, reps, flush)
+    return {"gpix_iter_s": h * w * iters / (ms * 1e-3) / 1e9, "ms_per_step": ms, "steps": reps}
+
+
+def measure_pr1(wmc, dev, reps=50):
+    """256 x 256 PR1 image (seed 0, 8 bumps + 4 shapes, sigma 0.05): one evaluation plus 100
+    iterations (lambda 1, step 0.25, replicate), the input resident on the device; timed as plain
+    launches and as one replay of a CUDA graph of the same calls, for the default and the largest
+    steps per launch.  The image (786 KB per iteration) lives in L2: the run is launch and latency
+    bound."""
+    import torch
+    from paper_1903_07189_gb300 import synth
+    f = torch.from_numpy(synth.pr1_image()).to(dev)
+    hw, out = torch.empty_like(f), torch.empty_like(f)
+    n = f.numel()
+    ws = torch.empty(wmc.load().wmc_denoise_workspace_size(256, 256, 256, 0), dtype=torch.uint8, device=dev)
+    res = {}
+    for T in (DEFAULT_T, 8):
+        def run():
+            wmc.eval(f, out=hw)
+            wmc.denoise(f, 1.0, 0.25, 100, out=out, steps_per_launch=T, workspace=ws)
+        for _ in range(3):
+            run()
+        t_plain = event_ms(run, reps)
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            run()
+        torch.cuda.current_stream(dev).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            run()
+        g.replay()
+        t_graph = event_ms(g.replay, reps)
+        launches = 1 + math.ceil(100 / T)
+        res[f"T{T}"] = {"plain_us": 1e3 * t_plain, "graph_us": 1e3 * t_graph, "launches": launches,
+                        "plain_gpix_iter_s": n * 100 / (t_plain * 1e-3) / 1e9,
+                        "graph_gpix_iter_s": n * 100 / (t_graph * 1e-3) / 1e9}
+    return {"workload": "256x256 f32 (seed 0, 8 bumps + 4 shapes, sigma 0.05): 1 eval + 100 iterations, "
+                        "lambda 1, step 0.25, replicate", "runs": reps, **res}
+
+
+def measure_precision_rates(wmc, dev, img, iters, T, reps=2):
+    """The 16384^2 image stored as FP32, BF16 and FP16 (FP32 arithmetic, every step rounded to
+    the storage type): `iters` iterations per storage type, Gpix-iter/s of the best of `reps`
+    runs.  Returns the rates and the results (host, FP64) for the error against the oracle."""
+    import torch
+    n = img.shape[0]
+    rates, outs = {}, {}
+    for name, dt in [("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)]:
+        f = torch.from_numpy(img).to(dev).to(dt)
+        out = torch.empty_like(f)
+        ws = torch.empty(wmc.load().wmc_denoise_workspace_size(n, n, n, wmc.DTYPES[dt]), dtype=torch.uint8,
+                         device=dev)
+        run = lambda: wmc.denoise(f, LAM, STEP, iters, out=out, steps_per_launch=T, workspace=ws)
+        run()
+        ms = min(event_ms(run, 1) for _ in range(reps))
+        rates[name] = {"gpix_iter_s": n * n * iters / (ms * 1e-3) / 1e9, "ms": ms}
+        outs[name] = out
+        del f, ws
+    return rates, outs
+
+
+def measure_batch(wmc, dev, fs, lams, steps, iters, reps, world=1, T=0, tile=0):
+    """Many uneven images advanced together: (a) one plan's run captured in a CUDA graph and
+    replayed, (b) the same run launched directly, (c) looping the single-image path; the steps
+    per launch and tile shape picked by the library's autotuner unless given."""
+    import torch
+    tune = {}
+    if not T:
+        (T, tile), tune = wmc.batch_autotune(fs, lams, steps)
+    b = wmc.Batch(fs, lams, steps, steps_per_launch=T, tile=tile)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        b.run(iters)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.run(iters)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, k):
+        barrier()
+        return max_over_ranks(min(event_ms(fn, 1) for _ in range(k)), world, dev)
+
+    graph.replay()
+    t_graph = timed(graph.replay, max(1, reps))
+    t_direct = timed(lambda: b.run(iters), max(1, min(reps, 3)))
+    b.check_status()
+    outs = [torch.empty_like(f) for f in fs]
+    ws = torch.empty(max([wmc.load().wmc_denoise_workspace_size(f.shape[0], f.shape[1], f.shape[1], 0)
+                          for f in fs] or [256]), dtype=torch.uint8, device=dev)
+
+    def loop():
+        for f, l, st, o in zip(fs, lams, steps, outs):
+            wmc.denoise(f, l, st, iters, out=o, steps_per_launch=T, workspace=ws, tile=tile)
+
+    loop()
+    t_loop = timed(loop, 1)
+    same = all(torch.equal(a, c) for a, c in zip(b.outs, outs))
+    same = max_over_ranks(0.0 if same else 1.0, world, dev) == 0.0
+    px = sum(f.numel() for f in fs) * world  # the ranks' shares are balanced within 1 %
+    return {"steps_per_launch": T, "tile": tile,
+            "autotune_ms_per_iter": {f"T{k[0]}_tile{k[1]}": v for k, v in tune.items()},
+            "batched_graph": px * iters / (t_graph * 1e-3) / 1e9,
+            "batched_direct": px * iters / (t_direct * 1e-3) / 1e9,
+            "single_image_loop": px * iters / (t_loop * 1e-3) / 1e9,
+            "ms": {"graph": t_graph, "direct": t_direct, "loop": t_loop},
+            "batched_equals_loop_bitwise": same}
+
+
+def batch_inputs(dev, n=512, mine=None):
+    """The 512-image batch: sides uniform in [64, 1536] (seed 999), image i seed 1000+i, 8 bumps +
+    4 shapes, sigma_i ~ U[0.01, 0.15], lambda_i ~ U[0.5, 2] (seed 998), step_i = 0.5/(1+lambda_i)."""
+    import torch
+    from paper_1903_07189_gb300 import synth
+    sizes = synth.batch_sizes(n)
+    params = synth.batch_params(n)
+    mine = list(range(n)) if mine is None else mine
+    fs = [torch.from_numpy(synth.make_image(sizes[i][0], sizes[i][1], seed=1000 + i, n_bumps=8,
+                                            n_shapes=4, sigma=params[i][0])).to(dev) for i in mine]
+    lams = [params[i][1] for i in mine]
+    return fs, lams, [0.5 / (1 + l) for l in lams], sizes
+
+
+def measure_diff(wmc, dev, reps=5):
+    """32 images of 512 x 512 (seed 2000+i, 8 bumps + 4 shapes, sigma 0.05), K = 50 unrolled steps
+    (step 0.25), checkpoints every 7, loss MSE(U^K, clean), one learnable lambda per image:
+    forward, backward and forward + backward pixel-steps/s (n h w K per call) and the extra
+    device memory the call holds."""
+    import torch
+    from paper_1903_07189_gb300 import synth
+    n, h, w, K, c, step = 32, 512, 512, 50, 7, 0.25
+    pairs = [synth.make_image(h, w, seed=2000 + i, n_bumps=8, n_shapes=4, sigma=0.05, return_clean=True)
+             for i in range(n)]
+    f = torch.from_numpy(np.stack([p[0] for p in pairs]).astype(np.float32)).to(dev)
+    clean = torch.from_numpy(np.stack([p[1] for p in pairs]).astype(np.float32)).to(dev)
+    lam = torch.full((n,), 1.0, device=dev, requires_grad=True)
+
+    def fwd_bwd():
+        u = wmc.unrolled_denoise(f, lam, step, K, ckpt_every=c)
+        loss = ((u - clean) ** 2).mean()
+        lam.grad = None
+        loss.backward()
+        return loss
+
+    for _ in range(3):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.reset_peak_memory_stats(dev)
+    base_mem = torch.cuda.memory_allocated(dev)
+    for a, m, e in ev:
+        a.record()
+        u = wmc.unrolled_denoise(f, lam, step, K, ckpt_every=c)
+        loss = ((u - clean) ** 2).mean()
+        m.record()
+        lam.grad = None
+        loss.backward()
+        e.record()
+    torch.cuda.synchronize()
+    peak = torch.cuda.max_memory_allocated(dev) - base_mem
+    t_f = min(a.elapsed_time(m) for a, m, _ in ev)
+    t_b = min(m.elapsed_time(e) for _, m, e in ev)
+    t_fb = min(a.elapsed_time(e) for a, _, e in ev)
+    units = n * h * w * K
+    return {"fwd_bwd": units / (t_fb * 1e-3) / 1e9, "fwd": units / (t_f * 1e-3) / 1e9,
+            "bwd": units / (t_b * 1e-3) / 1e9, "unit": "Gpix-step/s", "ms": {"fwd": t_f, "bwd": t_b, "fwd_bwd": t_fb},
+            "peak_extra_mib": peak / 2**20, "no_checkpoint_mib": n * h * w * 4 * (K + 1) / 2**20,
+            "workload": "32 x 512^2 f32, K = 50, step 0.25, checkpoints every 7, loss MSE(U^K, clean)"}, (f, clean, lam, fwd_bwd)
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -249,6 +510,7 @@ def run_gpu(args):
     iters = args.iters
     T = args.steps_per_launch or DEFAULT_T
     n_launch = math.ceil(iters / T)
+    peak_fma = fma_peak(wmc, dev)
 
     def step():
         v0.record()
@@ -304,16 +566,22 @@ def run_gpu(args):
     launch_ms = statistics.mean(den_ms) / n_launch
     peak, peak_kind = peaks()
     hbm_achieved = BYTES_PER_PX_LAUNCH * H * W / (launch_ms * 1e-3) / 1e9
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    fp32_peak = SMS * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12  # TFLOP-lane-ops/s on the FMA pipe
     fp32_achieved = FMA_OPS_PER_PX_ITER * H * W * T / (launch_ms * 1e-3) / 1e12
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    nominal_fma = peak_fma["sms"] * 128 * sm_mhz * 1e6 / 1e12
     if T > 1:
-        roofline = {"bound": "alu", "achieved": fp32_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": fp32_achieved / fp32_peak,
-                    "traffic": TILE_T4_DRAM_BYTES if (T == 4 and iters == ITERS) else None,
+        full = T == DEFAULT_T and iters == ITERS
+        roofline = {"bound": "alu", "achieved": fp32_achieved, "peak": peak_fma["tops"], "unit": "TFLOP/s",
+                    "frac": fp32_achieved / peak_fma["tops"],
+                    "traffic": TILE_T4_DRAM_BYTES if full else None,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one warm-L2 4-step "
+                                      "launch on this image (profiles/flow_tile_t4_4096x4096_full.md)"
+                                      if full and TILE_T4_DRAM_BYTES else "not captured for this configuration",
                     "kernel": f"wmc::tile_flow_kernel<T={T}> (flow, {T} Jacobi steps per launch, 128 x 64 regions)",
-                    "peak_kind": f"FP32 FMA pipe lane-operations (an FMA counts once): {SMS} SMs x {FP32_LANES_PER_SM} lanes x {sm_mhz:.0f} MHz "
-                                 "(unit counts and the sampled clock)",
+                    "peak_kind": "measured: FP32 FMA pipe lane-operations per second (an FMA counts once), " + peak_fma["how"],
+                    "peak_nominal": {"value": nominal_fma, "how": f"{peak_fma['sms']} SMs (queried) x 128 lanes x "
+                                                                   f"{sm_mhz:.0f} MHz (sampled)",
+                                     "frac": fp32_achieved / nominal_fma},
                     "algorithmic_ops_per_px_iter": FMA_OPS_PER_PX_ITER, "launch_ms": launch_ms,
                     # the same iterations unblocked would move 12 B per pixel-iteration
                     "unblocked_equivalent": {"gbs": value * BYTES_PER_PX_LAUNCH,
@@ -323,7 +591,7 @@ def run_gpu(args):
                             "peak_kind": peak_kind, "frac_of_nominal": hbm_achieved / NOMINAL_HBM_GBS}}
     else:
         roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": peak, "unit": "GB/s",
-                    "frac": hbm_achieved / peak, "traffic": None, "kernel": "wmc::stream_kernel (flow step)",
+                    "frac": hbm_achieved / peak, "traffic": None, "kernel": "wmc::stream4_kernel (flow step)",
                     "peak_kind": peak_kind, "launch_ms": launch_ms}
 
     e2e = None
@@ -346,6 +614,32 @@ def run_gpu(args):
         e2e = {"value": job_rate(H * W * iters, world, dt * 1e3), "unit": UNIT, "h2d_bytes_per_step": H * W * 4,
                "d2h_bytes_per_step": H * W * 4, "call": "wmc_denoise_host (pinned host f in, U out)"}
 
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary:
+        secondary = {}
+        u2 = synth.make_image(H, W, seed=2, n_bumps=64, n_shapes=32, sigma=0.1)
+        secondary["scale_sigma_0p1"] = {"image": f"{H}x{W}, 64 bumps + 32 shapes, sigma 0.1, seed 2",
+                                        **measure_scale_image(wmc, dev, u2, iters, T, 3, flush)}
+        secondary["pr1"] = measure_pr1(wmc, dev)
+        del flush
+        torch.cuda.empty_cache()
+        prec_img = synth.make_image(16384, 16384, seed=3, n_bumps=64, n_shapes=32, sigma=0.05)
+        rates, outs = measure_precision_rates(wmc, dev, prec_img, 200, T)
+        del outs, prec_img
+        torch.cuda.empty_cache()
+        secondary["precision_16384"] = {"iters": 200, **{k: v["gpix_iter_s"] for k, v in rates.items()},
+                                        "unit": UNIT, "note": "FP32 arithmetic; every step rounded to the storage type"}
+        fs, lams, steps_b, _ = batch_inputs(dev)
+        bres = measure_batch(wmc, dev, fs, lams, steps_b, 300, 3)
+        secondary["batch_512"] = {k: bres[k] for k in ("batched_graph", "single_image_loop", "steps_per_launch", "tile",
+                                                         "batched_equals_loop_bitwise")}
+        secondary["batch_512"]["vs_single_image_headline"] = bres["batched_graph"] / value
+        del fs, bres
+        torch.cuda.empty_cache()
+        dres, _ = measure_diff(wmc, dev)
+        secondary["diff_32x512"] = {k: dres[k] for k in ("fwd_bwd", "fwd", "bwd", "unit", "peak_extra_mib")}
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = host_threads()
@@ -356,6 +650,9 @@ def run_gpu(args):
                                  "sample": f"512x512 top-left crop, 32 iterations ({dt1:.1f} s)"},
                "sample": f"2048x2048 top-left crop, 32 iterations (FP64 oracle, {threads} threads, {dt:.1f} s wall, "
                          f"{dt * threads:.0f} core-s)"}
+        # the same crop and iterations on the GPU, in the bench's launch configuration, against it
+        g32 = wmc.denoise(f, LAM, STEP, 32, out=out, steps_per_launch=T, workspace=ws)
+        cpu["parity"] = oracle_parity(u_host, g32[:2048, :2048].double().cpu().numpy(), 2048, 32, threads)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -374,6 +671,7 @@ def run_gpu(args):
                 "energy": {"ms": energy_ms, "hbm_gbs": 8 * H * W / (energy_ms * 1e-3) / 1e9,
                            "hbm_frac": 8 * H * W / (energy_ms * 1e-3) / 1e9 / peak,
                            "kernel": "wmc::energy_tma_kernel (FP64 energies of U and f; persistent, TMA windows), 8 B per pixel"},
+                "secondary": secondary,
                 "gpu_launches": args.steps * (2 + n_launch), "clocks": clocks,
                 "wall_s_timed_region": wall}
         print(json.dumps(line), flush=True)
@@ -382,85 +680,73 @@ def run_gpu(args):
     return 0
 
 
+def run_pr1(args):
+    import torch
+    from paper_1903_07189_gb300 import wmc
+    dev = torch.device("cuda", 0)
+    res = measure_pr1(wmc, dev, reps=max(10, args.steps))
+    print(json.dumps({"workload": "pr1", "metric": METRIC, "unit": UNIT, "results": res}), flush=True)
+    return 0
+
+
 def run_precision(args):
     """16384 x 16384 image (64 bumps, 32 shapes, sigma 0.05, seed 3) stored as FP32, BF16 and FP16,
-    200 iterations each; throughput per storage type and error against the FP64 oracle on the
-    top-left 2048 x 2048 crop (the oracle runs on a 2248 x 2248 crop: 200 px of light cone)."""
+    200 iterations each: throughput per storage type, the single-pass kernels at this size, and a
+    CPU-baseline leg that times the FP64 oracle on the top-left 2248 x 2248 crop (200 px of light
+    cone) and, from that run, gives each result's error on the 2048 x 2048 crop."""
     import torch
-    import oracle
     from paper_1903_07189_gb300 import synth, wmc
     dev = torch.device("cuda", 0)
     n, iters, crop, margin = 16384, 200, 2048, 200
+    T = args.steps_per_launch or DEFAULT_T
     img = synth.make_image(n, n, seed=3, n_bumps=64, n_shapes=32, sigma=0.05)
-    oracle.set_threads(os.cpu_count() or 1)
-    t0 = time.perf_counter()
-    ref = oracle.denoise(img[:crop + margin, :crop + margin].astype(np.float64), LAM, STEP, iters)[:crop, :crop]
-    oracle_s = time.perf_counter() - t0
-    ref_bf = {}
-    for st in ("bf16", "f16"):
+    rates, outs = measure_precision_rates(wmc, dev, img, iters, T, reps=max(1, min(args.steps, 3)))
+    got = {k: o[:crop, :crop].float().cpu().numpy().astype(np.float64) for k, o in outs.items()}
+    # the single-pass kernels at this size: one evaluation (8 B per pixel) and one-step launches
+    # (12 B per pixel-iteration), against the measured copy bandwidth
+    peak, _ = peaks()
+    f = torch.from_numpy(img).to(dev)
+    hw, out = torch.empty_like(f), torch.empty_like(f)
+    ws = torch.empty(wmc.load().wmc_denoise_workspace_size(n, n, n, 0), dtype=torch.uint8, device=dev)
+    te = min(event_ms(lambda: wmc.eval(f, out=hw), 1) for _ in range(5))
+    t1 = min(event_ms(lambda: wmc.denoise(f, LAM, STEP, 10, out=out, steps_per_launch=1, workspace=ws), 1)
+             for _ in range(3)) / 10
+    single = {"eval_ms": te, "eval_hbm_frac": 8 * n * n / (te * 1e-3) / 1e9 / peak,
+              "step_ms": t1, "step_hbm_frac": 12 * n * n / (t1 * 1e-3) / 1e9 / peak,
+              "kernel": {"eval": "wmc::eval_tma_kernel (persistent, double-buffered TMA windows)",
+                         "step": "wmc::stream4_kernel (4 cells per lane)"}}
+    del f, hw, out, ws, outs
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        threads = host_threads()
+        oracle.set_threads(threads)
         sub = img[:crop + margin, :crop + margin].astype(np.float64)
-        ref_bf[st] = oracle.denoise(sub, LAM, STEP, iters, storage=st)[:crop, :crop]
-    results = {}
-    for name, dt in [("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)]:
-        f = torch.from_numpy(img).to(dev).to(dt)
-        out = torch.empty_like(f)
-        ws = torch.empty(wmc.load().wmc_denoise_workspace_size(n, n, n, wmc.DTYPES[dt]), dtype=torch.uint8,
-                         device=dev)
-        T = args.steps_per_launch or DEFAULT_T
-        wmc.denoise(f, LAM, STEP, iters, out=out, steps_per_launch=T, workspace=ws)
-        torch.cuda.synchronize()
-        times = []
-        for _ in range(max(1, min(args.steps, 3))):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            wmc.denoise(f, LAM, STEP, iters, out=out, steps_per_launch=T, workspace=ws)
-            b.record()
-            torch.cuda.synchronize()
-            times.append(a.elapsed_time(b))
-        got = out[:crop, :crop].float().cpu().numpy().astype(np.float64)
-        err = np.abs(got - ref)
-        mse = float((err ** 2).mean())
-        r = {"gpix_iter_s": n * n * iters / (min(times) * 1e-3) / 1e9, "ms": min(times),
-             "max_abs_err_vs_fp64": float(err.max()),
-             "psnr_vs_fp64_db": 10 * np.log10(1.0 / mse) if mse > 0 else float("inf")}
-        if name == "f32":
-            # the single-pass kernels at this size: one evaluation (8 B per pixel) and one-step
-            # launches (12 B per pixel-iteration), against the measured copy bandwidth
-            peak, _ = peaks()
-            hw = torch.empty_like(f)
-
-            def best(fn, reps=5):
-                fn()
-                ts = []
-                for _ in range(reps):
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record()
-                    fn()
-                    b.record()
-                    torch.cuda.synchronize()
-                    ts.append(a.elapsed_time(b))
-                return min(ts)
-            te = best(lambda: wmc.eval(f, out=hw))
-            t1 = best(lambda: wmc.denoise(f, LAM, STEP, 10, out=out, steps_per_launch=1, workspace=ws)) / 10
-            r["single_pass"] = {"eval_ms": te, "eval_hbm_frac": 8 * n * n / (te * 1e-3) / 1e9 / peak,
-                                "step_ms": t1, "step_hbm_frac": 12 * n * n / (t1 * 1e-3) / 1e9 / peak,
-                                "kernel": {"eval": "wmc::eval_tma_kernel (persistent, double-buffered TMA windows)",
-                                           "step": "wmc::stream4_kernel (4 cells per lane)"}}
-            del hw
-        if name in ref_bf:
-            e2 = np.abs(got - ref_bf[name])
-            r["max_abs_err_vs_emulated_storage"] = float(e2.max())
-            r["frac_beyond_1ulp_vs_emulated"] = float((e2 > np.abs(ref_bf[name]) * (2.0 ** -7 if name == "bf16" else 2.0 ** -10)).mean())
-        results[name] = r
-        del f, out, ws
-        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        ref = oracle.denoise(sub, LAM, STEP, iters)[:crop, :crop]
+        oracle_s = time.perf_counter() - t0
+        errs = {}
+        for name in ("f32", "bf16", "f16"):
+            err = np.abs(got[name] - ref)
+            mse = float((err ** 2).mean())
+            e = {"max_abs_err_vs_fp64": float(err.max()),
+                 "psnr_vs_fp64_db": 10 * np.log10(1.0 / mse) if mse > 0 else float("inf")}
+            if name != "f32":
+                emu = oracle.denoise(sub, LAM, STEP, iters, storage=name)[:crop, :crop]
+                e2 = np.abs(got[name] - emu)
+                e["max_abs_err_vs_emulated_storage"] = float(e2.max())
+                e["frac_beyond_1ulp_vs_emulated"] = float(
+                    (e2 > np.abs(emu) * (2.0 ** -7 if name == "bf16" else 2.0 ** -10)).mean())
+            errs[name] = e
+        px = (crop + margin) ** 2 * iters
+        cpu = {"value": px / oracle_s / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"top-left {crop + margin}x{crop + margin} crop, {iters} iterations (FP64, {oracle_s:.1f} s)",
+               "errors_on_top_left_2048": errs}
     line = {"workload": "precision", "metric": METRIC, "unit": UNIT, "config": {
         "image": f"{n}x{n} synthetic (64 bumps + 32 shapes, sigma 0.05, seed 3)", "iters": iters,
-        "lambda": LAM, "step": STEP, "boundary": "replicate",
-        "error_crop": f"top-left {crop}x{crop} (oracle on {crop + margin}x{crop + margin}, FP64, "
-                      f"{oracle.get_threads()} threads, {oracle_s:.1f} s)",
+        "lambda": LAM, "step": STEP, "boundary": "replicate", "steps_per_launch": T,
         "arithmetic": "FP32 for every storage type; every step rounds to the storage type"},
-        "results": results}
+        "results": rates, "single_pass_f32": single, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -483,78 +769,20 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=dev)
     n, iters = 512, 300
     sizes = synth.batch_sizes(n)
-    params = synth.batch_params(n)
     costs = [h * w for h, w in sizes]
     owner, loads = wmc.shard_lpt(costs, world)
     mine = [i for i in range(n) if owner[i] == rank]
-    fs = [torch.from_numpy(synth.make_image(sizes[i][0], sizes[i][1], seed=1000 + i, n_bumps=8,
-                                            n_shapes=4, sigma=params[i][0])).to(dev) for i in mine]
-    lams = [params[i][1] for i in mine]
-    steps = [0.5 / (1 + l) for l in lams]
-    px = sum(costs)
-    # steps per launch and tile shape picked by the library's autotuner (times each candidate on
-    # this batch)
-    if args.steps_per_launch:
-        (T, tile), tune = (args.steps_per_launch, 0), {}
-    else:
-        (T, tile), tune = wmc.batch_autotune(fs, lams, steps)
-    b = wmc.Batch(fs, lams, steps, steps_per_launch=T, tile=tile)
-    s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        b.run(iters)
-    torch.cuda.current_stream().wait_stream(s)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        b.run(iters)
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    def timed(fn, reps):
-        ts = []
-        for _ in range(reps):
-            barrier()
-            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            e.record()
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(e))
-        return max_over_ranks(min(ts), world, dev)
-
-    graph.replay()
-    t_graph = timed(graph.replay, max(1, min(args.steps, 5)))
-    t_direct = timed(lambda: b.run(iters), max(1, min(args.steps, 3)))
-    b.check_status()
-    outs = [torch.empty_like(f) for f in fs]
-    ws = torch.empty(max([wmc.load().wmc_denoise_workspace_size(sizes[i][0], sizes[i][1], sizes[i][1], 0)
-                          for i in mine] or [256]), dtype=torch.uint8, device=dev)
-
-    def loop():
-        for f, l, st, o in zip(fs, lams, steps, outs):
-            wmc.denoise(f, l, st, iters, out=o, steps_per_launch=T, workspace=ws, tile=tile)
-
-    loop()
-    t_loop = timed(loop, 1)
-    same = all(torch.equal(a, c) for a, c in zip(b.outs, outs))
-    same = max_over_ranks(0.0 if same else 1.0, world, dev) == 0.0
+    fs, lams, steps, _ = batch_inputs(dev, n, mine)
+    res = measure_batch(wmc, dev, fs, lams, steps, iters, max(1, min(args.steps, 5)), world,
+                        T=args.steps_per_launch, tile=0)
     if rank == 0:
         line = {"workload": "batch", "metric": METRIC, "unit": UNIT, "n_gpus": world,
                 "scaling": "strong", "config": {
-                    "images": n, "pixels": px, "sides": "uniform [64, 1536] (seed 999)", "iters": iters,
+                    "images": n, "pixels": sum(costs), "sides": "uniform [64, 1536] (seed 999)", "iters": iters,
                     "sigma": "U[0.01, 0.15]", "lambda": "U[0.5, 2]", "step": "0.5/(1+lambda)", "dtype": "f32",
-                    "steps_per_launch": T, "tile": tile,
-                    "autotune_ms_per_iter": {f"T{k[0]}_tile{k[1]}": v for k, v in tune.items()},
                     "shard": {"rule": "longest first to the least-loaded rank, by pixel count",
                               "pixels_per_rank": loads}},
-                "results": {"batched_graph": px * iters / (t_graph * 1e-3) / 1e9,
-                            "batched_direct": px * iters / (t_direct * 1e-3) / 1e9,
-                            "single_image_loop": px * iters / (t_loop * 1e-3) / 1e9,
-                            "ms": {"graph": t_graph, "direct": t_direct, "loop": t_loop},
-                            "batched_equals_loop_bitwise": same}}
+                "results": res}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -656,68 +884,23 @@ def run_fd(args):
 
 
 def run_diff(args):
-    """Training through the unrolled flow: 32 images of 512 x 512 (seed 2000+i, 8 bumps + 4
-    shapes, sigma 0.05), one learnable lambda per image (init 1.0), K = 50 denoising steps with
-    step 0.25, checkpoints every 7 steps, loss = mean squared error of U^K against the clean
-    image.  Reports forward, backward and forward+backward pixel-steps/s (n*h*w*K per call), the
-    device memory the checkpoints save, and the loss over a few gradient steps on lambda."""
+    """Training through the unrolled flow (measure_diff), plus the loss over a few Adam steps on
+    the 32 lambdas (it must go down)."""
     import torch
-    from paper_1903_07189_gb300 import synth, wmc
+    from paper_1903_07189_gb300 import wmc
     dev = torch.device("cuda", 0)
-    n, h, w, K, c, step = 32, 512, 512, 50, 7, 0.25
-    pairs = [synth.make_image(h, w, seed=2000 + i, n_bumps=8, n_shapes=4, sigma=0.05,
-                              return_clean=True) for i in range(n)]
-    f = torch.from_numpy(np.stack([p[0] for p in pairs]).astype(np.float32)).to(dev)
-    clean = torch.from_numpy(np.stack([p[1] for p in pairs]).astype(np.float32)).to(dev)
-    lam = torch.full((n,), 1.0, device=dev, requires_grad=True)
-
-    def fwd_bwd():
-        u = wmc.unrolled_denoise(f, lam, step, K, ckpt_every=c)
-        loss = ((u - clean) ** 2).mean()
-        lam.grad = None
-        loss.backward()
-        return loss
-
-    for _ in range(max(3, args.warmup)):
-        fwd_bwd()
-    torch.cuda.synchronize()
-    reps = max(3, min(args.steps, 20))
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-    torch.cuda.reset_peak_memory_stats(dev)
-    base_mem = torch.cuda.memory_allocated(dev)
-    for a, m, e in ev:
-        a.record()
-        u = wmc.unrolled_denoise(f, lam, step, K, ckpt_every=c)
-        loss = ((u - clean) ** 2).mean()
-        m.record()
-        lam.grad = None
-        loss.backward()
-        e.record()
-    torch.cuda.synchronize()
-    peak = torch.cuda.max_memory_allocated(dev) - base_mem
-    t_f = min(a.elapsed_time(m) for a, m, _ in ev)
-    t_b = min(m.elapsed_time(e) for _, m, e in ev)
-    t_fb = min(a.elapsed_time(e) for a, _, e in ev)
-    units = n * h * w * K
-    # a few Adam steps on lambda: the loss must go down
+    res, (f, clean, lam, fwd_bwd) = measure_diff(wmc, dev, reps=max(3, min(args.steps, 20)))
     opt = torch.optim.Adam([lam], lr=0.1)
     losses = []
     for _ in range(5):
         opt.zero_grad()
         losses.append(float(fwd_bwd()))
         opt.step()
+    res.update({"adam_losses": losses, "lambda_mean_after": float(lam.mean())})
     line = {"workload": "diff", "metric": "gigapixel-steps/s of unrolled denoising, forward + backward",
-            "unit": "Gpix-step/s", "config": {
-                "images": n, "h": h, "w": w, "K": K, "ckpt_every": c, "step": step, "lambda_init": 1.0,
-                "loss": "MSE(U^K, clean)", "dtype": "f32", "inputs": "synthetic, seed 2000+i, 8 bumps + "
-                "4 shapes, sigma 0.05"},
-            "results": {"fwd_bwd": units / (t_fb * 1e-3) / 1e9, "fwd": units / (t_f * 1e-3) / 1e9,
-                        "bwd": units / (t_b * 1e-3) / 1e9,
-                        "ms": {"fwd": t_f, "bwd": t_b, "fwd_bwd": t_fb},
-                        "peak_extra_mib": peak / 2**20,
-                        "no_checkpoint_mib": n * h * w * 4 * (K + 1) / 2**20,
-                        "adam_losses": losses, "lambda_mean_after": float(lam.mean())}}
+            "unit": "Gpix-step/s", "config": {"lambda_init": 1.0, "dtype": "f32",
+                                              "inputs": "synthetic, seed 2000+i, 8 bumps + 4 shapes, sigma 0.05"},
+            "results": res}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -726,6 +909,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "pr1":
+        return run_pr1(args)
     if args.workload == "precision":
         return run_precision(args)
     if args.workload == "batch":
