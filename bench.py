@@ -374,8 +374,9 @@ def measure_precision_rates(wmc, dev, img, iters, T, reps=2):
 
 def measure_batch(wmc, dev, fs, lams, steps, iters, reps, world=1, T=0, tile=0):
     """Many uneven images advanced together: (a) one plan's run captured in a CUDA graph and
-    replayed, (b) the same run launched directly, (c) looping the single-image path; the steps
-    per launch and tile shape picked by the library's autotuner unless given."""
+    replayed, (b) the same run launched directly, (c) looping the single-image path (its default
+    configuration); the batch's steps per launch and tile shape are picked by the library's
+    autotuner unless given."""
     import torch
     tune = {}
     if not T:
@@ -407,9 +408,9 @@ def measure_batch(wmc, dev, fs, lams, steps, iters, reps, world=1, T=0, tile=0):
     ws = torch.empty(max([wmc.load().wmc_denoise_workspace_size(f.shape[0], f.shape[1], f.shape[1], 0)
                           for f in fs] or [256]), dtype=torch.uint8, device=dev)
 
-    def loop():
+    def loop():  # the single-image path in its default configuration
         for f, l, st, o in zip(fs, lams, steps, outs):
-            wmc.denoise(f, l, st, iters, out=o, steps_per_launch=T, workspace=ws, tile=tile)
+            wmc.denoise(f, l, st, iters, out=o, workspace=ws)
 
     loop()
     t_loop = timed(loop, 1)

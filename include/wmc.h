@@ -114,7 +114,11 @@ wmc_status_t wmc_eval_status(wmc_stream_t stream);
  *   iters >= 0 (0 copies U^0 to u).
  *   workspace: device, >= wmc_denoise_workspace_size() bytes, WMC_WORKSPACE_ALIGN-aligned,
  *   must not overlap f, u0 or u (not needed when iters == 0).  It holds a status word (first
- *   bytes, cleared by every call) and one ping-pong image; see wmc_denoise_status().
+ *   bytes, cleared by every call) and one ping-pong image; see wmc_denoise_status().  When the
+ *   row pitch is not a multiple of 16 bytes (ld not a multiple of 4 elements for FP32, of 8 for
+ *   BF16/FP16) the multi-step kernels cannot read the images through TMA: the workspace then
+ *   holds three images of the next aligned pitch, the call copies U^0 and f into two of them,
+ *   the launches ping-pong in the workspace and only the last one writes u.
  *   Sides up to 2^24 pixels.
  * Errors: WMC_ERR_INVALID_ARG, WMC_ERR_ALIAS, WMC_ERR_WORKSPACE, WMC_ERR_CUDA.
  */
@@ -167,8 +171,9 @@ wmc_status_t wmc_selftest_status_timeout(int32_t target, int64_t limit_ns, wmc_s
  *   Scratch comes from one fixed device array of wmc_denoise_noalloc_max_bytes() bytes
  *   (32 MiB) inside the library; every GPU that loads the library holds it until the process
  *   exits.  Images whose wmc_denoise_workspace_size() exceeds that are rejected with
- *   WMC_ERR_INVALID_ARG (FP32 up to about 8.3 M pixels, e.g. 2880 x 2880; BF16/FP16 up to about
- *   16.7 M, e.g. 4064 x 4064) -- use wmc_denoise for larger ones.
+ *   WMC_ERR_INVALID_ARG (with a pitch that is a multiple of 16 bytes: FP32 up to about 8.3 M
+ *   pixels, e.g. 2880 x 2880; BF16/FP16 up to about 16.7 M, e.g. 4064 x 4064; other pitches
+ *   need three images of scratch, so about a third of that) -- use wmc_denoise for larger ones.
  *   The first call on each device looks up the array's device address with that device
  *   current; make that first call before capturing any stream into a CUDA graph.
  *   All calls on a device share the one array and the array keeps the last call's contents:
@@ -240,12 +245,16 @@ wmc_status_t wmc_energy(const void *u, const void *f, const void *clean, int32_t
  *   any f or any other u.  h or w may be 0 (the image is skipped).
  *
  *   wmc_batch_workspace_size: device bytes for the plan below (status word, per-image
- *   descriptors and tensor maps, the tile table, and one ping-pong image per input).
+ *   descriptors and tensor maps, the tile table, two ping-pong images per input, and a copy of f
+ *   for every input whose f cannot be read through TMA as it is: base or pitch not a multiple of
+ *   16 bytes).  The kernels read only 16-byte aligned buffers, whatever the caller's pitch;
+ *   u itself is only written, by the last launch of a run.
  *   wmc_batch_plan: validates the images, writes descriptors and the tile table into
  *   `workspace` (device, WMC_WORKSPACE_ALIGN-aligned) and fills `plan` (caller-owned host
  *   memory, opaque).  It synchronises `stream` once, so the `imgs` array may be freed on return.
  *   wmc_batch_run: `iters` Jacobi steps of every image; only kernel launches and one 4-byte
- *   memset are enqueued on `stream`, so the call can be captured into a CUDA graph and replayed.
+ *   memset are enqueued on `stream` (the first launch refreshes the workspace copies of f, so f
+ *   may change between runs), so the call can be captured into a CUDA graph and replayed.
  *   The plan (and its workspace) stays valid until the caller frees them.  wmc_denoise_status()
  *   on the workspace reports a timed-out tile load, as for single images.
  *   wmc_denoise_batched: plan + run in one call.

@@ -164,8 +164,19 @@ size_t image_bytes(int32_t h, int64_t ld, wmc_dtype_t dtype) {
     return round_up((size_t)h * (size_t)ld * elem_size(dtype), WMC_WORKSPACE_ALIGN);
 }
 
-// The flow on device buffers; all checks done by the caller.  `ws` holds the status word
-// (first kStatusBytes) followed by one image.
+// Whether an image with this pitch is staged through aligned workspace images for the
+// temporally blocked launches (TMA reads need a pitch that is a multiple of 16 bytes).
+bool staged_pitch(int64_t ld, size_t es) { return ((size_t)ld * es) % 16 != 0; }
+
+int64_t aligned_pitch(int32_t w, size_t es) {
+    const int64_t A = 16 / (int64_t)es;
+    return (w + A - 1) / A * A;
+}
+
+// The flow on device buffers; all checks done by the caller.  `ws` holds the status word (first
+// kStatusBytes) followed by one image of pitch ld, or, for pitches TMA cannot describe, three
+// images of an aligned pitch (two ping-pong images and a copy of f), so that every buffer a
+// multi-step launch reads is TMA-readable and only the last launch touches u.
 wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
                       wmc_dtype_t dtype, float lambda, float step, int32_t iters,
                       wmc_boundary_t bnd, int steps_per_launch, void *ws, cudaStream_t st,
@@ -191,12 +202,31 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
     const float mu = f ? 1.0f : 0.0f;
     const float c_keep = 1.0f - step * mu, c_f = step * mu;
     const float c_h = fd ? step * lambda : step * lambda / 12.0f;
-    // Ping-pong between u and the workspace so that the last launch writes u.  When U^0
-    // already lives in u, the first launch must write the workspace; if the parity then
-    // ends in the workspace, one copy finishes the job.
+    // Buffers: launch k reads src_k (pitch ld_in) and writes dst_k (pitch ld_out on the last
+    // launch, ld_in otherwise); f_read is the f the launches read.
+    const bool staged = T > 1 && nl > 1 && staged_pitch(ld, es);
+    const int64_t ld_in = staged ? aligned_pitch(w, es) : ld;
+    const void *f_read = f;
     void *bufs[2];
     bool copy_back = false;
-    if (u0 == u) {
+    const void *src = u0;
+    if (staged) {
+        // U^0 and f copied into aligned images; the launches between the first and the last
+        // ping-pong between the two ping-pong images
+        const size_t one = image_bytes(h, ld_in, dtype);
+        char *A = static_cast<char *>(ws), *B = A + one, *F = B + one;
+        e = cudaMemcpy2DAsync(A, ld_in * es, u0, ld * es, w * es, h, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && f)
+            e = cudaMemcpy2DAsync(F, ld_in * es, f, ld * es, w * es, h, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "stage U^0 and f");
+        src = A;
+        f_read = f ? F : nullptr;
+        bufs[0] = B;
+        bufs[1] = A;
+    } else if (u0 == u) {
+        // Ping-pong between u and the workspace so that the last launch writes u.  When U^0
+        // already lives in u, the first launch must write the workspace; if the parity then
+        // ends in the workspace, one copy finishes the job.
         bufs[0] = ws;
         bufs[1] = u;
         copy_back = (nl % 2) == 1;
@@ -207,32 +237,34 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
         bufs[0] = ws;
         bufs[1] = u;
     }
-    const bool vec = pair_aligned(u0, ld, es) && pair_aligned(f, ld, es) &&
-                     pair_aligned(u, ld, es) && pair_aligned(ws, ld, es);
+    const bool vec = pair_aligned(src, ld_in, es) && pair_aligned(f_read, ld_in, es) &&
+                     pair_aligned(u, ld, es) && pair_aligned(bufs[0], ld_in, es) && pair_aligned(bufs[1], ld_in, es);
     // Tensor maps for every buffer a tile launch may read: U^0 and the two ping-pong buffers.
     CUtensorMap maps[3];
     bool tma[3] = {false, false, false};
-    const void *srcs[3] = {u0, bufs[0], bufs[1]};
+    const void *srcs[3] = {src, bufs[0], bufs[1]};
     if (T > 1)
-        for (int k = 0; k < 3; ++k) tma[k] = encode_window_map(&maps[k], srcs[k], dtype, h, w, ld, tile);
+        for (int k = 0; k < 3; ++k) tma[k] = encode_window_map(&maps[k], srcs[k], dtype, h, w, ld_in, tile);
     // f's window is loaded by TMA with U's (same box)
     alignas(64) CUtensorMap fmap;
     memset(&fmap, 0, sizeof fmap);
-    const bool f_tma = T > 1 && f != nullptr && encode_window_map(&fmap, f, dtype, h, w, ld, tile);
+    const bool f_tma = T > 1 && f_read != nullptr && encode_window_map(&fmap, f_read, dtype, h, w, ld_in, tile);
 
-    const void *src = u0;
     int src_id = 0;
     int done = 0;
     bool prev_tile = false;
     for (int k = 0; k < nl; ++k) {
         const int s = (iters - done) < T ? (iters - done) : T;
-        void *dst = bufs[k & 1];
+        const bool last = k == nl - 1;
+        void *dst = (staged && last) ? u : bufs[k & 1];
+        const int64_t ldo = (staged && last) ? ld : ld_in;
         if (s == 1) {
             wmc::StreamParams sp{};
             sp.u = src;
-            sp.f = f;
+            sp.f = f_read;
             sp.out = dst;
-            sp.ldu = sp.ldf = sp.ldo = ld;
+            sp.ldu = sp.ldf = ld_in;
+            sp.ldo = ldo;
             sp.h = h;
             sp.w = w;
             sp.c_keep = c_keep;
@@ -243,9 +275,10 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
         } else {
             wmc::TileParams tp{};
             tp.u = src;
-            tp.f = f;
+            tp.f = f_read;
             tp.out = dst;
-            tp.ld = ld;
+            tp.ld = ld_in;
+            tp.ld_out = ldo;
             tp.h = h;
             tp.w = w;
             tp.use_tma = tma[src_id] ? 1 : 0;
@@ -314,6 +347,7 @@ struct BatchPlan {
     int32_t n, dtype, bnd, steps;
     int32_t owt, oht;
     int32_t tile;
+    int32_t any_copy;  // some image reads a workspace copy of its f
     uint32_t magic;
 };
 static_assert(sizeof(BatchPlan) <= sizeof(wmc_batch_t), "plan does not fit wmc_batch_t");
@@ -328,8 +362,15 @@ void out_tile(int T, int tile, int *owt, int *oht) {
 struct BatchLayout {
     size_t off_images, off_tiles, off_bufs, total;
     int64_t ntiles;
-    std::vector<size_t> buf_off;
+    std::vector<size_t> buf_off;   // per image: two ping-pong images, then f's copy if needed
+    std::vector<int64_t> ld_read;  // per image: pitch of the buffers the kernels read
+    std::vector<char> copy_f;      // per image: f is copied into the workspace (pitch or base not TMA-able)
 };
+
+// The caller's buffer can be read through TMA as it is: 16-byte aligned base and pitch.
+bool tma_able(const void *p, int64_t ld, size_t es) {
+    return ((uintptr_t)p % 16) == 0 && ((size_t)ld * es) % 16 == 0;
+}
 
 BatchLayout batch_layout(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype, int T, int tile) {
     BatchLayout L{};
@@ -343,10 +384,18 @@ BatchLayout batch_layout(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype, 
             L.ntiles += (int64_t)((imgs[i].w + owt - 1) / owt) * ((imgs[i].h + oht - 1) / oht);
     L.off_bufs = round_up(L.off_tiles + (size_t)L.ntiles * sizeof(int4), WMC_WORKSPACE_ALIGN);
     size_t off = L.off_bufs;
+    const size_t es = elem_size(dtype);
+    const int64_t A = 16 / (int64_t)es;
     L.buf_off.resize(n);
+    L.ld_read.resize(n);
+    L.copy_f.resize(n);
     for (int32_t i = 0; i < n; ++i) {
         L.buf_off[i] = off;
-        if (imgs[i].h > 0 && imgs[i].w > 0) off += image_bytes(imgs[i].h, imgs[i].ld, dtype);
+        const wmc_image_t &m = imgs[i];
+        const bool copy = !tma_able(m.f, m.ld, es);
+        L.copy_f[i] = copy;
+        L.ld_read[i] = copy ? (m.w + A - 1) / A * A : m.ld;
+        if (m.h > 0 && m.w > 0) off += (copy ? 3 : 2) * image_bytes(m.h, L.ld_read[i], dtype);
     }
     L.total = off;
     return L;
@@ -412,16 +461,19 @@ wmc_status_t check_batch(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtype, 
     return WMC_OK;
 }
 
-// U = f for every output tile of a batch (a run with zero iterations).
+// Copies the caller's f of every output tile: into u (to_u: a run with zero iterations), or
+// into the workspace copy the kernels read, for the images that have one (at the start of a run).
 template <typename E>
-__global__ void batch_copy_kernel(const wmc::BatchImage *images, const int4 *tiles, int owt, int oht) {
+__global__ void batch_copy_kernel(const wmc::BatchImage *images, const int4 *tiles, int owt, int oht, int to_u) {
     const int4 t = tiles[blockIdx.x];
     const wmc::BatchImage &im = images[t.x];
-    const E *f = static_cast<const E *>(im.buf[0]);
-    E *u = static_cast<E *>(const_cast<void *>(im.buf[1]));
+    if (!to_u && !im.copy_f) return;
+    const E *f = static_cast<const E *>(im.f_src);
+    E *dst = static_cast<E *>(const_cast<void *>(im.buf[to_u ? 1 : 0]));
+    const int64_t ldd = to_u ? im.ld_out : im.ld;
     for (int idx = threadIdx.x; idx < owt * oht; idx += blockDim.x) {
         const int y = t.z + idx / owt, x = t.y + idx % owt;
-        if (y < im.h && x < im.w) u[(int64_t)y * im.ld + x] = f[(int64_t)y * im.ld + x];
+        if (y < im.h && x < im.w) dst[(int64_t)y * ldd + x] = f[(int64_t)y * im.ld_out + x];
     }
 }
 
@@ -466,13 +518,13 @@ wmc_status_t check_unrolled(const float *f, const float *lambda, float step, int
 
 template <typename F>
 void for_each_launch(int iters, int T, F &&fn) {
-    // launch k takes min(T, remaining) steps; the roles alternate so that the last launch writes
-    // u (role 1): f (role 0) is read by the first launch only
+    // launch k takes min(T, remaining) steps; the first reads f (role 0) as U^0, the last writes u
+    // (role 1), and the ones between ping-pong between the workspace images (roles 2 and 3)
     const int nl = (iters + T - 1) / T;
     int src = 0, done = 0;
     for (int k = 0; k < nl; ++k) {
         const int s = (iters - done) < T ? (iters - done) : T;
-        const int dst = ((nl - 1 - k) % 2 == 0) ? 1 : 2;
+        const int dst = (k == nl - 1) ? 1 : 2 + (k & 1);
         fn(s, src, dst);
         src = dst;
         done += s;
@@ -619,7 +671,12 @@ wmc_status_t wmc_eval_fd(const void *u, void *hw, int32_t h, int32_t w, int64_t 
 }
 
 size_t wmc_denoise_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype) {
-    if (h <= 0 || w <= 0 || ld < w || elem_size(dtype) == 0) return 0;
+    const size_t es = elem_size(dtype);
+    if (h <= 0 || w <= 0 || ld < w || es == 0) return 0;
+    // staged pitches: three aligned images, and at least one image of pitch ld for the calls that
+    // are not staged (one launch, or one step per launch)
+    if (staged_pitch(ld, es))
+        return std::max(3 * image_bytes(h, aligned_pitch(w, es), dtype), image_bytes(h, ld, dtype)) + kStatusBytes;
     return image_bytes(h, ld, dtype) + kStatusBytes;
 }
 
@@ -846,6 +903,7 @@ wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtyp
     out_tile(T, tile, &owt, &oht);
     char *base = static_cast<char *>(workspace);
     std::vector<wmc::BatchImage> desc((size_t)n);
+    bool any_copy = false;
     std::vector<int4> tiles;
     tiles.reserve((size_t)L.ntiles);
     for (int32_t i = 0; i < n; ++i) {
@@ -853,17 +911,23 @@ wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtyp
         wmc::BatchImage &d = desc[i];
         memset(&d, 0, sizeof d);
         if (m.h == 0 || m.w == 0) continue;
-        d.buf[0] = m.f;
+        const size_t one = image_bytes(m.h, L.ld_read[i], dtype);
+        d.copy_f = L.copy_f[i];
+        d.f_src = m.f;
+        d.buf[0] = d.copy_f ? base + L.buf_off[i] + 2 * one : m.f;
         d.buf[1] = m.u;
         d.buf[2] = base + L.buf_off[i];
-        d.ld = m.ld;
+        d.buf[3] = base + L.buf_off[i] + one;
+        d.ld = L.ld_read[i];
+        d.ld_out = m.ld;
         d.h = m.h;
         d.w = m.w;
         d.c_keep = 1.0f - m.step;
         d.c_f = m.step;
         d.c_h = m.step * m.lambda / 12.0f;
-        for (int r = 0; r < 3; ++r)
-            d.use_tma[r] = encode_window_map(&d.map[r], d.buf[r], dtype, m.h, m.w, m.ld, tile) ? 1 : 0;
+        for (int r = 0; r < 4; ++r)
+            d.use_tma[r] = r != 1 && encode_window_map(&d.map[r], d.buf[r], dtype, m.h, m.w, d.ld, tile) ? 1 : 0;
+        any_copy |= d.copy_f != 0;
         for (int y0 = 0; y0 < m.h; y0 += oht)
             for (int x0 = 0; x0 < m.w; x0 += owt) tiles.push_back(make_int4(i, x0, y0, 0));
     }
@@ -889,6 +953,7 @@ wmc_status_t wmc_batch_plan(const wmc_image_t *imgs, int32_t n, wmc_dtype_t dtyp
     bp.owt = owt;
     bp.oht = oht;
     bp.tile = tile;
+    bp.any_copy = any_copy ? 1 : 0;
     bp.magic = kBatchMagic;
     memcpy(plan, &bp, sizeof bp);
     return WMC_OK;
@@ -913,16 +978,22 @@ wmc_status_t wmc_batch_run(const wmc_batch_t *plan, int32_t iters, wmc_stream_t 
     p.owt = bp.owt;
     p.oht = bp.oht;
     p.status = status;
-    if (iters == 0) {  // U^0 = f: copy every output tile
-        const int es = (int)elem_size((wmc_dtype_t)bp.dtype);
-        if (bp.ntiles > 0x7fffffffLL) return fail(WMC_ERR_INVALID_ARG, "too many tiles");
+    if (bp.ntiles > 0x7fffffffLL) return fail(WMC_ERR_INVALID_ARG, "too many tiles");
+    const int es = (int)elem_size((wmc_dtype_t)bp.dtype);
+    auto copy = [&](int to_u) {
         if (es == 4)
-            batch_copy_kernel<uint32_t><<<(unsigned)bp.ntiles, 256, 0, st>>>(p.images, p.tiles, bp.owt, bp.oht);
+            batch_copy_kernel<uint32_t><<<(unsigned)bp.ntiles, 256, 0, st>>>(p.images, p.tiles, bp.owt, bp.oht, to_u);
         else
-            batch_copy_kernel<uint16_t><<<(unsigned)bp.ntiles, 256, 0, st>>>(p.images, p.tiles, bp.owt, bp.oht);
-        e = cudaGetLastError();
+            batch_copy_kernel<uint16_t><<<(unsigned)bp.ntiles, 256, 0, st>>>(p.images, p.tiles, bp.owt, bp.oht, to_u);
+        return cudaGetLastError();
+    };
+    if (iters == 0) {  // U^0 = f: copy every output tile
+        e = copy(1);
         return e == cudaSuccess ? WMC_OK : cuda_fail(e, "batch copy launch");
     }
+    // the images whose f the kernels cannot read through TMA read the workspace copy, taken now
+    // (f may have changed since the plan or the last run)
+    if (bp.any_copy && (e = copy(0)) != cudaSuccess) return cuda_fail(e, "batch copy launch");
     int launches = 0;
     for_each_launch(iters, bp.steps, [&](int s, int src, int dst) {
         if (e != cudaSuccess) return;

@@ -49,9 +49,11 @@
 // so the arithmetic is identical to the single-step streaming kernel.
 //
 // Batches: a tile table lists (image, x0, y0) for every tile of every image; each image has a
-// descriptor with its buffers (f, u, workspace), pitch, size, update coefficients (its own
-// lambda and step) and one tensor map per buffer.  A launch reads every image from the buffer of
-// one role and writes the buffer of another, so all images advance T steps together.
+// descriptor with its buffers (f, u, two workspace images), pitches, size, update coefficients
+// (its own lambda and step) and one tensor map per buffer it reads.  A launch reads every image
+// from the buffer of one role and writes the buffer of another, so all images advance T steps
+// together; the launches between the first and the last ping-pong between the two workspace
+// images, so every buffer read has a pitch TMA can describe whatever the caller's pitch.
 #pragma once
 
 #include "wmc_window.cuh"
@@ -86,14 +88,20 @@ __host__ __device__ __forceinline__ int window_x0(int x0) {
     return (x0 - (T + 1)) & ~(Geom<S>::A - 1);  // floor to a multiple of A (also below 0)
 }
 
-// One image of a batch (device memory; 64-byte aligned for the tensor maps).
+// One image of a batch (device memory; 64-byte aligned for the tensor maps).  Every buffer a
+// launch reads (roles 0, 2, 3) has a pitch TMA can describe: when the caller's f does not, the
+// plan keeps an aligned copy of it in the workspace, refreshed at the start of every run.
 struct alignas(64) BatchImage {
-    CUtensorMap map[3];   // tensor maps over buf[0..2]
-    const void *buf[3];   // 0: f (read only), 1: u (output), 2: workspace image
-    int64_t ld;
+    CUtensorMap map[4];   // tensor maps over buf[0], buf[2], buf[3] (buf[1] is only written)
+    const void *buf[4];   // 0: f as read (the caller's f or its copy), 1: u (the caller's output),
+                          // 2, 3: workspace ping-pong images
+    const void *f_src;    // the caller's f
+    int64_t ld;           // pitch of buf[0], buf[2] and buf[3]
+    int64_t ld_out;       // pitch of u and f_src (the caller's)
     int32_t h, w;
     float c_keep, c_f, c_h;
-    int32_t use_tma[3];
+    int32_t use_tma[4];
+    int32_t copy_f;       // buf[0] is a workspace copy of f_src
 };
 
 struct TileParams {
@@ -101,7 +109,8 @@ struct TileParams {
     const void *u;    // U^t (device); read through the tensor map when use_tma
     const void *f;    // f or nullptr (mean-curvature flow)
     void *out;        // U^{t+T}
-    int64_t ld;       // pitch of u, f and out
+    int64_t ld;       // pitch of u and f
+    int64_t ld_out;   // pitch of out
     int32_t h, w;
     int32_t ntx;      // tiles per row of tiles
     int32_t use_tma;
@@ -409,10 +418,10 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW)
     tile_job<T, S, BND, NW>(jb, p.owt, p.oht, p.status, buf0, buf1, &bar, 0u, [&](int64_t *ldo) -> S * {
         if (BATCH) {
             const BatchImage &im = p.images[p.tiles[blockIdx.x].x];
-            *ldo = im.ld;
+            *ldo = p.dst_role == 1 ? im.ld_out : im.ld;
             return static_cast<S *>(const_cast<void *>(im.buf[p.dst_role]));
         }
-        *ldo = p.ld;
+        *ldo = p.ld_out;
         return static_cast<S *>(p.out);
     });
 }

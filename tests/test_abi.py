@@ -72,7 +72,13 @@ def test_workspace_sizes(lib):
     assert lib.wmc_denoise_workspace_size(3, 5, 8, 0) == 256 + 256
     assert lib.wmc_denoise_workspace_size(100, 100, 128, 1) == 256 + (100 * 128 * 2 + 255) // 256 * 256
     assert lib.wmc_denoise_workspace_size(4, 5, 4, 0) == 0  # ld < w
-    assert lib.wmc_denoise_host_workspace_size(10, 10, 10, 0) == 256 + 4 * 512
+    # pitches that are not a multiple of 16 bytes are staged: three images of the aligned pitch
+    # (FP32: a multiple of 4 elements; 16-bit: of 8), or one of pitch ld if that is larger
+    assert lib.wmc_denoise_workspace_size(10, 10, 10, 0) == 256 + 3 * 512  # pitch 12: 480 -> 512 B
+    assert lib.wmc_denoise_workspace_size(10, 10, 12, 0) == 256 + 512      # aligned: one image
+    assert lib.wmc_denoise_workspace_size(10, 10, 11, 1) == 256 + 3 * 512  # 16-bit, pitch 16: 320 -> 512 B
+    assert lib.wmc_denoise_workspace_size(2, 3, 201, 0) == 256 + (2 * 201 * 4 + 255) // 256 * 256
+    assert lib.wmc_denoise_host_workspace_size(10, 10, 10, 0) == 3 * 512 + 256 + 3 * 512
     assert lib.wmc_energy_workspace_size(10, 10) % 256 == 0
 
 

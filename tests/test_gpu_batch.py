@@ -116,3 +116,19 @@ def test_autotune_picks_a_candidate_and_the_plan_matches_single_images():
         assert torch.equal(o, wmc().denoise(f, l, st, 9, steps_per_launch=T, tile=tile))
     best, times = wmc().batch_autotune(fs, lams, steps, trial_iters=4)  # every default candidate
     assert len(times) == 12 and best in times
+
+
+def test_batch_rereads_f_on_every_run():
+    """Images whose pitch TMA cannot describe (widths that are not a multiple of 4 floats) are read
+    from an aligned copy of f in the plan's workspace; the copy is taken at the start of every run,
+    so a plan (or a graph of it) follows f when the caller changes it between runs."""
+    fs, lams, steps = batch_inputs(shapes=[(70, 101), (33, 40), (65, 130), (9, 7)], seed=7)
+    b = wmc().Batch(fs, lams, steps, steps_per_launch=4)
+    first = [o.clone() for o in b.run(9)]
+    for f, l, st, o in zip(fs, lams, steps, first):
+        assert torch.equal(o, wmc().denoise(f, l, st, 9, steps_per_launch=1))
+    for f in fs:
+        f.mul_(0.5).add_(0.25)
+    again = b.run(9)
+    for f, l, st, o in zip(fs, lams, steps, again):
+        assert torch.equal(o, wmc().denoise(f, l, st, 9, steps_per_launch=1)), f.shape

@@ -434,3 +434,21 @@ def test_overhanging_tiles_bitwise_invariant(bnd, shape):
     ref16 = wmc().denoise(bf, 1.0, 0.25, 11, bnd, steps_per_launch=1)
     for tile in (1, 2):
         assert torch.equal(wmc().denoise(bf, 1.0, 0.25, 11, bnd, steps_per_launch=4, tile=tile), ref16)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("iters", [5, 8, 13])
+def test_unaligned_pitch_is_staged_bit_exactly(dtype, iters):
+    """Rows whose pitch is not a multiple of 16 bytes (TMA cannot describe them) are staged through
+    aligned workspace images for the multi-step launches; the result must be the bits of the same
+    image stored with an aligned pitch, including a resume in place."""
+    h, w = 97, 131
+    img = synth.make_image(h, w, seed=28, sigma=0.08)
+    packed = to_gpu(img, dtype)                 # pitch 131: staged
+    wide = to_gpu(img, dtype, ld=136)           # pitch 136: read through TMA directly
+    a = wmc().denoise(packed, 1.0, 0.25, iters)
+    b = wmc().denoise(wide, 1.0, 0.25, iters)
+    assert torch.equal(a, b)
+    u = wmc().denoise(packed, 1.0, 0.25, 3)
+    wmc().denoise(packed, 1.0, 0.25, iters, u0=u, out=u)
+    assert torch.equal(u, wmc().denoise(wide, 1.0, 0.25, 3 + iters))
