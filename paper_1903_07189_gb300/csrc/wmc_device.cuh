@@ -50,6 +50,15 @@ __device__ __forceinline__ float select12(float L, float a1, float a2, float a5,
     return select12_ls(L, a1, a2, a5, a6, fmaf(0x1p-40f, a1, L));
 }
 
+// |H^w| alone (the energies): the least |t_j|, which is |select12(...)| bit for bit (equal
+// magnitudes are equal values), without the compare-select chain and the sign.
+__device__ __forceinline__ float abs_select12(float L, float a1, float a2, float a5, float a6) {
+    const float aL = fabsf(L);
+    const float m12 = fminf(fabsf(aL - fabsf(a1)), fabsf(aL - fabsf(a2)));
+    const float m56 = fminf(fabsf(aL - fabsf(a5)), fabsf(aL - fabsf(a6)));
+    return fminf(m12, m56);
+}
+
 // 12 * H^w at the centre of a 3x3 neighbourhood (rows: n* above, s* below).
 __device__ __forceinline__ float half_laplace12(float nw, float n, float ne, float w, float c,
                                                 float e, float sw, float s, float se) {
@@ -91,9 +100,13 @@ __device__ __forceinline__ float fd_wmc(float nw, float n, float ne, float w, fl
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 }
-__device__ __forceinline__ float2 half_laplace12_x2(float2 nw, float2 n, float2 ne, float2 w,
-                                                    float2 c, float2 e, float2 sw, float2 s,
-                                                    float2 se) {
+// The ×12 Laplacian and odd parts of two cells (the linear part of half_laplace12_x2).
+struct Terms2 {
+    float2 L, a1, a2, a5, a6;
+};
+__device__ __forceinline__ Terms2 half_laplace12_terms_x2(float2 nw, float2 n, float2 ne, float2 w,
+                                                          float2 c, float2 e, float2 sw, float2 s,
+                                                          float2 se) {
     const float2 two = make_float2(2.0f, 2.0f);
     const float2 m12 = make_float2(-12.0f, -12.0f);
     const float2 p = sub2(n, s);
@@ -102,14 +115,32 @@ __device__ __forceinline__ float2 half_laplace12_x2(float2 nw, float2 n, float2 
     const float2 B = sub2(ne, sw);
     const float2 corners = __fadd2_rn(__fadd2_rn(nw, se), __fadd2_rn(ne, sw));
     const float2 edges = __fadd2_rn(__fadd2_rn(n, s), __fadd2_rn(w, e));
-    const float2 L = __ffma2_rn(m12, c, __ffma2_rn(two, edges, corners));
-    const float2 a1 = __ffma2_rn(two, q, sub2(A, B));
-    const float2 a2 = __ffma2_rn(two, p, __fadd2_rn(A, B));
-    const float2 a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
-    const float2 a6 = __ffma2_rn(two, sub2(p, q), B);
+    Terms2 t;
+    t.L = __ffma2_rn(m12, c, __ffma2_rn(two, edges, corners));
+    t.a1 = __ffma2_rn(two, q, sub2(A, B));
+    t.a2 = __ffma2_rn(two, p, __fadd2_rn(A, B));
+    t.a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
+    t.a6 = __ffma2_rn(two, sub2(p, q), B);
+    return t;
+}
+
+// 12 |H^w| of two cells (abs_select12 per lane).
+__device__ __forceinline__ float2 abs_half_laplace12_x2(float2 nw, float2 n, float2 ne, float2 w,
+                                                        float2 c, float2 e, float2 sw, float2 s,
+                                                        float2 se) {
+    const Terms2 t = half_laplace12_terms_x2(nw, n, ne, w, c, e, sw, s, se);
+    return make_float2(abs_select12(t.L.x, t.a1.x, t.a2.x, t.a5.x, t.a6.x),
+                       abs_select12(t.L.y, t.a1.y, t.a2.y, t.a5.y, t.a6.y));
+}
+
+__device__ __forceinline__ float2 half_laplace12_x2(float2 nw, float2 n, float2 ne, float2 w,
+                                                    float2 c, float2 e, float2 sw, float2 s,
+                                                    float2 se) {
+    const Terms2 t = half_laplace12_terms_x2(nw, n, ne, w, c, e, sw, s, se);
     // the sign guard of select12 stays a scalar FMA per lane: one packed FMA for both lanes makes
     // each selection wait for the other lane's operands and measured 1.3 % slower
-    return make_float2(select12(L.x, a1.x, a2.x, a5.x, a6.x), select12(L.y, a1.y, a2.y, a5.y, a6.y));
+    return make_float2(select12(t.L.x, t.a1.x, t.a2.x, t.a5.x, t.a6.x),
+                       select12(t.L.y, t.a1.y, t.a2.y, t.a5.y, t.a6.y));
 }
 
 // ---------------------------------------------------------------- storage types

@@ -3,11 +3,16 @@
 //
 // The streaming evaluation kernel issues every load of its strip before computing, so the bytes
 // a thread has in flight bound it.  Here a persistent CTA (2 per SM) walks boxes of 128 x 64
-// output cells with two 136 x 66 window buffers in shared memory: while it computes one box the
-// TMA copy of its next box is already in flight, and no register holds those bytes.  The window
-// geometry, the ring refresh of REPLICATE border boxes, the bounded mbarrier waits and the lane
-// layout (columns j and j + 32 of one thread paired in packed FP32x2 arithmetic) are those of the
-// temporally blocked flow kernel, so every value equals the streaming kernel's bit for bit.
+// output cells through a three-stage pipeline of 136 x 66 window buffers in shared memory: while
+// it computes one box, the TMA copies of its next two boxes are in flight, and no register holds
+// those bytes.  Each buffer has a "full" mbarrier (the copy's bytes) and an "empty" one (one
+// arrival per warp once its lanes have read the box): every warp waits for its data itself and
+// releases the buffer when done, and thread 0 refills a buffer once all warps have released it,
+// so the warps do not wait for each other between boxes (only border boxes under REPLICATE,
+// whose ring refresh rewrites the window, take one CTA barrier).  The window geometry, the ring
+// refresh, the bounded mbarrier waits and the lane layout (columns j and j + 32 of one thread
+// paired in packed FP32x2 arithmetic) are those of the temporally blocked flow kernel, so every
+// value equals the streaming kernel's bit for bit.
 //
 // Box b covers image columns x0 = 128 (b mod nbx) .. x0 + 127 and rows y0 = 64 (b div nbx) ..
 // y0 + 63; its window starts at (X0, Y0) = (x0 - 4, y0 - 1): x0 - 4 keeps the TMA x coordinate on
@@ -29,8 +34,10 @@ struct EvalTmaParams {
 };
 
 constexpr int kEvalBoxW = 128, kEvalBoxH = 64;
-// buffer stride in floats, rounded so that the second buffer also starts on the 128-byte
-// boundary a TMA destination needs
+constexpr int kEvalStages = 3;
+constexpr int kEvalWarps = kTileThreadsV2 / 32;
+// buffer stride in floats, rounded so that every buffer starts on the 128-byte boundary a TMA
+// destination needs
 constexpr int kEvalBuf = (Geom<float>::LH * Geom<float>::P + 31) / 32 * 32;
 static_assert((kEvalBuf * 4) % 128 == 0, "TMA destinations must be 128-byte aligned");
 constexpr int kEvalX = 4;  // window column of output column x0 (and window row 1 of row y0)
@@ -39,14 +46,16 @@ template <int BND>
 __global__ void __launch_bounds__(kTileThreadsV2, 2)
     eval_tma_kernel(const __grid_constant__ CUtensorMap tmap, const EvalTmaParams p) {
     using G = Geom<float>;
-    constexpr int P = G::P, LW = G::LW, LH = G::LH, BUF = kEvalBuf;
+    constexpr int P = G::P, LW = G::LW, LH = G::LH, BUF = kEvalBuf, NS = kEvalStages;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS];
+    __shared__ int abort_flag;
     float *buf0 = reinterpret_cast<float *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = kEvalX + 64 * (warp & 1) + lane;  // window column of the thread's first cell
     const int ib = 1 + kRY * (warp >> 1);           // window row of its first row
     const int h = p.h, w = p.w;
+    const int stride = gridDim.x;
     auto box_xy = [&](int b, int &X0, int &Y0) {
         const int by = b / p.nbx, bx = b - by * p.nbx;
         X0 = bx * kEvalBoxW - kEvalX;
@@ -56,62 +65,86 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
         int X0, Y0;
         box_xy(b, X0, Y0);
         fence_proxy_async_smem();
-        mbar_expect_tx(smem_u32(&bar[k]), (uint32_t)(LW * LH * 4));
-        tma_load_2d(smem_u32(buf0 + k * BUF), &tmap, X0, Y0, smem_u32(&bar[k]));
+        mbar_expect_tx(smem_u32(&full[k]), (uint32_t)(LW * LH * 4));
+        tma_load_2d(smem_u32(buf0 + k * BUF), &tmap, X0, Y0, smem_u32(&full[k]));
     };
+    // thread 0's copies in flight: bit k of `pending` is set while stage k's copy has not been
+    // waited for by it, bit k of `pparity` holds that copy's phase parity (a stage has at most
+    // one copy in flight: it is refilled only after its previous copy was waited for)
+    unsigned pending = 0, pparity = 0;
     if (tid == 0) {
-        mbar_init(smem_u32(&bar[0]), 1);
-        mbar_init(smem_u32(&bar[1]), 1);
-        if ((int)blockIdx.x < p.nboxes) issue(blockIdx.x, 0);
-        if ((int)(blockIdx.x + gridDim.x) < p.nboxes) issue(blockIdx.x + gridDim.x, 1);
+        abort_flag = 0;
+        for (int k = 0; k < NS; ++k) {
+            mbar_init(smem_u32(&full[k]), 1);
+            mbar_init(smem_u32(&empty[k]), kEvalWarps);
+        }
+        for (int k = 0; k < NS; ++k)
+            if ((int)blockIdx.x + k * stride < p.nboxes) {
+                issue(blockIdx.x + k * stride, k);
+                pending |= 1u << k;  // use k of stage k: phase parity 0
+            }
     }
+    __syncthreads();  // the barriers are initialised before anyone waits on them
     const float2 sc = make_float2(p.scale, p.scale);
     int n = 0;
-    for (int b = blockIdx.x; b < p.nboxes; b += gridDim.x, ++n) {
-        const int k = n & 1;
-        const uint32_t phase = (uint32_t)(n >> 1) & 1u;
+    for (int b = blockIdx.x; b < p.nboxes; b += stride, ++n) {
+        const int k = n % NS;
+        const uint32_t phase = (uint32_t)(n / NS) & 1u;
         float *buf = buf0 + k * BUF;
-        // thread 0 waits for the copy (its completion makes the data visible to it); the CTA
-        // barrier then orders everyone's reads after that
-        const bool ok = (tid != 0) || mbar_wait_bounded(smem_u32(&bar[k]), phase, kWaitLimitNs);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(&g_eval_status, 1u);
-                // copies may still be in flight into either buffer: wait for them (bounded)
-                // before the CTA's shared memory goes away
-                mbar_wait_bounded(smem_u32(&bar[k]), phase, kWaitLimitNs);
-                if ((int)(b + gridDim.x) < p.nboxes)
-                    mbar_wait_bounded(smem_u32(&bar[k ^ 1]), (uint32_t)((n + 1) >> 1) & 1u, kWaitLimitNs);
-            }
-            return;
-        }
+        // every thread waits for the copy itself (its completion makes the data visible)
+        bool ok = !*static_cast<volatile int *>(&abort_flag) &&
+                  mbar_wait_bounded(smem_u32(&full[k]), phase, kWaitLimitNs);
+        if (tid == 0 && ok) pending &= ~(1u << k);
+        if (!ok) *static_cast<volatile int *>(&abort_flag) = 1;
         int X0, Y0;
         box_xy(b, X0, Y0);
         const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
-        if (BND == BND_REPLICATE && border) {
-            refresh_ring<float>(buf, X0, Y0, h, w, tid);
+        if (BND == BND_REPLICATE && border) {  // the same decision in every thread of the CTA
+            const bool bad = __syncthreads_or(!ok);
+            if (!bad) refresh_ring<float>(buf, X0, Y0, h, w, tid);
             __syncthreads();
+            ok = !bad;
         }
-        // the thread's 8 rows x 2 columns, packed FP32x2, stored where they lie in the image
-        const int gx = X0 + j;
-        const bool c0 = gx < w, c1 = gx + 32 < w;  // gx >= 0 always (X0 + 4 >= 0)
-        const float *rp = buf + (ib - 1) * P + j;
-        Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
-        float *orow = p.out + (int64_t)(Y0 + ib) * p.ldo + gx;
+        if (ok) {
+            // the thread's 8 rows x 2 columns, packed FP32x2, stored where they lie in the image
+            const int gx = X0 + j;
+            const bool c0 = gx < w, c1 = gx + 32 < w;  // gx >= 0 always (X0 + 4 >= 0)
+            const float *rp = buf + (ib - 1) * P + j;
+            Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
+            float *orow = p.out + (int64_t)(Y0 + ib) * p.ldo + gx;
 #pragma unroll
-        for (int r = 0; r < kRY; ++r) {
-            const Row3 r2 = load_row3(rp + (r + 2) * P);
-            const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
-            const float2 o = __fmul2_rn(sc, hw);
-            const bool rin = Y0 + ib + r < h;
-            float *q = orow + (int64_t)r * p.ldo;
-            if (rin & c0) q[0] = o.x;
-            if (rin & c1) q[32] = o.y;
-            r0 = r1;
-            r1 = r2;
+            for (int r = 0; r < kRY; ++r) {
+                const Row3 r2 = load_row3(rp + (r + 2) * P);
+                const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+                const float2 o = __fmul2_rn(sc, hw);
+                const bool rin = Y0 + ib + r < h;
+                float *q = orow + (int64_t)r * p.ldo;
+                if (rin & c0) q[0] = o.x;
+                if (rin & c1) q[32] = o.y;
+                r0 = r1;
+                r1 = r2;
+            }
         }
-        __syncthreads();  // every thread is done with this buffer
-        if (tid == 0 && (int)(b + 2 * gridDim.x) < p.nboxes) issue(b + 2 * gridDim.x, k);
+        // release the buffer: one arrival per warp, after all its lanes have read the box
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty[k]));
+        // thread 0 refills it with its box after next once every warp has released it
+        if (tid == 0 && b + NS * stride < p.nboxes) {
+            if (!*static_cast<volatile int *>(&abort_flag) &&
+                mbar_wait_bounded(smem_u32(&empty[k]), phase, kWaitLimitNs)) {
+                issue(b + NS * stride, k);
+                pending |= 1u << k;
+                pparity = (pparity & ~(1u << k)) | ((((uint32_t)(n / NS) + 1u) & 1u) << k);  // use n + NS
+            } else {
+                *static_cast<volatile int *>(&abort_flag) = 1;
+            }
+        }
+    }
+    if (tid == 0) {
+        if (*static_cast<volatile int *>(&abort_flag)) atomicOr(&g_eval_status, 1u);
+        // copies still in flight (after a timeout) land before the CTA's shared memory goes away
+        for (int k = 0; k < NS; ++k)
+            if (pending & (1u << k)) mbar_wait_bounded(smem_u32(&full[k]), (pparity >> k) & 1u, kWaitLimitNs);
     }
 }
 
@@ -139,7 +172,7 @@ cudaError_t launch_eval_tma(const CUtensorMap *map, float *out, int64_t ldo, int
         if (e != cudaSuccess) return e;
         sms[dev & 63].store(nsm, std::memory_order_relaxed);
     }
-    const int smem = 2 * kEvalBuf * 4 + 128;
+    const int smem = kEvalStages * kEvalBuf * 4 + 128;
     const uint64_t bit = 1ull << (dev & 63);
     if (!(attr_set.load(std::memory_order_acquire) & bit)) {
         e = cudaFuncSetAttribute(eval_tma_kernel<BND_ZERO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

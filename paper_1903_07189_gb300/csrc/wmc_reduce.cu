@@ -359,20 +359,26 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 2)
 // FP32 images that TMA can read: persistent CTAs (one per SM, 512 threads) walk boxes of 128 x 64
 // cells.  A buffer holds U's 136 x 66 window (origin (x0 - 4, y0 - 1), the flow kernel's, ring
 // refreshed for REPLICATE border boxes) and dense 128 x 64 boxes of f and clean; two buffers per
-// CTA, so the next box's copies are in flight while the current box is summed.  A thread takes
-// columns j and j + 32 of 8 rows (the packed FP32x2 stencil), sums its 16 cells in FP32 per box
-// and adds those sums into its double-float accumulators.  A window wait that runs out turns the
-// CTA's partial sums into NaN (after a bounded wait for its copies in flight), so the energies come
-// out NaN instead of wrong.
+// CTA, each with a "full" mbarrier (the copies' bytes) and an "empty" one (one arrival per warp
+// once it has read the box), so the next box's copies are in flight while the current box is
+// summed and the warps do not wait for each other between boxes (border boxes under REPLICATE
+// take one CTA barrier for the ring refresh).  A thread takes columns j and j + 32 of 8 rows
+// (the packed FP32x2 stencil, the magnitude of the selection only), sums its 16 cells in FP32 per
+// box and adds those sums into its double-float accumulators.  (1024 threads of 4 rows each,
+// for more warps per SM, measured slower: 54.8 against 44.5 us at 4096^2.)  A window wait that runs out turns
+// the CTA's partial sums into NaN (after a bounded wait for its copies in flight), so the
+// energies come out NaN instead of wrong.
 constexpr int kEUBuf = (Geom<float>::LH * Geom<float>::P + 31) / 32 * 32;  // U window, floats
 constexpr int kEFBuf = kEBoxW * kEBoxH;                                     // f or clean box
+constexpr int kEThreads = 512, kERY = 8, kEWarps = kEThreads / 32;
 static_assert((kEUBuf * 4) % 128 == 0 && (kEFBuf * 4) % 128 == 0, "TMA destinations 128-byte aligned");
+static_assert(kERY * (kEWarps / 2) == kEBoxH, "2 warps across, kEWarps / 2 warps down cover a box");
 
 template <bool HF, bool HC>
 __host__ __device__ constexpr int energy_tma_buf() { return kEUBuf + (HF ? kEFBuf : 0) + (HC ? kEFBuf : 0); }
 
 template <int BND, bool HF, bool HC>
-__global__ void __launch_bounds__(kTileThreadsV2, 1)
+__global__ void __launch_bounds__(kEThreads, 1)
     energy_tma_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap fmap,
                       const __grid_constant__ CUtensorMap cmap, int h, int w, double *__restrict__ out,
                       double *__restrict__ partials, unsigned int *__restrict__ ticket) {
@@ -380,88 +386,115 @@ __global__ void __launch_bounds__(kTileThreadsV2, 1)
     constexpr int P = G::P, LW = G::LW, LH = G::LH, NB = energy_tma_buf<HF, HC>();
     constexpr uint32_t BYTES = (uint32_t)(LW * LH + (HF ? kEFBuf : 0) + (HC ? kEFBuf : 0)) * 4u;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
+    __shared__ int abort_flag;
     float *buf0 = reinterpret_cast<float *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int j = 4 + 64 * (warp & 1) + lane;  // window column of the thread's first cell
-    const int ib = 1 + kRY * (warp >> 1);       // window row of its first row
+    const int ib = 1 + kERY * (warp >> 1);      // window row of its first row
     const int nbx = (w + kEBoxW - 1) / kEBoxW;
     const int nboxes = nbx * ((h + kEBoxH - 1) / kEBoxH);
+    const int stride = gridDim.x;
     auto issue = [&](int b, int k) {  // thread 0: the copies of box b into buffer k
         const int by = b / nbx, bx = b - by * nbx;
         float *bk = buf0 + k * NB;
         fence_proxy_async_smem();
-        mbar_expect_tx(smem_u32(&bar[k]), BYTES);
-        tma_load_2d(smem_u32(bk), &umap, bx * kEBoxW - 4, by * kEBoxH - 1, smem_u32(&bar[k]));
-        if (HF) tma_load_2d(smem_u32(bk + kEUBuf), &fmap, bx * kEBoxW, by * kEBoxH, smem_u32(&bar[k]));
+        mbar_expect_tx(smem_u32(&full[k]), BYTES);
+        tma_load_2d(smem_u32(bk), &umap, bx * kEBoxW - 4, by * kEBoxH - 1, smem_u32(&full[k]));
+        if (HF) tma_load_2d(smem_u32(bk + kEUBuf), &fmap, bx * kEBoxW, by * kEBoxH, smem_u32(&full[k]));
         if (HC)
             tma_load_2d(smem_u32(bk + kEUBuf + (HF ? kEFBuf : 0)), &cmap, bx * kEBoxW, by * kEBoxH,
-                        smem_u32(&bar[k]));
+                        smem_u32(&full[k]));
     };
+    // thread 0's copies in flight (bit k of `pending`) and their phase parities (`pparity`)
+    unsigned pending = 0, pparity = 0;
     if (tid == 0) {
-        mbar_init(smem_u32(&bar[0]), 1);
-        mbar_init(smem_u32(&bar[1]), 1);
-        if ((int)blockIdx.x < nboxes) issue(blockIdx.x, 0);
-        if ((int)(blockIdx.x + gridDim.x) < nboxes) issue(blockIdx.x + gridDim.x, 1);
+        abort_flag = 0;
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(smem_u32(&full[k]), 1);
+            mbar_init(smem_u32(&empty[k]), kEWarps);
+        }
+        for (int k = 0; k < 2; ++k)
+            if ((int)blockIdx.x + k * stride < nboxes) {
+                issue(blockIdx.x + k * stride, k);
+                pending |= 1u << k;
+            }
     }
+    __syncthreads();  // the barriers are initialised before anyone waits on them
+    volatile int *abort_v = &abort_flag;
     DF acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     int n = 0;
-    for (int b = blockIdx.x; b < nboxes; b += gridDim.x, ++n) {
+    for (int b = blockIdx.x; b < nboxes; b += stride, ++n) {
         const int k = n & 1;
         const uint32_t phase = (uint32_t)(n >> 1) & 1u;
         const float *bu = buf0 + k * NB;
         const float *bf = bu + kEUBuf, *bc = bu + kEUBuf + (HF ? kEFBuf : 0);
-        const bool ok = (tid != 0) || mbar_wait_bounded(smem_u32(&bar[k]), phase, kWaitLimitNs);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {  // copies may still be in flight into either buffer
-                mbar_wait_bounded(smem_u32(&bar[k]), phase, kWaitLimitNs);
-                if ((int)(b + gridDim.x) < nboxes)
-                    mbar_wait_bounded(smem_u32(&bar[k ^ 1]), (uint32_t)((n + 1) >> 1) & 1u, kWaitLimitNs);
-            }
-            const float nan = __int_as_float(0x7fc00000);
-            for (int q = 0; q < 3; ++q) acc[q] = {nan, 0.f};
-            break;
-        }
+        bool ok = !*abort_v && mbar_wait_bounded(smem_u32(&full[k]), phase, kWaitLimitNs);
+        if (tid == 0 && ok) pending &= ~(1u << k);
+        if (!ok) *abort_v = 1;
         const int by = b / nbx, bx = b - by * nbx;
         const int X0 = bx * kEBoxW - 4, Y0 = by * kEBoxH - 1;
         const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
-        if (BND == BND_REPLICATE && border) {
-            refresh_ring<float>(const_cast<float *>(bu), X0, Y0, h, w, tid);
+        if (BND == BND_REPLICATE && border) {  // the same decision in every thread of the CTA
+            const bool bad = __syncthreads_or(!ok);
+            if (!bad) refresh_ring<float, G::LH, kEThreads>(const_cast<float *>(bu), X0, Y0, h, w, tid);
             __syncthreads();
+            ok = !bad;
         }
-        const int gx = X0 + j;
-        const bool c0 = gx < w, c1 = gx + 32 < w;
-        const float *rp = bu + (ib - 1) * P + j;
-        const int fo = (ib - 1) * kEBoxW + (j - 4);  // box offset of the thread's first cell
-        Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
-        float s[3] = {0.f, 0.f, 0.f};
+        if (ok) {
+            const int gx = X0 + j;
+            const bool c0 = gx < w, c1 = gx + 32 < w;
+            const float *rp = bu + (ib - 1) * P + j;
+            const int fo = (ib - 1) * kEBoxW + (j - 4);  // box offset of the thread's first cell
+            Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
+            float s[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int r = 0; r < kRY; ++r) {
-            const Row3 r2 = load_row3(rp + (r + 2) * P);
-            const float2 h12 = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
-            const bool rin = Y0 + ib + r < h;
-            const bool in0 = rin & c0, in1 = rin & c1;
-            if (in0) s[0] += fabsf(h12.x);
-            if (in1) s[0] += fabsf(h12.y);
-            if (HF) {
-                const float d0 = r1.c.x - bf[fo + r * kEBoxW], d1 = r1.c.y - bf[fo + r * kEBoxW + 32];
-                if (in0) s[1] = fmaf(d0, d0, s[1]);
-                if (in1) s[1] = fmaf(d1, d1, s[1]);
+            for (int r = 0; r < kERY; ++r) {
+                const Row3 r2 = load_row3(rp + (r + 2) * P);
+                const float2 a12 = abs_half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+                const bool rin = Y0 + ib + r < h;
+                const bool in0 = rin & c0, in1 = rin & c1;
+                if (in0) s[0] += a12.x;
+                if (in1) s[0] += a12.y;
+                if (HF) {
+                    const float d0 = r1.c.x - bf[fo + r * kEBoxW], d1 = r1.c.y - bf[fo + r * kEBoxW + 32];
+                    if (in0) s[1] = fmaf(d0, d0, s[1]);
+                    if (in1) s[1] = fmaf(d1, d1, s[1]);
+                }
+                if (HC) {
+                    const float d0 = r1.c.x - bc[fo + r * kEBoxW], d1 = r1.c.y - bc[fo + r * kEBoxW + 32];
+                    if (in0) s[2] = fmaf(d0, d0, s[2]);
+                    if (in1) s[2] = fmaf(d1, d1, s[2]);
+                }
+                r0 = r1;
+                r1 = r2;
             }
-            if (HC) {
-                const float d0 = r1.c.x - bc[fo + r * kEBoxW], d1 = r1.c.y - bc[fo + r * kEBoxW + 32];
-                if (in0) s[2] = fmaf(d0, d0, s[2]);
-                if (in1) s[2] = fmaf(d1, d1, s[2]);
-            }
-            r0 = r1;
-            r1 = r2;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) df_add(acc[q], s[q]);
         }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) df_add(acc[q], s[q]);
-        __syncthreads();  // every thread is done with this buffer
-        if (tid == 0 && (int)(b + 2 * gridDim.x) < nboxes) issue(b + 2 * gridDim.x, k);
+        // release the buffer: one arrival per warp, after all its lanes have read the box
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty[k]));
+        // thread 0 refills it with its box after next once every warp has released it
+        if (tid == 0 && b + 2 * stride < nboxes) {
+            if (!*abort_v && mbar_wait_bounded(smem_u32(&empty[k]), phase, kWaitLimitNs)) {
+                issue(b + 2 * stride, k);
+                pending |= 1u << k;
+                pparity = (pparity & ~(1u << k)) | ((((uint32_t)(n >> 1) + 1u) & 1u) << k);
+            } else {
+                *abort_v = 1;
+            }
+        }
     }
-    energy_reduce<kTileThreadsV2 / 32>(acc, out, partials, ticket);
+    if (tid == 0)  // copies still in flight (after a timeout) land before the CTA's shared memory goes away
+        for (int k = 0; k < 2; ++k)
+            if (pending & (1u << k)) mbar_wait_bounded(smem_u32(&full[k]), (pparity >> k) & 1u, kWaitLimitNs);
+    __syncthreads();
+    if (*abort_v) {  // the energies come out NaN instead of wrong
+        const float nan = __int_as_float(0x7fc00000);
+        for (int q = 0; q < 3; ++q) acc[q] = {nan, 0.f};
+    }
+    energy_reduce<kEWarps>(acc, out, partials, ticket);
 }
 
 void energy_tma_box(int *bw, int *bh) {
@@ -475,7 +508,7 @@ cudaError_t launch_energy_tma(const CUtensorMap *maps, bool has_f, bool has_clea
     double *partials = reinterpret_cast<double *>(static_cast<char *>(ws) + 256);
     cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    const unsigned g = (unsigned)energy_tma_grid(h, w), b = kTileThreadsV2;
+    const unsigned g = (unsigned)energy_tma_grid(h, w), b = kEThreads;
     // one shared-memory size for every instance: two buffers of the largest kind
     const int smem = 2 * energy_tma_buf<true, true>() * 4 + 128;
     int dev = 0;
