@@ -206,7 +206,7 @@ template <typename S> struct TileJob {
 // write the output tile through `out_of()` (called after the steps, so the output pointer is not
 // kept in registers through them).  `phase` is the mbarrier parity this tile's load completes.
 // Returns false if the window load timed out (the status word is set).
-template <int T, typename S, int BND, int NW, typename OutFn>
+template <int T, typename S, int BND, int NW, bool UNROLL, typename OutFn>
 __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht, unsigned int *status,
                                          float *buf0, float *buf1, uint64_t *bar, uint32_t phase,
                                          OutFn out_of) {
@@ -338,8 +338,7 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     // any in-image cell reads, so it skips the arithmetic (it still takes part in the barriers).
     const int lane0 = c.gx - lane;
     const bool idle = (Y0 + c.ib >= h + 1) | (lane0 >= w + 1);
-#pragma unroll 1
-    for (int s = 0; s < T - 1; ++s) {
+    auto one_step = [&](int s) {
         const float *src = (s & 1) ? buf1 : buf0;
         float *dst = (s & 1) ? buf0 : buf1;
         if (!border) {
@@ -353,6 +352,16 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
                 __syncthreads();
             }
         }
+    };
+    // Single images unroll the T - 1 steps (T is a template parameter): 2.3 % faster at 4096^2
+    // than a loop, whose pointer selection and back edge each step paid.  The batch kernel keeps
+    // the loop: unrolled, its descriptor state spills.
+    if constexpr (UNROLL) {
+#pragma unroll
+        for (int s = 0; s < T - 1; ++s) one_step(s);
+    } else {
+#pragma unroll 1
+        for (int s = 0; s < T - 1; ++s) one_step(s);
     }
     if (idle) return true;  // none of its cells is an output cell inside the image
     int64_t ldo;
@@ -415,7 +424,7 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW)
     if (jb.use_tma && threadIdx.x == 0) mbar_init(smem_u32(&bar), 1);
     // the output pointer is looked up again after the steps (kernel parameters, or the image
     // descriptor in L1) rather than kept in registers through them
-    tile_job<T, S, BND, NW>(jb, p.owt, p.oht, p.status, buf0, buf1, &bar, 0u, [&](int64_t *ldo) -> S * {
+    tile_job<T, S, BND, NW, !BATCH>(jb, p.owt, p.oht, p.status, buf0, buf1, &bar, 0u, [&](int64_t *ldo) -> S * {
         if (BATCH) {
             const BatchImage &im = p.images[p.tiles[blockIdx.x].x];
             *ldo = p.dst_role == 1 ? im.ld_out : im.ld;
