@@ -326,7 +326,8 @@ def measure_pr1(wmc, dev, reps=50):
     n = f.numel()
     ws = torch.empty(wmc.load().wmc_denoise_workspace_size(256, 256, 256, 0), dtype=torch.uint8, device=dev)
     res = {}
-    for T in (DEFAULT_T, 8):
+    ctas = wmc.cluster_size(256, 256, 100, dev)
+    for T in (DEFAULT_T, 8, 0):
         def run():
             wmc.eval(f, out=hw)
             wmc.denoise(f, 1.0, 0.25, 100, out=out, steps_per_launch=T, workspace=ws)
@@ -343,10 +344,15 @@ def measure_pr1(wmc, dev, reps=50):
             run()
         g.replay()
         t_graph = event_ms(g.replay, reps)
-        launches = 1 + math.ceil(100 / T)
-        res[f"T{T}"] = {"plain_us": 1e3 * t_plain, "graph_us": 1e3 * t_graph, "launches": launches,
-                        "plain_gpix_iter_s": n * 100 / (t_plain * 1e-3) / 1e9,
-                        "graph_gpix_iter_s": n * 100 / (t_graph * 1e-3) / 1e9}
+        # the default configuration runs the 100 iterations as one cluster launch (when the
+        # device schedules a cluster of `ctas` CTAs)
+        launches = 1 + (1 if (T == 0 and ctas) else math.ceil(100 / (T or DEFAULT_T)))
+        key = f"T{T}" if T else "default"
+        res[key] = {"plain_us": 1e3 * t_plain, "graph_us": 1e3 * t_graph, "launches": launches,
+                    "plain_gpix_iter_s": n * 100 / (t_plain * 1e-3) / 1e9,
+                    "graph_gpix_iter_s": n * 100 / (t_graph * 1e-3) / 1e9}
+        if T == 0:
+            res[key]["cluster_ctas"] = ctas
     return {"workload": "256x256 f32 (seed 0, 8 bumps + 4 shapes, sigma 0.05): 1 eval + 100 iterations, "
                         "lambda 1, step 0.25, replicate", "runs": reps, **res}
 

@@ -120,6 +120,10 @@ wmc_status_t wmc_eval_status(wmc_stream_t stream);
  *   holds three images of the next aligned pitch, the call copies U^0 and f into two of them,
  *   the launches ping-pong in the workspace and only the last one writes u.
  *   Sides up to 2^24 pixels.
+ *   Small images (h <= 256, w <= 256) with iters >= 2 under the default configuration run all
+ *   their iterations in ONE launch of one thread-block cluster of ceil(h / 16) CTAs that keep the
+ *   image in shared memory (see wmc_denoise_cluster_size); only the status word of the workspace
+ *   is then used.  The result is the same bits as the multi-launch path's.
  * Errors: WMC_ERR_INVALID_ARG, WMC_ERR_ALIAS, WMC_ERR_WORKSPACE, WMC_ERR_CUDA.
  */
 size_t wmc_denoise_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype);
@@ -128,6 +132,13 @@ wmc_status_t wmc_denoise(const void *f, const void *u0, void *u, int32_t h, int3
                          wmc_dtype_t dtype, float lambda, float step, int32_t iters,
                          wmc_boundary_t bnd, void *workspace, size_t workspace_bytes,
                          wmc_stream_t stream);
+
+/* wmc_denoise_cluster_size: the number of CTAs of the one-launch cluster path that wmc_denoise,
+ * wmc_denoise_host and wmc_denoise_noalloc (and wmc_denoise_ex with a NULL or all-zero config)
+ * take for an h x w image and `iters` iterations on the current device; 0 when they take the
+ * multi-launch path (image larger than 256 x 256, iters < 2, or no such cluster can be scheduled
+ * on the device).  Any dtype, either boundary.  Errors: none (negative sizes give 0). */
+int32_t wmc_denoise_cluster_size(int32_t h, int32_t w, int32_t iters);
 
 /* As wmc_denoise, with an explicit kernel configuration (NULL = defaults). */
 wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, int32_t w,

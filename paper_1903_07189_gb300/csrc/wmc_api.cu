@@ -158,6 +158,8 @@ constexpr int kDefaultTile = 1;
 constexpr int kTileShapes = 2;  // wmc_config_t.tile = 1 .. kTileShapes (0: kDefaultTile)
 
 constexpr int kDefaultSteps = 4;
+// Fewest iterations for which the default configuration runs a small image as one cluster launch
+constexpr int kClusterMinIters = 2;
 constexpr size_t kStatusBytes = WMC_WORKSPACE_ALIGN;
 
 size_t image_bytes(int32_t h, int64_t ld, wmc_dtype_t dtype) {
@@ -180,7 +182,7 @@ int64_t aligned_pitch(int32_t w, size_t es) {
 wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
                       wmc_dtype_t dtype, float lambda, float step, int32_t iters,
                       wmc_boundary_t bnd, int steps_per_launch, void *ws, cudaStream_t st,
-                      bool fd = false, int tile = kDefaultTile) {
+                      bool fd = false, int tile = kDefaultTile, bool default_config = false) {
     const size_t es = elem_size(dtype);
     if (!u0) u0 = f;
     if (h == 0 || w == 0) return WMC_OK;
@@ -194,14 +196,25 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
     }
     unsigned int *status = static_cast<unsigned int *>(ws);
     ws = static_cast<char *>(ws) + kStatusBytes;
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned int), st);
+    const float mu = f ? 1.0f : 0.0f;
+    const float c_keep = 1.0f - step * mu, c_f = step * mu;
+    const float c_h = fd ? step * lambda : step * lambda / 12.0f;
+    cudaError_t e;
+    // Small images under the default configuration: all the iterations in one cluster launch
+    // (it clears the status word itself and needs no workspace image)
+    if (!fd && default_config && iters >= kClusterMinIters) {
+        const int ctas = wmc::cluster_ctas(h, w);
+        if (ctas > 0 && wmc::cluster_fits(ctas)) {
+            e = wmc::launch_flow_cluster((int)dtype, (int)bnd, u0, f, u, status, ld, ld, h, w, iters, c_keep,
+                                         c_f, c_h, st);
+            return e == cudaSuccess ? WMC_OK : cuda_fail(e, "cluster flow kernel launch");
+        }
+    }
+    e = cudaMemsetAsync(status, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return cuda_fail(e, "clear status");
 
     const int T = fd ? 1 : steps_per_launch;  // the finite-difference comparator streams
     const int nl = (iters + T - 1) / T;  // launches; the last takes the remainder
-    const float mu = f ? 1.0f : 0.0f;
-    const float c_keep = 1.0f - step * mu, c_f = step * mu;
-    const float c_h = fd ? step * lambda : step * lambda / 12.0f;
     // Buffers: launch k reads src_k (pitch ld_in) and writes dst_k (pitch ld_out on the last
     // launch, ld_in otherwise); f_read is the f the launches read.
     const bool staged = T > 1 && nl > 1 && staged_pitch(ld, es);
@@ -307,7 +320,7 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
 wmc_status_t check_flow_args(const void *f, const void *u0, void *u, int32_t h, int32_t w,
                              int64_t ld, wmc_dtype_t dtype, float lambda, float step,
                              int32_t iters, wmc_boundary_t bnd, const wmc_config_t *cfg,
-                             int *steps_out, int *tile_out = nullptr) {
+                             int *steps_out, int *tile_out = nullptr, bool *default_out = nullptr) {
     wmc_status_t s;
     if ((s = check_enums(dtype, bnd)) != WMC_OK) return s;
     if ((s = check_image(h, w, ld, "image")) != WMC_OK) return s;
@@ -327,6 +340,7 @@ wmc_status_t check_flow_args(const void *f, const void *u0, void *u, int32_t h, 
     }
     *steps_out = T;
     if (tile_out) *tile_out = (cfg && cfg->tile > 0) ? cfg->tile : kDefaultTile;
+    if (default_out) *default_out = !cfg || (cfg->steps_per_launch == 0 && cfg->tile == 0);
     if (h > 0 && w > 0) {
         if (!u) return fail(WMC_ERR_INVALID_ARG, "u is NULL");
         if (!f && !u0) return fail(WMC_ERR_INVALID_ARG, "f and u0 are both NULL");
@@ -686,8 +700,9 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
                             void *workspace, size_t workspace_bytes, wmc_stream_t stream) {
     g_last_error[0] = 0;
     int T = 0, tile = kDefaultTile;
+    bool dflt = false;
     wmc_status_t s =
-        check_flow_args(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, config, &T, &tile);
+        check_flow_args(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, config, &T, &tile, &dflt);
     if (s != WMC_OK) return s;
     if (h == 0 || w == 0) return WMC_OK;
     if (iters > 0) {
@@ -703,7 +718,14 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
             return fail(WMC_ERR_ALIAS, "workspace overlaps an image");
     }
     return run_flow(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, T, workspace,
-                    (cudaStream_t)stream, false, tile);
+                    (cudaStream_t)stream, false, tile, dflt);
+}
+
+int32_t wmc_denoise_cluster_size(int32_t h, int32_t w, int32_t iters) {
+    g_last_error[0] = 0;
+    if (iters < kClusterMinIters) return 0;
+    const int ctas = wmc::cluster_ctas(h, w);
+    return (ctas > 0 && wmc::cluster_fits(ctas)) ? ctas : 0;
 }
 
 wmc_status_t wmc_denoise_fd(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
@@ -780,7 +802,8 @@ wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_h
     if (d_u0 && (e = cudaMemcpy2DAsync(d_u0, pitch, u0_host, pitch, w * es, h,
                                        cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "copy u0 to device");
-    s = run_flow(d_f, d_u0, d_u, h, w, ld, dtype, lambda, step, iters, bnd, T, d_ws, st);
+    s = run_flow(d_f, d_u0, d_u, h, w, ld, dtype, lambda, step, iters, bnd, T, d_ws, st, false,
+                 kDefaultTile, true);
     if (s != WMC_OK) return s;
     if ((e = cudaMemcpy2DAsync(u_host, pitch, d_u, pitch, w * es, h, cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
@@ -1362,7 +1385,7 @@ wmc_status_t wmc_denoise_noalloc(const void *f, const void *u0, void *u, int32_t
     // run_flow clears the status word at the start of every call; nothing else in the scratch
     // needs a defined value (the ping-pong image is always written before it is read)
     return run_flow(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, T, scratch,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, false, kDefaultTile, true);
 }
 
 wmc_status_t wmc_denoise_noalloc_status(wmc_stream_t stream) {

@@ -1,0 +1,288 @@
+// wmc_cluster.cu -- the whole WMC flow (Sec. V-B, Eq. MCF) of a small image in ONE launch: one
+// thread-block cluster whose CTAs keep the image in their shared memory for all the iterations.
+//
+// A small image (PR1: 256 x 256) is bound by latency, not by bytes or arithmetic: a launch per few
+// Jacobi steps covers it with a handful of CTAs, so most of the time goes to each launch's load
+// and the serial steps of one CTA.  Here a cluster of C <= 16 CTAs (one per SM) splits the image
+// into bands of kCRows rows; CTA r keeps rows [kCRows r, kCRows (r + 1)) plus one halo row above
+// and below in two ping-pong buffers in shared memory, and f's term in registers.  Every step it
+// computes its band from one buffer into the other; the threads that compute a band's first and
+// last rows also store those values into the neighbouring CTAs' halo rows, through distributed
+// shared memory, and one cluster barrier per step (release / acquire) makes them visible before
+// the next step reads them.  The arithmetic is the tile kernel's (the packed pair stencil of
+// half_laplace12_x2, the same update and storage rounding), so the result is the same bits.
+//
+// Image boundary.  ZERO: the ring of cells just outside the image starts at 0 and is never
+// written.  REPLICATE: a cell on the image's edge also writes its new value into the ring cells
+// that replicate it (the row above or below, the column left or right, the corner), in its own
+// CTA or, for a band's halo row, in the neighbour's; cells outside the image are never written.
+//
+// Threads: 16 warps as 4 column groups x 4 row groups; lane l of warp (wc, wr) updates columns
+// 64 wc + l and 64 wc + l + 32 (the two lanes of the packed FP32x2 arithmetic) of band rows
+// 4 wr .. 4 wr + 3.  Images up to 256 x 256.
+//
+// Control flow is the same in every CTA of the cluster (no early return before the last barrier,
+// no data-dependent wait), so every CTA reaches every barrier; no CTA leaves while another may
+// still write into its shared memory (the barrier after the last step orders those writes).
+#include <atomic>
+
+#include "wmc_window.cuh"
+
+namespace wmc {
+
+constexpr int kCWarpCols = 4, kCWarpRows = 4, kCRowsPerThread = 4;
+constexpr int kCThreads = 32 * kCWarpCols * kCWarpRows;  // 512
+constexpr int kCCols = 64 * kCWarpCols;                   // 256 columns per band
+constexpr int kCRows = kCWarpRows * kCRowsPerThread;      // 16 rows per band
+constexpr int kCMaxCtas = 16;
+constexpr int kCPitch = kCCols + 4;   // shared pitch: image column x at index x + 1; -1 and w inside
+constexpr int kCBuf = (kCRows + 2) * kCPitch;  // floats per buffer (band + 2 halo rows)
+
+struct ClusterParams {
+    const void *u0;   // U^0 (device, pitch ld)
+    const void *f;    // f or nullptr (mean-curvature flow)
+    void *out;        // U^iters (pitch ldo)
+    unsigned int *status;  // the call's status word, cleared (no wait here can run out)
+    int64_t ld, ldo;
+    int32_t h, w, iters;
+    float c_keep, c_f, c_h;
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_rank(uint32_t local, uint32_t rank) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+    return remote;
+}
+
+__device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename S, int BND>
+__global__ void __launch_bounds__(kCThreads, 1) flow_cluster_kernel(const ClusterParams p) {
+    extern __shared__ __align__(16) float smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rank = (int)cluster_rank(), nranks = (int)gridDim.x;
+    const int h = p.h, w = p.w;
+    const int y_band = kCRows * rank;  // image row of band row 0
+
+    // ---- initial state: band rows -1 .. kCRows of U^0 (the boundary rule outside the image) in
+    // buffer 0; the ring columns -1 and w in both buffers (they hold the rule's values throughout
+    // for ZERO, and REPLICATE rewrites them every step)
+    if (rank == 0 && tid == 0 && p.status) *p.status = 0u;
+    for (int idx = tid; idx < 2 * kCBuf; idx += kCThreads) smem[idx] = 0.0f;
+    __syncthreads();
+    for (int idx = tid; idx < (kCRows + 2) * (w + 2); idx += kCThreads) {
+        const int i = idx / (w + 2), j = idx - i * (w + 2);  // band row i - 1, image column j - 1
+        const int y = y_band + i - 1, x = j - 1;
+        float v = 0.0f;
+        if (BND == BND_REPLICATE) {
+            const int yc = min(max(y, 0), h - 1), xc = min(max(x, 0), w - 1);
+            if (y >= -1 && y <= h) v = Store<S>::load(static_cast<const S *>(p.u0) + (int64_t)yc * p.ld + xc);
+        } else if (y >= 0 && y < h && x >= 0 && x < w) {
+            v = Store<S>::load(static_cast<const S *>(p.u0) + (int64_t)y * p.ld + x);
+        }
+        smem[i * kCPitch + j] = v;
+    }
+
+    // ---- per-thread geometry and f's term (registers, for the whole run)
+    const int wc = warp % kCWarpCols, wr = warp / kCWarpCols;
+    const int x0 = 64 * wc + lane, x1 = x0 + 32;  // image columns of the two cells
+    const int j = x0 + 1;                         // shared column of the first cell
+    const int ib = 1 + kCRowsPerThread * wr;      // shared row of the first row
+    const bool cin0 = x0 < w, cin1 = x1 < w;
+    float2 g[kCRowsPerThread];
+    const float2 cf = make_float2(p.c_f, p.c_f);
+#pragma unroll
+    for (int k = 0; k < kCRowsPerThread; ++k) {
+        const int y = y_band + ib - 1 + k;
+        float a = 0.0f, b = 0.0f;
+        if (p.f != nullptr && y < h) {
+            const S *fr = static_cast<const S *>(p.f) + (int64_t)y * p.ld;
+            if (cin0) a = Store<S>::load(fr + x0);
+            if (cin1) b = Store<S>::load(fr + x1);
+        }
+        g[k] = __fmul2_rn(cf, make_float2(a, b));
+    }
+    const float2 ch = make_float2(p.c_h, p.c_h), ck = make_float2(p.c_keep, p.c_keep);
+    const uint32_t up = (uint32_t)(rank - 1), down = (uint32_t)(rank + 1);
+    // A value stored into a neighbour's halo row, with the ring cells that replicate it there
+    // (REPLICATE: image columns -1 and w of that row; a halo row is never image row -1 or h).
+    auto halo_store = [&](uint32_t a, float vx, float vy) {
+        if (cin0) {
+            st_cluster(a, vx);
+            if (BND == BND_REPLICATE && x0 == 0) st_cluster(a - 4, vx);
+            if (BND == BND_REPLICATE && x0 == w - 1) st_cluster(a + 4, vx);
+        }
+        if (cin1) {
+            st_cluster(a + 128, vy);
+            if (BND == BND_REPLICATE && x1 == w - 1) st_cluster(a + 132, vy);
+        }
+    };
+    // Every CTA of the cluster has started and filled its buffers before any CTA writes into
+    // another's shared memory.
+    cluster_sync();
+
+    // ---- the iterations
+    for (int s = 0; s < p.iters; ++s) {
+        const float *src = smem + (s & 1) * kCBuf;
+        float *dst = smem + ((s + 1) & 1) * kCBuf;
+        const float *rp = src + (ib - 1) * kCPitch + j;
+        Row3 r0 = load_row3(rp), r1 = load_row3(rp + kCPitch);
+#pragma unroll
+        for (int k = 0; k < kCRowsPerThread; ++k) {
+            const Row3 r2 = load_row3(rp + (k + 2) * kCPitch);
+            const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+            const float2 v = Store<S>::round2(__ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k])));
+            const int i = ib + k, y = y_band + i - 1;  // shared row, image row
+            if (y < h) {
+                float *d = dst + i * kCPitch + j;
+                if (cin0) d[0] = v.x;
+                if (cin1) d[32] = v.y;
+                // the band's first and last rows are the neighbours' halo rows
+                if (i == 1 && rank > 0)
+                    halo_store(map_rank((uint32_t)__cvta_generic_to_shared(dst + (kCRows + 1) * kCPitch + j), up), v.x, v.y);
+                if (i == kCRows && rank + 1 < nranks)
+                    halo_store(map_rank((uint32_t)__cvta_generic_to_shared(dst + j), down), v.x, v.y);
+                if (BND == BND_REPLICATE) {
+                    // the ring cells that replicate this cell: columns -1 / w, rows -1 / h (in this
+                    // band: image rows -1 and h are band rows 0 and h - y_band + 1, inside the band
+                    // or its halo), and the corners
+                    const bool top = y == 0, bottom = y == h - 1;
+                    auto mirror = [&](int x, float val, int jj) {
+                        if (x == 0) d[jj - 1] = val;
+                        if (x == w - 1) d[jj + 1] = val;
+                        if (top) {
+                            d[jj - kCPitch] = val;
+                            if (x == 0) d[jj - kCPitch - 1] = val;
+                            if (x == w - 1) d[jj - kCPitch + 1] = val;
+                        }
+                        if (bottom) {
+                            d[jj + kCPitch] = val;
+                            if (x == 0) d[jj + kCPitch - 1] = val;
+                            if (x == w - 1) d[jj + kCPitch + 1] = val;
+                        }
+                    };
+                    if (cin0) mirror(x0, v.x, 0);
+                    if (cin1) mirror(x1, v.y, 32);
+                }
+            }
+            r0 = r1;
+            r1 = r2;
+        }
+        // every CTA's writes of this step (its band, its ring cells, the neighbours' halo rows)
+        // are visible before the next step reads them
+        cluster_sync();
+    }
+
+    // ---- U^iters: the band's own rows
+    const float *fin = smem + (p.iters & 1) * kCBuf;
+    for (int idx = tid; idx < kCRows * w; idx += kCThreads) {
+        const int i = idx / w, x = idx - i * w, y = y_band + i;
+        if (y < h) Store<S>::store(static_cast<S *>(p.out) + (int64_t)y * p.ldo + x, fin[(i + 1) * kCPitch + x + 1]);
+    }
+}
+
+// Cluster size for an h x w image, 0 if this path does not apply (larger than one cluster holds).
+int cluster_ctas(int32_t h, int32_t w) {
+    if (h < 1 || w < 1 || w > kCCols || h > kCRows * kCMaxCtas) return 0;
+    return (h + kCRows - 1) / kCRows;
+}
+
+template <typename S, int BND>
+static cudaError_t launch_cluster_t(const ClusterParams &p, int ctas, cudaStream_t st) {
+    auto kern = flow_cluster_kernel<S, BND>;
+    const size_t smem = 2 * kCBuf * sizeof(float);
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(attr_set.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set.fetch_or(bit, std::memory_order_release);
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)ctas);
+    cfg.blockDim = dim3(kCThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+// Whether a cluster of `ctas` CTAs of the kernel can be scheduled on the current device (asked
+// once per device and size; any failure of the query reads as "no").
+bool cluster_fits(int ctas) {
+    if (ctas < 1 || ctas > kCMaxCtas) return false;
+    static std::atomic<uint32_t> asked[64], fits[64];  // per device: one bit per cluster size
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const uint32_t bit = 1u << (ctas - 1);
+    if (asked[dev & 63].load(std::memory_order_acquire) & bit)
+        return (fits[dev & 63].load(std::memory_order_acquire) & bit) != 0;
+    auto kern = flow_cluster_kernel<float, BND_REPLICATE>;
+    const size_t smem = 2 * kCBuf * sizeof(float);
+    bool ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+              cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+    if (ok) {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)ctas);
+        cfg.blockDim = dim3(kCThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)ctas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        ok = cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1;
+    }
+    cudaGetLastError();
+    if (ok) fits[dev & 63].fetch_or(bit, std::memory_order_acq_rel);
+    asked[dev & 63].fetch_or(bit, std::memory_order_acq_rel);
+    return ok;
+}
+
+cudaError_t launch_flow_cluster(int dtype, int bnd, const void *u0, const void *f, void *out,
+                                unsigned int *status, int64_t ld, int64_t ldo, int32_t h, int32_t w,
+                                int32_t iters, float c_keep, float c_f, float c_h, cudaStream_t st) {
+    const int ctas = cluster_ctas(h, w);
+    if (ctas == 0) return cudaErrorInvalidValue;
+    ClusterParams p{u0, f, out, status, ld, ldo, h, w, iters, c_keep, c_f, c_h};
+    const bool z = bnd == BND_ZERO;
+    switch (dtype) {
+        case 0: return z ? launch_cluster_t<float, BND_ZERO>(p, ctas, st) : launch_cluster_t<float, BND_REPLICATE>(p, ctas, st);
+        case 1: return z ? launch_cluster_t<__nv_bfloat16, BND_ZERO>(p, ctas, st)
+                         : launch_cluster_t<__nv_bfloat16, BND_REPLICATE>(p, ctas, st);
+        case 2: return z ? launch_cluster_t<__half, BND_ZERO>(p, ctas, st) : launch_cluster_t<__half, BND_REPLICATE>(p, ctas, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace wmc

@@ -40,6 +40,15 @@ WMC_DECLARE_TILE(launch_tile_f16_rep_w8)
 WMC_DECLARE_TILE(launch_tile_f16_zero_w8)
 #undef WMC_DECLARE_TILE
 
+// The whole flow of a small image (up to 256 x 256) in one launch of one thread-block cluster
+// (wmc_cluster.cu).  cluster_ctas: the cluster size for h x w, 0 when the image is too large;
+// cluster_fits: whether that cluster can be scheduled on the current device.
+int cluster_ctas(int32_t h, int32_t w);
+bool cluster_fits(int ctas);
+cudaError_t launch_flow_cluster(int dtype, int bnd, const void *u0, const void *f, void *out,
+                                unsigned int *status, int64_t ld, int64_t ldo, int32_t h, int32_t w,
+                                int32_t iters, float c_keep, float c_f, float c_h, cudaStream_t st);
+
 // Shape of the TMA box the flow kernel loads for tile shape `tile` (1 or 2), in elements of the
 // storage type.
 void tile_box(int dtype, int tile, int *box_w, int *box_h);

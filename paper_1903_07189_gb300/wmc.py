@@ -57,6 +57,7 @@ SIGNATURES = {
                               ctypes.POINTER(Config), _vp, _sz, _vp]),
     "wmc_denoise_status": (_i32, [_vp, _vp]),
     "wmc_denoise_noalloc_max_bytes": (_sz, []),
+    "wmc_denoise_cluster_size": (_i32, [_i32, _i32, _i32]),
     "wmc_denoise_noalloc": (_i32, [_vp, _vp, _vp, _i32, _i32, _i64, _i32, _f32, _f32, _i32, _i32, _vp]),
     "wmc_denoise_noalloc_status": (_i32, [_vp]),
     "wmc_selftest_status_timeout": (_i32, [_i32, _i64, _vp]),
@@ -245,6 +246,14 @@ def denoise(f: torch.Tensor | None, lam: float = 1.0, step: float | None = None,
                               BOUNDARY[boundary], ctypes.byref(cfg), workspace.data_ptr(),
                               workspace.numel(), _stream(ref.device)), "wmc_denoise")
     return out
+
+
+def cluster_size(h: int, w: int, iters: int, device=None) -> int:
+    """CTAs of the one-launch cluster path that the default configuration takes for an h x w
+    image and `iters` iterations on `device` (0: the multi-launch path)."""
+    lib = load()
+    with torch.cuda.device(device if device is not None else torch.cuda.current_device()):
+        return int(lib.wmc_denoise_cluster_size(int(h), int(w), int(iters)))
 
 
 def mcf(u0: torch.Tensor, step: float = 0.25, iters: int = 100, boundary: str = "replicate", **kw):
