@@ -30,13 +30,14 @@
 
 namespace wmc {
 
-constexpr int kCWarpCols = 4, kCWarpRows = 4, kCRowsPerThread = 4;
-constexpr int kCThreads = 32 * kCWarpCols * kCWarpRows;  // 512
+constexpr int kCWarpCols = 4;                             // 4 warps side by side: 256 columns
 constexpr int kCCols = 64 * kCWarpCols;                   // 256 columns per band
-constexpr int kCRows = kCWarpRows * kCRowsPerThread;      // 16 rows per band
+constexpr int kCRows = 16;                                // rows per band
 constexpr int kCMaxCtas = 16;
 constexpr int kCPitch = kCCols + 4;   // shared pitch: image column x at index x + 1; -1 and w inside
 constexpr int kCBuf = (kCRows + 2) * kCPitch;  // floats per buffer (band + 2 halo rows)
+constexpr int kCWarpRows = 4;                             // warp rows: 16 warps, 4 rows per thread
+constexpr int kCThreads = 32 * kCWarpCols * kCWarpRows;   // 512
 
 struct ClusterParams {
     const void *u0;   // U^0 (device, pitch ld)
@@ -65,13 +66,22 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
-__device__ __forceinline__ void cluster_sync() {
+__device__ __forceinline__ void cluster_arrive() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void cluster_sync() {
+    cluster_arrive();
+    cluster_wait();
+}
 
-template <typename S, int BND>
-__global__ void __launch_bounds__(kCThreads, 1) flow_cluster_kernel(const ClusterParams p) {
+template <typename S, int BND, int WR = kCWarpRows>
+__global__ void __launch_bounds__(32 * kCWarpCols * WR, 1) flow_cluster_kernel(const ClusterParams p) {
+    constexpr int NT = 32 * kCWarpCols * WR;  // threads
+    constexpr int RPT = kCRows / WR;          // rows per thread
+    static_assert(kCRows % WR == 0 && RPT >= 2, "band rows split evenly, two or more per thread");
     extern __shared__ __align__(16) float smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rank = (int)cluster_rank(), nranks = (int)gridDim.x;
@@ -82,9 +92,9 @@ __global__ void __launch_bounds__(kCThreads, 1) flow_cluster_kernel(const Cluste
     // buffer 0; the ring columns -1 and w in both buffers (they hold the rule's values throughout
     // for ZERO, and REPLICATE rewrites them every step)
     if (rank == 0 && tid == 0 && p.status) *p.status = 0u;
-    for (int idx = tid; idx < 2 * kCBuf; idx += kCThreads) smem[idx] = 0.0f;
+    for (int idx = tid; idx < 2 * kCBuf; idx += NT) smem[idx] = 0.0f;
     __syncthreads();
-    for (int idx = tid; idx < (kCRows + 2) * (w + 2); idx += kCThreads) {
+    for (int idx = tid; idx < (kCRows + 2) * (w + 2); idx += NT) {
         const int i = idx / (w + 2), j = idx - i * (w + 2);  // band row i - 1, image column j - 1
         const int y = y_band + i - 1, x = j - 1;
         float v = 0.0f;
@@ -101,12 +111,13 @@ __global__ void __launch_bounds__(kCThreads, 1) flow_cluster_kernel(const Cluste
     const int wc = warp % kCWarpCols, wr = warp / kCWarpCols;
     const int x0 = 64 * wc + lane, x1 = x0 + 32;  // image columns of the two cells
     const int j = x0 + 1;                         // shared column of the first cell
-    const int ib = 1 + kCRowsPerThread * wr;      // shared row of the first row
+    const int ib = 1 + RPT * wr;                  // shared row of the first row
     const bool cin0 = x0 < w, cin1 = x1 < w;
-    float2 g[kCRowsPerThread];
+    const bool first_rows = wr == 0, last_rows = wr == WR - 1;  // hold the band's edge rows
+    float2 g[RPT];
     const float2 cf = make_float2(p.c_f, p.c_f);
 #pragma unroll
-    for (int k = 0; k < kCRowsPerThread; ++k) {
+    for (int k = 0; k < RPT; ++k) {
         const int y = y_band + ib - 1 + k;
         float a = 0.0f, b = 0.0f;
         if (p.f != nullptr && y < h) {
@@ -131,65 +142,78 @@ __global__ void __launch_bounds__(kCThreads, 1) flow_cluster_kernel(const Cluste
             if (BND == BND_REPLICATE && x1 == w - 1) st_cluster(a + 132, vy);
         }
     };
+    // Row k of this thread's rows: the update of its two cells from rows k - 1, k, k + 1 of
+    // `src`, stored into `dst` (and into the neighbour's halo row for a band edge row, and into
+    // the ring cells that replicate an image edge cell).
+    auto row_out = [&](float *dst, int k, const Row3 &r0, const Row3 &r1, const Row3 &r2) {
+        const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+        const float2 v = Store<S>::round2(__ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k])));
+        const int i = ib + k, y = y_band + i - 1;  // shared row, image row
+        if (y >= h) return;
+        float *d = dst + i * kCPitch + j;
+        if (cin0) d[0] = v.x;
+        if (cin1) d[32] = v.y;
+        if (i == 1 && rank > 0)
+            halo_store(map_rank((uint32_t)__cvta_generic_to_shared(dst + (kCRows + 1) * kCPitch + j), up), v.x, v.y);
+        if (i == kCRows && rank + 1 < nranks)
+            halo_store(map_rank((uint32_t)__cvta_generic_to_shared(dst + j), down), v.x, v.y);
+        if (BND == BND_REPLICATE) {
+            // the ring cells that replicate this cell: columns -1 / w, rows -1 / h (image rows -1
+            // and h lie in this band or its halo rows), and the corners
+            const bool top = y == 0, bottom = y == h - 1;
+            auto mirror = [&](int x, float val, int jj) {
+                if (x == 0) d[jj - 1] = val;
+                if (x == w - 1) d[jj + 1] = val;
+                if (top) {
+                    d[jj - kCPitch] = val;
+                    if (x == 0) d[jj - kCPitch - 1] = val;
+                    if (x == w - 1) d[jj - kCPitch + 1] = val;
+                }
+                if (bottom) {
+                    d[jj + kCPitch] = val;
+                    if (x == 0) d[jj + kCPitch - 1] = val;
+                    if (x == w - 1) d[jj + kCPitch + 1] = val;
+                }
+            };
+            if (cin0) mirror(x0, v.x, 0);
+            if (cin1) mirror(x1, v.y, 32);
+        }
+    };
     // Every CTA of the cluster has started and filled its buffers before any CTA writes into
     // another's shared memory.
     cluster_sync();
 
-    // ---- the iterations
+    // ---- the iterations.  Each step first computes the band's two edge rows (the only ones
+    // that read the halo rows, and the ones the neighbours need), stores them, and arrives at the
+    // cluster barrier; the rest of the band is computed while the barrier completes.  A CTA
+    // barrier then orders this CTA's own writes, and the cluster wait the neighbours' halo rows.
+    // No CTA writes a neighbour's halo rows of step s + 1 before every CTA has arrived at step
+    // s, i.e. before their readers (the edge rows of step s) are done.
     for (int s = 0; s < p.iters; ++s) {
         const float *src = smem + (s & 1) * kCBuf;
         float *dst = smem + ((s + 1) & 1) * kCBuf;
         const float *rp = src + (ib - 1) * kCPitch + j;
-        Row3 r0 = load_row3(rp), r1 = load_row3(rp + kCPitch);
+        Row3 r0 = load_row3(rp), r1 = load_row3(rp + kCPitch), r2 = load_row3(rp + 2 * kCPitch);
+        if (first_rows) row_out(dst, 0, r0, r1, r2);
+        if (last_rows)
+            row_out(dst, RPT - 1, load_row3(rp + (RPT - 1) * kCPitch), load_row3(rp + RPT * kCPitch),
+                    load_row3(rp + (RPT + 1) * kCPitch));
+        cluster_arrive();
+        if (!first_rows) row_out(dst, 0, r0, r1, r2);
 #pragma unroll
-        for (int k = 0; k < kCRowsPerThread; ++k) {
-            const Row3 r2 = load_row3(rp + (k + 2) * kCPitch);
-            const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
-            const float2 v = Store<S>::round2(__ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k])));
-            const int i = ib + k, y = y_band + i - 1;  // shared row, image row
-            if (y < h) {
-                float *d = dst + i * kCPitch + j;
-                if (cin0) d[0] = v.x;
-                if (cin1) d[32] = v.y;
-                // the band's first and last rows are the neighbours' halo rows
-                if (i == 1 && rank > 0)
-                    halo_store(map_rank((uint32_t)__cvta_generic_to_shared(dst + (kCRows + 1) * kCPitch + j), up), v.x, v.y);
-                if (i == kCRows && rank + 1 < nranks)
-                    halo_store(map_rank((uint32_t)__cvta_generic_to_shared(dst + j), down), v.x, v.y);
-                if (BND == BND_REPLICATE) {
-                    // the ring cells that replicate this cell: columns -1 / w, rows -1 / h (in this
-                    // band: image rows -1 and h are band rows 0 and h - y_band + 1, inside the band
-                    // or its halo), and the corners
-                    const bool top = y == 0, bottom = y == h - 1;
-                    auto mirror = [&](int x, float val, int jj) {
-                        if (x == 0) d[jj - 1] = val;
-                        if (x == w - 1) d[jj + 1] = val;
-                        if (top) {
-                            d[jj - kCPitch] = val;
-                            if (x == 0) d[jj - kCPitch - 1] = val;
-                            if (x == w - 1) d[jj - kCPitch + 1] = val;
-                        }
-                        if (bottom) {
-                            d[jj + kCPitch] = val;
-                            if (x == 0) d[jj + kCPitch - 1] = val;
-                            if (x == w - 1) d[jj + kCPitch + 1] = val;
-                        }
-                    };
-                    if (cin0) mirror(x0, v.x, 0);
-                    if (cin1) mirror(x1, v.y, 32);
-                }
-            }
+        for (int k = 1; k < RPT; ++k) {
             r0 = r1;
             r1 = r2;
+            r2 = load_row3(rp + (k + 2) * kCPitch);
+            if (k < RPT - 1 || !last_rows) row_out(dst, k, r0, r1, r2);
         }
-        // every CTA's writes of this step (its band, its ring cells, the neighbours' halo rows)
-        // are visible before the next step reads them
-        cluster_sync();
+        __syncthreads();
+        cluster_wait();
     }
 
     // ---- U^iters: the band's own rows
     const float *fin = smem + (p.iters & 1) * kCBuf;
-    for (int idx = tid; idx < kCRows * w; idx += kCThreads) {
+    for (int idx = tid; idx < kCRows * w; idx += NT) {
         const int i = idx / w, x = idx - i * w, y = y_band + i;
         if (y < h) Store<S>::store(static_cast<S *>(p.out) + (int64_t)y * p.ldo + x, fin[(i + 1) * kCPitch + x + 1]);
     }
