@@ -69,6 +69,11 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
 __device__ __forceinline__ void cluster_arrive() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 }
+// Arrival that orders none of the thread's earlier memory accesses (for threads that wrote
+// nothing another CTA reads).
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void cluster_wait() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -114,6 +119,12 @@ __global__ void __launch_bounds__(32 * kCWarpCols * WR, 1) flow_cluster_kernel(c
     const int ib = 1 + RPT * wr;                  // shared row of the first row
     const bool cin0 = x0 < w, cin1 = x1 < w;
     const bool first_rows = wr == 0, last_rows = wr == WR - 1;  // hold the band's edge rows
+    // Warps whose rows are all inside the image and neither a band edge row nor the image's top
+    // or bottom row take a lean path: no halo stores, no row checks, only the column mirror of
+    // REPLICATE (the lanes of image columns 0 and w - 1).  The condition is the same for the
+    // whole warp.
+    const bool lean = !first_rows && !last_rows && y_band + ib - 1 + RPT - 1 < h - 1;
+    const bool col_edge = (x0 == 0) | (x0 == w - 1) | (x1 == w - 1);
     float2 g[RPT];
     const float2 cf = make_float2(p.c_f, p.c_f);
 #pragma unroll
@@ -185,27 +196,51 @@ __global__ void __launch_bounds__(32 * kCWarpCols * WR, 1) flow_cluster_kernel(c
 
     // ---- the iterations.  Each step first computes the band's two edge rows (the only ones
     // that read the halo rows, and the ones the neighbours need), stores them, and arrives at the
-    // cluster barrier; the rest of the band is computed while the barrier completes.  A CTA
-    // barrier then orders this CTA's own writes, and the cluster wait the neighbours' halo rows.
-    // No CTA writes a neighbour's halo rows of step s + 1 before every CTA has arrived at step
-    // s, i.e. before their readers (the edge rows of step s) are done.
+    // cluster barrier with release semantics; the other warps arrive at once (relaxed: they wrote
+    // nothing another CTA reads), and the rest of the band is computed while the barrier
+    // completes.  A CTA barrier then orders this CTA's own writes, and the cluster wait (acquire)
+    // the neighbours' halo rows.  No CTA writes a neighbour's halo rows of step s + 1 before
+    // every CTA has arrived at step s, i.e. before their readers (the edge rows of step s) are
+    // done.
     for (int s = 0; s < p.iters; ++s) {
         const float *src = smem + (s & 1) * kCBuf;
         float *dst = smem + ((s + 1) & 1) * kCBuf;
         const float *rp = src + (ib - 1) * kCPitch + j;
         Row3 r0 = load_row3(rp), r1 = load_row3(rp + kCPitch), r2 = load_row3(rp + 2 * kCPitch);
-        if (first_rows) row_out(dst, 0, r0, r1, r2);
-        if (last_rows)
-            row_out(dst, RPT - 1, load_row3(rp + (RPT - 1) * kCPitch), load_row3(rp + RPT * kCPitch),
-                    load_row3(rp + (RPT + 1) * kCPitch));
-        cluster_arrive();
-        if (!first_rows) row_out(dst, 0, r0, r1, r2);
+        if (lean) {
+            cluster_arrive_relaxed();
 #pragma unroll
-        for (int k = 1; k < RPT; ++k) {
-            r0 = r1;
-            r1 = r2;
-            r2 = load_row3(rp + (k + 2) * kCPitch);
-            if (k < RPT - 1 || !last_rows) row_out(dst, k, r0, r1, r2);
+            for (int k = 0; k < RPT; ++k) {
+                if (k > 0) {
+                    r0 = r1;
+                    r1 = r2;
+                    r2 = load_row3(rp + (k + 2) * kCPitch);
+                }
+                const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+                const float2 v = Store<S>::round2(__ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k])));
+                float *d = dst + (ib + k) * kCPitch + j;
+                if (cin0) d[0] = v.x;
+                if (cin1) d[32] = v.y;
+                if (BND == BND_REPLICATE && col_edge) {
+                    if (x0 == 0) d[-1] = v.x;
+                    if (x0 == w - 1) d[1] = v.x;
+                    if (x1 == w - 1) d[33] = v.y;
+                }
+            }
+        } else {
+            if (first_rows) row_out(dst, 0, r0, r1, r2);
+            if (last_rows)
+                row_out(dst, RPT - 1, load_row3(rp + (RPT - 1) * kCPitch), load_row3(rp + RPT * kCPitch),
+                        load_row3(rp + (RPT + 1) * kCPitch));
+            cluster_arrive();
+            if (!first_rows) row_out(dst, 0, r0, r1, r2);
+#pragma unroll
+            for (int k = 1; k < RPT; ++k) {
+                r0 = r1;
+                r1 = r2;
+                r2 = load_row3(rp + (k + 2) * kCPitch);
+                if (k < RPT - 1 || !last_rows) row_out(dst, k, r0, r1, r2);
+            }
         }
         __syncthreads();
         cluster_wait();
