@@ -25,6 +25,7 @@
 // no data-dependent wait), so every CTA reaches every barrier; no CTA leaves while another may
 // still write into its shared memory (the barrier after the last step orders those writes).
 #include <atomic>
+#include <type_traits>
 
 #include "wmc_window.cuh"
 
@@ -122,9 +123,16 @@ __global__ void __launch_bounds__(32 * kCWarpCols * WR, 1) flow_cluster_kernel(c
     // Warps whose rows are all inside the image and neither a band edge row nor the image's top
     // or bottom row take a lean path: no halo stores, no row checks, only the column mirror of
     // REPLICATE (the lanes of image columns 0 and w - 1).  The condition is the same for the
-    // whole warp.
-    const bool lean = !first_rows && !last_rows && y_band + ib - 1 + RPT - 1 < h - 1;
-    const bool col_edge = (x0 == 0) | (x0 == w - 1) | (x1 == w - 1);
+    // whole warp.  A one-column image, whose cells have ring cells on both sides, takes the full
+    // path.
+    const bool lean = !first_rows && !last_rows && y_band + ib - 1 + RPT - 1 < h - 1 && w > 1;
+    // REPLICATE column mirror: a lane of image column 0 or w - 1 also writes the ring cell beside
+    // it; m0 / m1 are the offsets of the two cells' mirror stores (a cell with no ring cell beside
+    // it gets its own offset: the store rewrites the value just stored).  Only the warps holding
+    // column 0 or w - 1 issue them.
+    const int m0 = x0 == 0 ? -1 : (x0 == w - 1 ? 1 : 0);
+    const int m1 = x1 == w - 1 ? 33 : 32;
+    const bool mirror_warp = BND == BND_REPLICATE && ((wc == 0) | ((w - 1) / 64 == wc));
     float2 g[RPT];
     const float2 cf = make_float2(p.c_f, p.c_f);
 #pragma unroll
@@ -190,6 +198,34 @@ __global__ void __launch_bounds__(32 * kCWarpCols * WR, 1) flow_cluster_kernel(c
             if (cin1) mirror(x1, v.y, 32);
         }
     };
+    // A row that is neither a band edge row nor the image's bottom row, and inside the image
+    // (no halo store, no row mirror; only the column mirror of REPLICATE).
+    auto row_plain = [&](auto mirror, float *dst, int k, const Row3 &r0, const Row3 &r1, const Row3 &r2) {
+        const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+        const float2 v = Store<S>::round2(__ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k])));
+        float *d = dst + (ib + k) * kCPitch + j;
+        if (cin0) d[0] = v.x;
+        if (cin1) d[32] = v.y;
+        if constexpr (decltype(mirror)::value) {
+            if (cin0) d[m0] = v.x;
+            if (cin1) d[m1] = v.y;
+        }
+    };
+    using Mirror = std::integral_constant<bool, BND == BND_REPLICATE>;
+    using NoMirror = std::integral_constant<bool, false>;
+    // bit k: row k of this thread's rows is plain (the same for the whole warp)
+    uint32_t plain_rows = 0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int i = ib + k, y = y_band + i - 1;
+        if (i != 1 && i != kCRows && y < h - 1 && w > 1) plain_rows |= 1u << k;
+    }
+    auto row_pick = [&](float *dst, int k, const Row3 &r0, const Row3 &r1, const Row3 &r2) {
+        if ((plain_rows >> k) & 1u)
+            row_plain(Mirror{}, dst, k, r0, r1, r2);
+        else
+            row_out(dst, k, r0, r1, r2);
+    };
     // Every CTA of the cluster has started and filled its buffers before any CTA writes into
     // another's shared memory.
     cluster_sync();
@@ -209,37 +245,34 @@ __global__ void __launch_bounds__(32 * kCWarpCols * WR, 1) flow_cluster_kernel(c
         Row3 r0 = load_row3(rp), r1 = load_row3(rp + kCPitch), r2 = load_row3(rp + 2 * kCPitch);
         if (lean) {
             cluster_arrive_relaxed();
+            auto rows = [&](auto mirror) {
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                if (k > 0) {
-                    r0 = r1;
-                    r1 = r2;
-                    r2 = load_row3(rp + (k + 2) * kCPitch);
+                for (int k = 0; k < RPT; ++k) {
+                    if (k > 0) {
+                        r0 = r1;
+                        r1 = r2;
+                        r2 = load_row3(rp + (k + 2) * kCPitch);
+                    }
+                    row_plain(mirror, dst, k, r0, r1, r2);
                 }
-                const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
-                const float2 v = Store<S>::round2(__ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k])));
-                float *d = dst + (ib + k) * kCPitch + j;
-                if (cin0) d[0] = v.x;
-                if (cin1) d[32] = v.y;
-                if (BND == BND_REPLICATE && col_edge) {
-                    if (x0 == 0) d[-1] = v.x;
-                    if (x0 == w - 1) d[1] = v.x;
-                    if (x1 == w - 1) d[33] = v.y;
-                }
-            }
+            };
+            if (mirror_warp)
+                rows(Mirror{});
+            else
+                rows(NoMirror{});
         } else {
             if (first_rows) row_out(dst, 0, r0, r1, r2);
             if (last_rows)
                 row_out(dst, RPT - 1, load_row3(rp + (RPT - 1) * kCPitch), load_row3(rp + RPT * kCPitch),
                         load_row3(rp + (RPT + 1) * kCPitch));
             cluster_arrive();
-            if (!first_rows) row_out(dst, 0, r0, r1, r2);
+            if (!first_rows) row_pick(dst, 0, r0, r1, r2);
 #pragma unroll
             for (int k = 1; k < RPT; ++k) {
                 r0 = r1;
                 r1 = r2;
                 r2 = load_row3(rp + (k + 2) * kCPitch);
-                if (k < RPT - 1 || !last_rows) row_out(dst, k, r0, r1, r2);
+                if (k < RPT - 1 || !last_rows) row_pick(dst, k, r0, r1, r2);
             }
         }
         __syncthreads();
