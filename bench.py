@@ -353,6 +353,31 @@ def measure_pr1(wmc, dev, reps=50):
                     "graph_gpix_iter_s": n * 100 / (t_graph * 1e-3) / 1e9}
         if T == 0:
             res[key]["cluster_ctas"] = ctas
+    # The evaluation and the iterations both read only f: with the evaluation on a second stream
+    # (forked from and joined to the first) the two kernels run side by side on separate SMs.
+    main, side = torch.cuda.current_stream(dev), torch.cuda.Stream(dev)
+
+    def run_forked():
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            wmc.eval(f, out=hw)
+        wmc.denoise(f, 1.0, 0.25, 100, out=out, workspace=ws)
+        torch.cuda.current_stream(dev).wait_stream(side)
+    for _ in range(3):
+        run_forked()
+    t_plain = event_ms(run_forked, reps)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(main)
+    with torch.cuda.stream(s):
+        run_forked()
+    main.wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run_forked()
+    g.replay()
+    t_graph = event_ms(g.replay, reps)
+    res["default_eval_on_second_stream"] = {"plain_us": 1e3 * t_plain, "graph_us": 1e3 * t_graph,
+                                            "graph_gpix_iter_s": n * 100 / (t_graph * 1e-3) / 1e9}
     return {"workload": "256x256 f32 (seed 0, 8 bumps + 4 shapes, sigma 0.05): 1 eval + 100 iterations, "
                         "lambda 1, step 0.25, replicate", "runs": reps, **res}
 
