@@ -122,7 +122,7 @@ def test_unrolled_gradient_matches_oracle(bnd, shape):
 
 
 @pytest.mark.parametrize("bnd", ["replicate", "zero"])
-@pytest.mark.parametrize("shape", [(70, 140), (97, 65)])
+@pytest.mark.parametrize("shape", [(70, 140), (97, 65), (5, 150), (150, 5)])
 def test_unrolled_gradient_multi_tile(bnd, shape):
     """Several 64 x 32 adjoint tiles with ragged edges: away from the pixels a near-tie can
     touch, dL/df matches to FP32 accuracy; dL/dlambda (a sum over every pixel) to 1e-3."""
@@ -241,6 +241,24 @@ def test_energy_grad_matches_oracle(bnd, shape):
     gap, hw = gap_map(u64, bnd)
     mask = dilate((gap <= GAP) | (np.abs(hw) <= GAP), 1)
     assert mask.mean() < 0.05, mask.mean()
+    ref = oracle.energy_grad(u64, bnd)
+    got = wmc().energy_grad(torch.from_numpy(u).to(DEV), bnd).cpu().double().numpy()
+    np.testing.assert_allclose(got[~mask], ref[~mask], rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("bnd,shape", [(b, s) for b in ("replicate", "zero")
+                                       for s in [(2, 2), (3, 65), (2, 130), (33, 2), (65, 3)]]
+                         + [("replicate", (1, 70)), ("replicate", (70, 1))])
+def test_energy_grad_thin_images(bnd, shape):
+    """A few rows or columns: every pixel is a border pixel, so the REPLICATE fold of the ring
+    terms (top and bottom, left and right on the same pixel) is exercised everywhere.  (One-row
+    images are mostly ties: a row's vertical neighbours are its own values or zeros; under ZERO
+    every pixel is one.)"""
+    u = image(*shape, seed=300 + shape[0] + shape[1])
+    u64 = u.astype(np.float64)
+    gap, hw = gap_map(u64, bnd)
+    mask = dilate((gap <= GAP) | (np.abs(hw) <= GAP), 1)
+    assert (~mask).sum() >= min(10, mask.size), mask.mean()
     ref = oracle.energy_grad(u64, bnd)
     got = wmc().energy_grad(torch.from_numpy(u).to(DEV), bnd).cpu().double().numpy()
     np.testing.assert_allclose(got[~mask], ref[~mask], rtol=0, atol=1e-6)
