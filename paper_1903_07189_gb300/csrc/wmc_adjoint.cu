@@ -61,7 +61,7 @@ __device__ __forceinline__ float half_laplace12_sel(float nw, float n, float ne,
     const float q = w - e;
     const float A = nw - se;
     const float B = ne - sw;
-    const float corners = (nw + se) + (ne + sw);
+    const float corners = (nw + ne) + (sw + se);
     const float edges = (n + s) + (w + e);
     const float L = fmaf(-12.0f, c, fmaf(2.0f, edges, corners));
     return select12_idx(L, fmaf(2.0f, q, A - B), fmaf(2.0f, p, A + B), fmaf(2.0f, p + q, A),
@@ -79,7 +79,7 @@ __device__ __forceinline__ float2 half_laplace12_sel_x2(float2 nw, float2 n, flo
     const float2 q = sub2(w, e);
     const float2 A = sub2(nw, se);
     const float2 B = sub2(ne, sw);
-    const float2 corners = __fadd2_rn(__fadd2_rn(nw, se), __fadd2_rn(ne, sw));
+    const float2 corners = __fadd2_rn(__fadd2_rn(nw, ne), __fadd2_rn(sw, se));
     const float2 edges = __fadd2_rn(__fadd2_rn(n, s), __fadd2_rn(w, e));
     const float2 L = __ffma2_rn(m12, c, __ffma2_rn(two, edges, corners));
     const float2 a1 = __ffma2_rn(two, q, sub2(A, B));

@@ -59,14 +59,16 @@ __device__ __forceinline__ float abs_select12(float L, float a1, float a2, float
     return fminf(m12, m56);
 }
 
-// 12 * H^w at the centre of a 3x3 neighbourhood (rows: n* above, s* below).
+// 12 * H^w at the centre of a 3x3 neighbourhood (rows: n* above, s* below).  The corner sum is
+// taken as (row above) + (row below), so that a kernel walking down a column can reuse each
+// row's w + e sum three times (as the row below, the centre row's edges, the row above).
 __device__ __forceinline__ float half_laplace12(float nw, float n, float ne, float w, float c,
                                                 float e, float sw, float s, float se) {
     const float p = n - s;   // N - S
     const float q = w - e;   // W - E
     const float A = nw - se;
     const float B = ne - sw;
-    const float corners = (nw + se) + (ne + sw);
+    const float corners = (nw + ne) + (sw + se);
     const float edges = (n + s) + (w + e);
     const float L = fmaf(-12.0f, c, fmaf(2.0f, edges, corners));
     const float a1 = fmaf(2.0f, q, A - B);
@@ -100,21 +102,23 @@ __device__ __forceinline__ float fd_wmc(float nw, float n, float ne, float w, fl
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 }
-// The ×12 Laplacian and odd parts of two cells (the linear part of half_laplace12_x2).
+// The ×12 Laplacian and odd parts of two cells (the linear part of half_laplace12_x2), given the
+// three rows' horizontal sums hn = nw + ne, hc = w + e, hs = sw + se (a caller walking down the
+// column computes each row's once).
 struct Terms2 {
     float2 L, a1, a2, a5, a6;
 };
-__device__ __forceinline__ Terms2 half_laplace12_terms_x2(float2 nw, float2 n, float2 ne, float2 w,
-                                                          float2 c, float2 e, float2 sw, float2 s,
-                                                          float2 se) {
+__device__ __forceinline__ Terms2 half_laplace12_terms_hs_x2(float2 nw, float2 n, float2 ne, float2 w,
+                                                             float2 c, float2 e, float2 sw, float2 s,
+                                                             float2 se, float2 hn, float2 hc, float2 hs) {
     const float2 two = make_float2(2.0f, 2.0f);
     const float2 m12 = make_float2(-12.0f, -12.0f);
     const float2 p = sub2(n, s);
     const float2 q = sub2(w, e);
     const float2 A = sub2(nw, se);
     const float2 B = sub2(ne, sw);
-    const float2 corners = __fadd2_rn(__fadd2_rn(nw, se), __fadd2_rn(ne, sw));
-    const float2 edges = __fadd2_rn(__fadd2_rn(n, s), __fadd2_rn(w, e));
+    const float2 corners = __fadd2_rn(hn, hs);
+    const float2 edges = __fadd2_rn(__fadd2_rn(n, s), hc);
     Terms2 t;
     t.L = __ffma2_rn(m12, c, __ffma2_rn(two, edges, corners));
     t.a1 = __ffma2_rn(two, q, sub2(A, B));
@@ -122,6 +126,12 @@ __device__ __forceinline__ Terms2 half_laplace12_terms_x2(float2 nw, float2 n, f
     t.a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
     t.a6 = __ffma2_rn(two, sub2(p, q), B);
     return t;
+}
+__device__ __forceinline__ Terms2 half_laplace12_terms_x2(float2 nw, float2 n, float2 ne, float2 w,
+                                                          float2 c, float2 e, float2 sw, float2 s,
+                                                          float2 se) {
+    return half_laplace12_terms_hs_x2(nw, n, ne, w, c, e, sw, s, se, __fadd2_rn(nw, ne), __fadd2_rn(w, e),
+                                      __fadd2_rn(sw, se));
 }
 
 // 12 |H^w| of two cells (abs_select12 per lane).
@@ -133,14 +143,37 @@ __device__ __forceinline__ float2 abs_half_laplace12_x2(float2 nw, float2 n, flo
                        abs_select12(t.L.y, t.a1.y, t.a2.y, t.a5.y, t.a6.y));
 }
 
+// select12 from the four differences t_j = |L| - |a_j| (computed by the caller) and Ls.
+__device__ __forceinline__ float select12_t(float t1, float t2, float t5, float t6, float Ls) {
+    float t = t1;
+    t = fabsf(t2) < fabsf(t) ? t2 : t;
+    t = fabsf(t5) < fabsf(t) ? t5 : t;
+    t = fabsf(t6) < fabsf(t) ? t6 : t;
+    return __int_as_float(__float_as_int(t) ^ (__float_as_int(Ls) & 0x80000000));
+}
+// The selection of two cells: the four differences |L| - |a_j| of both as packed FP32x2 adds (the
+// same roundings as select12's scalar ones), the compare-select chain per lane.  The sign guard
+// stays a scalar FMA per lane: one packed FMA for both lanes makes each selection wait for the
+// other lane's operands and measured 1.3 % slower.
+__device__ __forceinline__ float2 select12_x2(const Terms2 &t) {
+    const float2 aL = make_float2(fabsf(t.L.x), fabsf(t.L.y));
+    auto nabs = [](float2 v) { return make_float2(-fabsf(v.x), -fabsf(v.y)); };
+    const float2 t1 = __fadd2_rn(aL, nabs(t.a1)), t2 = __fadd2_rn(aL, nabs(t.a2));
+    const float2 t5 = __fadd2_rn(aL, nabs(t.a5)), t6 = __fadd2_rn(aL, nabs(t.a6));
+    return make_float2(select12_t(t1.x, t2.x, t5.x, t6.x, fmaf(0x1p-40f, t.a1.x, t.L.x)),
+                       select12_t(t1.y, t2.y, t5.y, t6.y, fmaf(0x1p-40f, t.a1.y, t.L.y)));
+}
+
 __device__ __forceinline__ float2 half_laplace12_x2(float2 nw, float2 n, float2 ne, float2 w,
                                                     float2 c, float2 e, float2 sw, float2 s,
                                                     float2 se) {
-    const Terms2 t = half_laplace12_terms_x2(nw, n, ne, w, c, e, sw, s, se);
-    // the sign guard of select12 stays a scalar FMA per lane: one packed FMA for both lanes makes
-    // each selection wait for the other lane's operands and measured 1.3 % slower
-    return make_float2(select12(t.L.x, t.a1.x, t.a2.x, t.a5.x, t.a6.x),
-                       select12(t.L.y, t.a1.y, t.a2.y, t.a5.y, t.a6.y));
+    return select12_x2(half_laplace12_terms_x2(nw, n, ne, w, c, e, sw, s, se));
+}
+// The same with the rows' horizontal sums supplied (see half_laplace12_terms_hs_x2).
+__device__ __forceinline__ float2 half_laplace12_hs_x2(float2 nw, float2 n, float2 ne, float2 w,
+                                                       float2 c, float2 e, float2 sw, float2 s,
+                                                       float2 se, float2 hn, float2 hc, float2 hs) {
+    return select12_x2(half_laplace12_terms_hs_x2(nw, n, ne, w, c, e, sw, s, se, hn, hc, hs));
 }
 
 // ---------------------------------------------------------------- storage types
