@@ -358,9 +358,10 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
             }
         }
     };
-    // Single images unroll the T - 1 steps (T is a template parameter): 2.3 % faster at 4096^2
-    // than a loop, whose pointer selection and back edge each step paid.  The batch kernel keeps
-    // the loop: unrolled, its descriptor state spills.
+    // Single images and 16-warp batch tiles unroll the T - 1 steps (T is a template parameter):
+    // 2.3 % faster at 4096^2 than a loop, whose pointer selection and back edge each step paid;
+    // the 512-image batch 643.5 -> 648.0 Gpix-iter/s.  8-warp batch tiles keep the loop: unrolled
+    // they ran slower at T >= 4.
     if constexpr (UNROLL) {
 #pragma unroll
         for (int s = 0; s < T - 1; ++s) one_step(s);
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW)
     if (jb.use_tma && threadIdx.x == 0) mbar_init(smem_u32(&bar), 1);
     // the output pointer is looked up again after the steps (kernel parameters, or the image
     // descriptor in L1) rather than kept in registers through them
-    tile_job<T, S, BND, NW, !BATCH>(jb, p.owt, p.oht, p.status, buf0, buf1, &bar, 0u, [&](int64_t *ldo) -> S * {
+    tile_job<T, S, BND, NW, !BATCH || NW == 16>(jb, p.owt, p.oht, p.status, buf0, buf1, &bar, 0u, [&](int64_t *ldo) -> S * {
         if (BATCH) {
             const BatchImage &im = p.images[p.tiles[blockIdx.x].x];
             *ldo = p.dst_role == 1 ? im.ld_out : im.ld;
