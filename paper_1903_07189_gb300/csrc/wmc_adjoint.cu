@@ -31,8 +31,6 @@ __constant__ float kH12Taps[8][9] = {
     {1, 0, 0, 4, -12, 0, 2, 4, 1},    // h8: south-west
 };
 
-// half_laplace12 with the index (0..7 for h1..h8) of the candidate it returns.  Same FP32
-// operations, hence the same value and the same piece as the forward kernels.
 // select12 with the index (0..7 for h1..h8) of the candidate it returns: the same comparisons
 // in the same order, so the same value and the same piece as the forward kernels.
 __device__ __forceinline__ float select12_idx(float L, float a1, float a2, float a5, float a6,
@@ -54,40 +52,20 @@ __device__ __forceinline__ float select12_idx(float L, float a1, float a2, float
     return __int_as_float(__float_as_int(t) ^ (__float_as_int(Ls) & 0x80000000));
 }
 
-// 12 H^w and the selected kernel index at the centre of a 3x3 neighbourhood.
+// 12 H^w and the selected kernel index at the centre of a 3x3 neighbourhood (the forward's terms).
 __device__ __forceinline__ float half_laplace12_sel(float nw, float n, float ne, float w, float c,
                                                     float e, float sw, float s, float se, int *m) {
-    const float p = n - s;
-    const float q = w - e;
-    const float A = nw - se;
-    const float B = ne - sw;
-    const float corners = (nw + ne) + (sw + se);
-    const float edges = (n + s) + (w + e);
-    const float L = fmaf(-12.0f, c, fmaf(2.0f, edges, corners));
-    return select12_idx(L, fmaf(2.0f, q, A - B), fmaf(2.0f, p, A + B), fmaf(2.0f, p + q, A),
-                        fmaf(2.0f, p - q, B), m);
+    const Terms1 t = half_laplace12_terms(nw, n, ne, w, c, e, sw, s, se);
+    return select12_idx(t.L, t.a1, t.a2, t.a5, t.a6, m);
 }
 
-// The same for two cells at once (lane .x, lane .y): the linear part as packed FP32x2 operations,
-// each lane rounding exactly as the scalar form (a - b as fma(b, -1, a), exact in the product).
+// The same for two cells at once (lane .x, lane .y): the forward's packed terms.
 __device__ __forceinline__ float2 half_laplace12_sel_x2(float2 nw, float2 n, float2 ne, float2 w,
                                                         float2 c, float2 e, float2 sw, float2 s,
                                                         float2 se, int *m0, int *m1) {
-    const float2 two = make_float2(2.0f, 2.0f);
-    const float2 m12 = make_float2(-12.0f, -12.0f);
-    const float2 p = sub2(n, s);
-    const float2 q = sub2(w, e);
-    const float2 A = sub2(nw, se);
-    const float2 B = sub2(ne, sw);
-    const float2 corners = __fadd2_rn(__fadd2_rn(nw, ne), __fadd2_rn(sw, se));
-    const float2 edges = __fadd2_rn(__fadd2_rn(n, s), __fadd2_rn(w, e));
-    const float2 L = __ffma2_rn(m12, c, __ffma2_rn(two, edges, corners));
-    const float2 a1 = __ffma2_rn(two, q, sub2(A, B));
-    const float2 a2 = __ffma2_rn(two, p, __fadd2_rn(A, B));
-    const float2 a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
-    const float2 a6 = __ffma2_rn(two, sub2(p, q), B);
-    return make_float2(select12_idx(L.x, a1.x, a2.x, a5.x, a6.x, m0),
-                       select12_idx(L.y, a1.y, a2.y, a5.y, a6.y, m1));
+    const Terms2 t = half_laplace12_terms_x2(nw, n, ne, w, c, e, sw, s, se);
+    return make_float2(select12_idx(t.L.x, t.a1.x, t.a2.x, t.a5.x, t.a6.x, m0),
+                       select12_idx(t.L.y, t.a1.y, t.a2.y, t.a5.y, t.a6.y, m1));
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {

@@ -59,23 +59,39 @@ __device__ __forceinline__ float abs_select12(float L, float a1, float a2, float
     return fminf(m12, m56);
 }
 
-// 12 * H^w at the centre of a 3x3 neighbourhood (rows: n* above, s* below).  The corner sum is
-// taken as (row above) + (row below), so that a kernel walking down a column can reuse each
-// row's w + e sum three times (as the row below, the centre row's edges, the row above).
+// The x12 Laplacian L and the odd parts a1, a2, a5, a6 at the centre of a 3x3 neighbourhood
+// (rows: n* above, s* below), written through per-row values so that a kernel walking down a
+// column forms each row's once and shares it between the three cells that read that row: with
+// h = w + e and R = h + 2 c of a row,
+//   L  = R(above) + R(below) + 2 h(centre) - 12 c
+//   a2 = R(above) - R(below)              (= 2 (n - s) + A + B)
+//   a1 = 2 q + (A - B),  a5 = 2 (p + q) + A,  a6 = 2 (p - q) + B,
+// with p = n - s, q = w - e, A = nw - se, B = ne - sw.
+// Every form of the stencil (scalar, packed, adjoint) takes these operations in this order, so
+// they agree bit for bit.
+struct Terms1 {
+    float L, a1, a2, a5, a6;
+};
+__device__ __forceinline__ Terms1 half_laplace12_terms(float nw, float n, float ne, float w, float c,
+                                                       float e, float sw, float s, float se) {
+    const float Rn = fmaf(2.0f, n, nw + ne), Rs = fmaf(2.0f, s, sw + se);
+    const float q = w - e;
+    const float p = n - s;
+    const float A = nw - se, B = ne - sw;
+    Terms1 t;
+    t.L = fmaf(-12.0f, c, fmaf(2.0f, w + e, Rn + Rs));
+    t.a2 = Rn - Rs;
+    t.a1 = fmaf(2.0f, q, A - B);
+    t.a5 = fmaf(2.0f, p + q, A);
+    t.a6 = fmaf(2.0f, p - q, B);
+    return t;
+}
+
+// 12 * H^w at the centre of a 3x3 neighbourhood.
 __device__ __forceinline__ float half_laplace12(float nw, float n, float ne, float w, float c,
                                                 float e, float sw, float s, float se) {
-    const float p = n - s;   // N - S
-    const float q = w - e;   // W - E
-    const float A = nw - se;
-    const float B = ne - sw;
-    const float corners = (nw + ne) + (sw + se);
-    const float edges = (n + s) + (w + e);
-    const float L = fmaf(-12.0f, c, fmaf(2.0f, edges, corners));
-    const float a1 = fmaf(2.0f, q, A - B);
-    const float a2 = fmaf(2.0f, p, A + B);
-    const float a5 = fmaf(2.0f, p + q, A);
-    const float a6 = fmaf(2.0f, p - q, B);
-    return select12(L, a1, a2, a5, a6);
+    const Terms1 t = half_laplace12_terms(nw, n, ne, w, c, e, sw, s, se);
+    return select12(t.L, t.a1, t.a2, t.a5, t.a6);
 }
 
 // Conventional finite-difference WMC of Eq. rhs at the centre of a 3x3 neighbourhood (rows: n*
@@ -102,36 +118,26 @@ __device__ __forceinline__ float fd_wmc(float nw, float n, float ne, float w, fl
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
 }
-// The ×12 Laplacian and odd parts of two cells (the linear part of half_laplace12_x2), given the
-// three rows' horizontal sums hn = nw + ne, hc = w + e, hs = sw + se (a caller walking down the
-// column computes each row's once).
+// The same linear part for two cells (the terms of half_laplace12_x2), operation for operation.
 struct Terms2 {
     float2 L, a1, a2, a5, a6;
 };
-__device__ __forceinline__ Terms2 half_laplace12_terms_hs_x2(float2 nw, float2 n, float2 ne, float2 w,
-                                                             float2 c, float2 e, float2 sw, float2 s,
-                                                             float2 se, float2 hn, float2 hc, float2 hs) {
-    const float2 two = make_float2(2.0f, 2.0f);
-    const float2 m12 = make_float2(-12.0f, -12.0f);
-    const float2 p = sub2(n, s);
-    const float2 q = sub2(w, e);
-    const float2 A = sub2(nw, se);
-    const float2 B = sub2(ne, sw);
-    const float2 corners = __fadd2_rn(hn, hs);
-    const float2 edges = __fadd2_rn(__fadd2_rn(n, s), hc);
-    Terms2 t;
-    t.L = __ffma2_rn(m12, c, __ffma2_rn(two, edges, corners));
-    t.a1 = __ffma2_rn(two, q, sub2(A, B));
-    t.a2 = __ffma2_rn(two, p, __fadd2_rn(A, B));
-    t.a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
-    t.a6 = __ffma2_rn(two, sub2(p, q), B);
-    return t;
-}
 __device__ __forceinline__ Terms2 half_laplace12_terms_x2(float2 nw, float2 n, float2 ne, float2 w,
                                                           float2 c, float2 e, float2 sw, float2 s,
                                                           float2 se) {
-    return half_laplace12_terms_hs_x2(nw, n, ne, w, c, e, sw, s, se, __fadd2_rn(nw, ne), __fadd2_rn(w, e),
-                                      __fadd2_rn(sw, se));
+    const float2 two = make_float2(2.0f, 2.0f);
+    const float2 m12 = make_float2(-12.0f, -12.0f);
+    const float2 Rn = __ffma2_rn(two, n, __fadd2_rn(nw, ne)), Rs = __ffma2_rn(two, s, __fadd2_rn(sw, se));
+    const float2 q = sub2(w, e);
+    const float2 p = sub2(n, s);
+    const float2 A = sub2(nw, se), B = sub2(ne, sw);
+    Terms2 t;
+    t.L = __ffma2_rn(m12, c, __ffma2_rn(two, __fadd2_rn(w, e), __fadd2_rn(Rn, Rs)));
+    t.a2 = sub2(Rn, Rs);
+    t.a1 = __ffma2_rn(two, q, sub2(A, B));
+    t.a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
+    t.a6 = __ffma2_rn(two, sub2(p, q), B);
+    return t;
 }
 
 // 12 |H^w| of two cells (abs_select12 per lane).
@@ -169,12 +175,7 @@ __device__ __forceinline__ float2 half_laplace12_x2(float2 nw, float2 n, float2 
                                                     float2 se) {
     return select12_x2(half_laplace12_terms_x2(nw, n, ne, w, c, e, sw, s, se));
 }
-// The same with the rows' horizontal sums supplied (see half_laplace12_terms_hs_x2).
-__device__ __forceinline__ float2 half_laplace12_hs_x2(float2 nw, float2 n, float2 ne, float2 w,
-                                                       float2 c, float2 e, float2 sw, float2 s,
-                                                       float2 se, float2 hn, float2 hc, float2 hs) {
-    return select12_x2(half_laplace12_terms_hs_x2(nw, n, ne, w, c, e, sw, s, se, hn, hc, hs));
-}
+
 
 // ---------------------------------------------------------------- storage types
 template <typename S> struct Store;

@@ -150,13 +150,12 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
     const float2 ch = make_float2(c.c_h, c.c_h), ck = make_float2(c.c_keep, c.c_keep);
     const float *rp = src + (c.ib - 1) * P + c.j;
     Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
-    // each row's w + e sum serves three cells (corners of the rows below and above, edges of its own)
-    float2 h0 = __fadd2_rn(r0.w, r0.e), h1 = __fadd2_rn(r1.w, r1.e);
+    // (the rows are unrolled: each row's w + e, w - e and w + e + 2 c are formed once and shared by
+    // the three cells that read the row, see half_laplace12_terms)
 #pragma unroll
     for (int k = 0; k < kRY; ++k) {
         const Row3 r2 = load_row3(rp + (k + 2) * P);
-        const float2 h2 = __fadd2_rn(r2.w, r2.e);
-        const float2 hw = half_laplace12_hs_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e, h0, h1, h2);
+        const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
         float2 v = __ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k]));
         const int i = c.ib + k;
         if (WMODE == WRITE_INTERIOR) {
@@ -188,8 +187,6 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
         }
         r0 = r1;
         r1 = r2;
-        h0 = h1;
-        h1 = h2;
     }
 }
 
