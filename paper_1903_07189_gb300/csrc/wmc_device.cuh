@@ -60,30 +60,32 @@ __device__ __forceinline__ float abs_select12(float L, float a1, float a2, float
 }
 
 // The x12 Laplacian L and the odd parts a1, a2, a5, a6 at the centre of a 3x3 neighbourhood
-// (rows: n* above, s* below), written through per-row values so that a kernel walking down a
-// column forms each row's once and shares it between the three cells that read that row: with
-// h = w + e and R = h + 2 c of a row,
-//   L  = R(above) + R(below) + 2 h(centre) - 12 c
-//   a2 = R(above) - R(below)              (= 2 (n - s) + A + B)
-//   a1 = 2 q + (A - B),  a5 = 2 (p + q) + A,  a6 = 2 (p - q) + B,
-// with p = n - s, q = w - e, A = nw - se, B = ne - sw.
-// Every form of the stencil (scalar, packed, adjoint) takes these operations in this order, so
-// they agree bit for bit.
+// (rows: n* above, s* below), written through four values of each row so that a kernel walking
+// down a column forms each row's once and shares them between the three cells that read that
+// row.  For a row with cells (w, c, e):
+//   P = w + 2c,  Q = 2c + e,  R = P + e,  D = w - e,
+// and then, with q = D(centre),
+//   L  = R(above) + R(below) + 2 R(centre) - 16 c   (= corners + 2 edges - 12 c)
+//   a1 = 2 q + D(above) + D(below)                   (= 2 (w - e) + A - B)
+//   a2 = R(above) - R(below)                         (= 2 (n - s) + A + B)
+//   a5 = 2 q + P(above) - Q(below)                   (= 2 (p + q) + A)
+//   a6 = -2 q + Q(above) - P(below)                  (= 2 (p - q) + B)
+// with p = n - s, A = nw - se, B = ne - sw.  Every form of the stencil (scalar, packed, adjoint)
+// takes these operations in this order, so they agree bit for bit.
 struct Terms1 {
     float L, a1, a2, a5, a6;
 };
 __device__ __forceinline__ Terms1 half_laplace12_terms(float nw, float n, float ne, float w, float c,
                                                        float e, float sw, float s, float se) {
-    const float Rn = fmaf(2.0f, n, nw + ne), Rs = fmaf(2.0f, s, sw + se);
-    const float q = w - e;
-    const float p = n - s;
-    const float A = nw - se, B = ne - sw;
+    const float Pa = fmaf(2.0f, n, nw), Qa = fmaf(2.0f, n, ne), Ra = Pa + ne, Da = nw - ne;
+    const float Pc = fmaf(2.0f, c, w), Rc = Pc + e, q = w - e;
+    const float Pb = fmaf(2.0f, s, sw), Qb = fmaf(2.0f, s, se), Rb = Pb + se, Db = sw - se;
     Terms1 t;
-    t.L = fmaf(-12.0f, c, fmaf(2.0f, w + e, Rn + Rs));
-    t.a2 = Rn - Rs;
-    t.a1 = fmaf(2.0f, q, A - B);
-    t.a5 = fmaf(2.0f, p + q, A);
-    t.a6 = fmaf(2.0f, p - q, B);
+    t.L = fmaf(-16.0f, c, fmaf(2.0f, Rc, Ra + Rb));
+    t.a1 = fmaf(2.0f, q, Da + Db);
+    t.a2 = Ra - Rb;
+    t.a5 = fmaf(2.0f, q, Pa - Qb);
+    t.a6 = fmaf(-2.0f, q, Qa - Pb);
     return t;
 }
 
@@ -125,18 +127,17 @@ struct Terms2 {
 __device__ __forceinline__ Terms2 half_laplace12_terms_x2(float2 nw, float2 n, float2 ne, float2 w,
                                                           float2 c, float2 e, float2 sw, float2 s,
                                                           float2 se) {
-    const float2 two = make_float2(2.0f, 2.0f);
-    const float2 m12 = make_float2(-12.0f, -12.0f);
-    const float2 Rn = __ffma2_rn(two, n, __fadd2_rn(nw, ne)), Rs = __ffma2_rn(two, s, __fadd2_rn(sw, se));
-    const float2 q = sub2(w, e);
-    const float2 p = sub2(n, s);
-    const float2 A = sub2(nw, se), B = sub2(ne, sw);
+    const float2 two = make_float2(2.0f, 2.0f), mtwo = make_float2(-2.0f, -2.0f);
+    const float2 m16 = make_float2(-16.0f, -16.0f);
+    const float2 Pa = __ffma2_rn(two, n, nw), Qa = __ffma2_rn(two, n, ne), Ra = __fadd2_rn(Pa, ne), Da = sub2(nw, ne);
+    const float2 Pc = __ffma2_rn(two, c, w), Rc = __fadd2_rn(Pc, e), q = sub2(w, e);
+    const float2 Pb = __ffma2_rn(two, s, sw), Qb = __ffma2_rn(two, s, se), Rb = __fadd2_rn(Pb, se), Db = sub2(sw, se);
     Terms2 t;
-    t.L = __ffma2_rn(m12, c, __ffma2_rn(two, __fadd2_rn(w, e), __fadd2_rn(Rn, Rs)));
-    t.a2 = sub2(Rn, Rs);
-    t.a1 = __ffma2_rn(two, q, sub2(A, B));
-    t.a5 = __ffma2_rn(two, __fadd2_rn(p, q), A);
-    t.a6 = __ffma2_rn(two, sub2(p, q), B);
+    t.L = __ffma2_rn(m16, c, __ffma2_rn(two, Rc, __fadd2_rn(Ra, Rb)));
+    t.a1 = __ffma2_rn(two, q, __fadd2_rn(Da, Db));
+    t.a2 = sub2(Ra, Rb);
+    t.a5 = __ffma2_rn(two, q, sub2(Pa, Qb));
+    t.a6 = __ffma2_rn(mtwo, q, sub2(Qa, Pb));
     return t;
 }
 
