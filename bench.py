@@ -50,16 +50,19 @@ WORKLOAD = (f"{H}x{W} f32 synthetic image (64 bumps + 32 shapes, sigma {SIGMA}, 
             f"1 WMC eval pass + {ITERS} L2-denoising iterations (lambda {LAM}, step {STEP}, "
             f"replicate) + FP64 energies")
 BYTES_PER_PX_LAUNCH = 12  # read U, read f, write U (FP32): algorithmic bytes of one pass
-# FP32 operations on the FMA pipe per output pixel-iteration of the stencil + update as the
-# kernels compute it (L and the four odd parts: 20, |L|-|a_j|: 4, sign guard: 1, update: 2);
-# compare/select/sign logic (7 more) runs on the separate ALU pipe and is not counted.
+# Algorithmic FP32 operations on the FMA pipe per output pixel-iteration: the stencil in the
+# L +- a_j form evaluated cell by cell (L and the four odd parts: 20, |L|-|a_j|: 4, sign guard: 1)
+# and the update (2); compare/select/sign logic (7 more) runs on the separate ALU pipe and is not
+# counted.  The kernels share four per-row values between the three cells that read a row, so
+# they execute fewer: FMA_OPS_EXECUTED_PER_PX_ITER (14 for the linear part instead of 20).
 FMA_OPS_PER_PX_ITER = 27
+FMA_OPS_EXECUTED_PER_PX_ITER = 21
 DEFAULT_T = 4
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one 4-step flow launch on this
 # image, from the ncu capture of one warm-L2 launch of the current kernel summarised in
 # profiles/flow_tile_t4_4096x4096_full.md; reported as roofline.traffic for the default 4 steps
 # per launch and the full 500 iterations only
-TILE_T4_DRAM_BYTES = 88.31e6  # 67.18 MB read + 21.13 MB written
+TILE_T4_DRAM_BYTES = 88.30e6  # 67.18 MB read + 21.12 MB written
 # GB300 HBM3e nominal bandwidth (GB/s); fractions are reported against it and against the
 # measured copy bandwidth
 NOMINAL_HBM_GBS = 8000.0
@@ -614,7 +617,10 @@ def run_gpu(args):
                     "peak_nominal": {"value": nominal_fma, "how": f"{peak_fma['sms']} SMs (queried) x 128 lanes x "
                                                                    f"{sm_mhz:.0f} MHz (sampled)",
                                      "frac": fp32_achieved / nominal_fma},
-                    "algorithmic_ops_per_px_iter": FMA_OPS_PER_PX_ITER, "launch_ms": launch_ms,
+                    "algorithmic_ops_per_px_iter": FMA_OPS_PER_PX_ITER,
+                    "executed_ops_per_px_iter": FMA_OPS_EXECUTED_PER_PX_ITER,
+                    "executed_frac": fp32_achieved * FMA_OPS_EXECUTED_PER_PX_ITER / FMA_OPS_PER_PX_ITER / peak_fma["tops"],
+                    "launch_ms": launch_ms,
                     # the same iterations unblocked would move 12 B per pixel-iteration
                     "unblocked_equivalent": {"gbs": value * BYTES_PER_PX_LAUNCH,
                                              "frac": value * BYTES_PER_PX_LAUNCH / peak,
