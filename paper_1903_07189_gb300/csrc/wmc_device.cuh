@@ -50,14 +50,6 @@ __device__ __forceinline__ float select12(float L, float a1, float a2, float a5,
     return select12_ls(L, a1, a2, a5, a6, fmaf(0x1p-40f, a1, L));
 }
 
-// |H^w| alone (the energies): the least |t_j|, which is |select12(...)| bit for bit (equal
-// magnitudes are equal values), without the compare-select chain and the sign.
-__device__ __forceinline__ float abs_select12(float L, float a1, float a2, float a5, float a6) {
-    const float aL = fabsf(L);
-    const float m12 = fminf(fabsf(aL - fabsf(a1)), fabsf(aL - fabsf(a2)));
-    const float m56 = fminf(fabsf(aL - fabsf(a5)), fabsf(aL - fabsf(a6)));
-    return fminf(m12, m56);
-}
 
 // The x12 Laplacian L and the odd parts a1, a2, a5, a6 at the centre of a 3x3 neighbourhood
 // (rows: n* above, s* below), written through four values of each row so that a kernel walking
@@ -141,13 +133,21 @@ __device__ __forceinline__ Terms2 half_laplace12_terms_x2(float2 nw, float2 n, f
     return t;
 }
 
-// 12 |H^w| of two cells (abs_select12 per lane).
+// 12 |H^w| of two cells (the energies): the least |t_j| per lane, without the compare-select chain
+// and the sign (equal magnitudes are equal values, so this is |half_laplace12_x2| bit for bit); the
+// four differences |L| - |a_j| as packed adds, with the same roundings.
 __device__ __forceinline__ float2 abs_half_laplace12_x2(float2 nw, float2 n, float2 ne, float2 w,
                                                         float2 c, float2 e, float2 sw, float2 s,
                                                         float2 se) {
     const Terms2 t = half_laplace12_terms_x2(nw, n, ne, w, c, e, sw, s, se);
-    return make_float2(abs_select12(t.L.x, t.a1.x, t.a2.x, t.a5.x, t.a6.x),
-                       abs_select12(t.L.y, t.a1.y, t.a2.y, t.a5.y, t.a6.y));
+    const float2 aL = make_float2(fabsf(t.L.x), fabsf(t.L.y));
+    auto nabs = [](float2 v) { return make_float2(-fabsf(v.x), -fabsf(v.y)); };
+    const float2 t1 = __fadd2_rn(aL, nabs(t.a1)), t2 = __fadd2_rn(aL, nabs(t.a2));
+    const float2 t5 = __fadd2_rn(aL, nabs(t.a5)), t6 = __fadd2_rn(aL, nabs(t.a6));
+    auto m = [](float a, float b, float c2, float d) {
+        return fminf(fminf(fabsf(a), fabsf(b)), fminf(fabsf(c2), fabsf(d)));
+    };
+    return make_float2(m(t1.x, t2.x, t5.x, t6.x), m(t1.y, t2.y, t5.y, t6.y));
 }
 
 // select12 from the four differences t_j = |L| - |a_j| (computed by the caller) and Ls.

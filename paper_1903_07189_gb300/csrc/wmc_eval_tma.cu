@@ -17,6 +17,8 @@
 // Box b covers image columns x0 = 128 (b mod nbx) .. x0 + 127 and rows y0 = 64 (b div nbx) ..
 // y0 + 63; its window starts at (X0, Y0) = (x0 - 4, y0 - 1): x0 - 4 keeps the TMA x coordinate on
 // a 16-byte boundary, and output cell (y, x) is window cell (y - Y0, x - X0).
+#include <type_traits>
+
 #include "wmc_window.cuh"
 
 namespace wmc {
@@ -111,19 +113,32 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
             const bool c0 = gx < w, c1 = gx + 32 < w;  // gx >= 0 always (X0 + 4 >= 0)
             const float *rp = buf + (ib - 1) * P + j;
             Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
-            float *orow = p.out + (int64_t)(Y0 + ib) * p.ldo + gx;
+            float *q = p.out + (int64_t)(Y0 + ib) * p.ldo + gx;
+            const int64_t ldo = p.ldo;
+            // a box wholly inside the image (the same for the whole CTA) stores without masks
+            const bool full = (X0 + kEvalX + kEvalBoxW <= w) & (Y0 + 1 + kEvalBoxH <= h);
+            auto rows = [&](auto masked) {
 #pragma unroll
-            for (int r = 0; r < kRY; ++r) {
-                const Row3 r2 = load_row3(rp + (r + 2) * P);
-                const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
-                const float2 o = __fmul2_rn(sc, hw);
-                const bool rin = Y0 + ib + r < h;
-                float *q = orow + (int64_t)r * p.ldo;
-                if (rin & c0) q[0] = o.x;
-                if (rin & c1) q[32] = o.y;
-                r0 = r1;
-                r1 = r2;
-            }
+                for (int r = 0; r < kRY; ++r, q += ldo) {
+                    const Row3 r2 = load_row3(rp + (r + 2) * P);
+                    const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+                    const float2 o = __fmul2_rn(sc, hw);
+                    if constexpr (decltype(masked)::value) {
+                        const bool rin = Y0 + ib + r < h;
+                        if (rin & c0) q[0] = o.x;
+                        if (rin & c1) q[32] = o.y;
+                    } else {
+                        q[0] = o.x;
+                        q[32] = o.y;
+                    }
+                    r0 = r1;
+                    r1 = r2;
+                }
+            };
+            if (full)
+                rows(std::integral_constant<bool, false>{});
+            else
+                rows(std::integral_constant<bool, true>{});
         }
         // release the buffer: one arrival per warp, after all its lanes have read the box
         __syncwarp();

@@ -15,6 +15,8 @@
 #include "wmc_device.cuh"
 #include "wmc_internal.h"
 #include "wmc_stream.cuh"
+#include <type_traits>
+
 #include "wmc_window.cuh"
 
 namespace wmc {
@@ -447,28 +449,37 @@ __global__ void __launch_bounds__(kEThreads, 1)
             const float *rp = bu + (ib - 1) * P + j;
             const int fo = (ib - 1) * kEBoxW + (j - 4);  // box offset of the thread's first cell
             Row3 r0 = load_row3(rp), r1 = load_row3(rp + P);
-            float s[3] = {0.f, 0.f, 0.f};
+            // per-lane sums of the thread's two columns (8 cells each), as FP32x2 pairs
+            float2 s2[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            // a box wholly inside the image (the same for the whole CTA) needs no cell masks
+            const bool full = (bx + 1) * kEBoxW <= w && (by + 1) * kEBoxH <= h;
+            auto rows = [&](auto masked) {
 #pragma unroll
-            for (int r = 0; r < kERY; ++r) {
-                const Row3 r2 = load_row3(rp + (r + 2) * P);
-                const float2 a12 = abs_half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
-                const bool rin = Y0 + ib + r < h;
-                const bool in0 = rin & c0, in1 = rin & c1;
-                if (in0) s[0] += a12.x;
-                if (in1) s[0] += a12.y;
-                if (HF) {
-                    const float d0 = r1.c.x - bf[fo + r * kEBoxW], d1 = r1.c.y - bf[fo + r * kEBoxW + 32];
-                    if (in0) s[1] = fmaf(d0, d0, s[1]);
-                    if (in1) s[1] = fmaf(d1, d1, s[1]);
+                for (int r = 0; r < kERY; ++r) {
+                    const Row3 r2 = load_row3(rp + (r + 2) * P);
+                    float2 a12 = abs_half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+                    float2 df = make_float2(0.f, 0.f), dc = make_float2(0.f, 0.f);
+                    if (HF) df = sub2(r1.c, make_float2(bf[fo + r * kEBoxW], bf[fo + r * kEBoxW + 32]));
+                    if (HC) dc = sub2(r1.c, make_float2(bc[fo + r * kEBoxW], bc[fo + r * kEBoxW + 32]));
+                    if constexpr (decltype(masked)::value) {
+                        const bool rin = Y0 + ib + r < h;
+                        const bool in0 = rin & c0, in1 = rin & c1;
+                        a12 = make_float2(in0 ? a12.x : 0.f, in1 ? a12.y : 0.f);
+                        df = make_float2(in0 ? df.x : 0.f, in1 ? df.y : 0.f);
+                        dc = make_float2(in0 ? dc.x : 0.f, in1 ? dc.y : 0.f);
+                    }
+                    s2[0] = __fadd2_rn(s2[0], a12);
+                    if (HF) s2[1] = __ffma2_rn(df, df, s2[1]);
+                    if (HC) s2[2] = __ffma2_rn(dc, dc, s2[2]);
+                    r0 = r1;
+                    r1 = r2;
                 }
-                if (HC) {
-                    const float d0 = r1.c.x - bc[fo + r * kEBoxW], d1 = r1.c.y - bc[fo + r * kEBoxW + 32];
-                    if (in0) s[2] = fmaf(d0, d0, s[2]);
-                    if (in1) s[2] = fmaf(d1, d1, s[2]);
-                }
-                r0 = r1;
-                r1 = r2;
-            }
+            };
+            if (full)
+                rows(std::integral_constant<bool, false>{});
+            else
+                rows(std::integral_constant<bool, true>{});
+            const float s[3] = {s2[0].x + s2[0].y, s2[1].x + s2[1].y, s2[2].x + s2[2].y};
 #pragma unroll
             for (int q = 0; q < 3; ++q) df_add(acc[q], s[q]);
         }
