@@ -134,6 +134,11 @@ struct TileCtx {
     int h, w;
     bool cin0, cin1;   // the two cells' columns lie inside the image
     bool out0, out1;   // ... and inside the output tile
+    // REPLICATE border tiles: the shared columns the two cells are computed at (their own, or for
+    // a cell outside the image the nearest image column's), and whether the cell is stored (its
+    // column lies in the image or is the ring column just outside it)
+    int jc0, jc1;
+    bool st0, st1;
     unsigned out_rows; // bit k: row ib + k is an output row inside the image
     float c_keep, c_h;
 };
@@ -164,26 +169,68 @@ __device__ __forceinline__ void tile_step(const float *__restrict__ src, float *
             d[0] = rv.x;
             d[32] = rv.y;
         } else if (WMODE == WRITE_BORDER) {
-            // tiles touching the border: cells outside the image keep 0 (ZERO) or are left
-            // for the ring refresh after the step (REPLICATE)
+            // tiles touching the border: cells outside the image keep 0 (ZERO)
             const int gy = c.Y0 + i;
             const bool rin = (gy >= 0) & (gy < c.h);
             const bool in0 = rin & c.cin0, in1 = rin & c.cin1;
             float *d = dst + i * P + c.j;
             const float2 rv = Store<S>::round2(v);
-            if (BND == BND_ZERO) {
-                d[0] = in0 ? rv.x : 0.0f;
-                d[32] = in1 ? rv.y : 0.0f;
-            } else {
-                if (in0) d[0] = rv.x;
-                if (in1) d[32] = rv.y;
-            }
+            d[0] = in0 ? rv.x : 0.0f;
+            d[32] = in1 ? rv.y : 0.0f;
         } else {
             // predicated stores, no branch: row Y0 + ib + k, columns gx and gx + 32
             const bool rk = (c.out_rows >> k) & 1u;
             S *o = orow + (int64_t)k * ld;
             if (rk & c.out0) Store<S>::store(o, v.x);
             if (rk & c.out1) Store<S>::store(o + 32, v.y);
+        }
+        r0 = r1;
+        r1 = r2;
+    }
+}
+
+// One Jacobi step of a REPLICATE border tile.  The ring just outside the image must hold, after
+// every step, the value of the image cell it replicates.  A cell of the ring columns (image column
+// -1 or w) is computed at its source column (jc0 / jc1: the same operands, so the same bits as the
+// source cell) and stored at its own; the ring rows (image rows -1 and h) are written by the
+// threads of image rows 0 and h - 1, which store their two values a row further out as well (a
+// warp-uniform branch, taken by one thread row of the tile), the corners included.  Cells of
+// other rows and columns outside the image are not stored: no in-image cell reads them.  So no
+// refresh pass and no extra CTA barrier separate the steps.
+template <typename S, int NW>
+__device__ __forceinline__ void tile_step_replicate_border(const float *__restrict__ src,
+                                                          float *__restrict__ dst, const TileCtx &c,
+                                                          const float2 (&g)[kRY]) {
+    constexpr int P = TGeom<S, NW>::P;
+    const float2 ch = make_float2(c.c_h, c.c_h), ck = make_float2(c.c_keep, c.c_keep);
+    const float *p0 = src + (c.ib - 1) * P + c.jc0, *p1 = src + (c.ib - 1) * P + c.jc1;
+    auto row = [&](int r) {
+        Row3 o;
+        o.w = make_float2(p0[r * P - 1], p1[r * P - 1]);
+        o.c = make_float2(p0[r * P], p1[r * P]);
+        o.e = make_float2(p0[r * P + 1], p1[r * P + 1]);
+        return o;
+    };
+    Row3 r0 = row(0), r1 = row(1);
+    const int top = -c.Y0 - c.ib, bottom = c.h - 1 - c.Y0 - c.ib;  // k of image rows 0 and h - 1
+#pragma unroll
+    for (int k = 0; k < kRY; ++k) {
+        const Row3 r2 = row(k + 2);
+        const float2 hw = half_laplace12_x2(r0.w, r0.c, r0.e, r1.w, r1.c, r1.e, r2.w, r2.c, r2.e);
+        const float2 rv = Store<S>::round2(__ffma2_rn(ch, hw, __ffma2_rn(ck, r1.c, g[k])));
+        const int gy = c.Y0 + c.ib + k;
+        float *d = dst + (c.ib + k) * P + c.j;
+        if ((gy >= 0) & (gy < c.h)) {
+            if (c.st0) d[0] = rv.x;
+            if (c.st1) d[32] = rv.y;
+        }
+        if (k == top) {
+            if (c.st0) d[-P] = rv.x;
+            if (c.st1) d[32 - P] = rv.y;
+        }
+        if (k == bottom) {
+            if (c.st0) d[P] = rv.x;
+            if (c.st1) d[32 + P] = rv.y;
         }
         r0 = r1;
         r1 = r2;
@@ -265,6 +312,18 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     c.cin1 = (c.gx + 32 >= 0) & (c.gx + 32 < w);
     c.out0 = c.cin0 & (c.gx >= x0) & (c.gx < x0 + owt);
     c.out1 = c.cin1 & (c.gx + 32 >= x0) & (c.gx + 32 < x0 + owt);
+    if (BND == BND_REPLICATE) {  // see tile_step_replicate_border
+        const int x1 = c.gx + 32;
+        c.jc0 = c.j + (min(max(c.gx, 0), w - 1) - c.gx);
+        c.jc1 = c.j + 32 + (min(max(x1, 0), w - 1) - x1);
+        c.st0 = (c.gx >= -1) & (c.gx <= w);
+        c.st1 = (x1 >= -1) & (x1 <= w);
+    } else {
+        c.jc0 = c.j;
+        c.jc1 = c.j + 32;
+        c.st0 = c.cin0;
+        c.st1 = c.cin1;
+    }
     // bit k of in_rows: image row Y0 + ib + k exists; of out_rows: it is also an output row.
     // Both are contiguous ranges of the thread's kRY rows.
     auto row_range = [](int lo, int hi) -> unsigned {  // bits [max(lo,0), min(hi,kRY))
@@ -278,15 +337,17 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     float2 g[kRY];
     const float2 cf = make_float2(jb.c_f, jb.c_f);
     if (!ftma) {
-        const S *fr = jb.f + (int64_t)(Y0 + c.ib) * jb.ld + c.gx;
+        // f at the columns the cells are computed at (REPLICATE: a ring-column cell takes its
+        // source cell's f)
+        const S *fr = jb.f + (int64_t)(Y0 + c.ib) * jb.ld + X0;
         const bool hasf = jb.f != nullptr;
 #pragma unroll
         for (int k = 0; k < kRY; ++k) {
             // predicated loads, no branch
             const bool rk = hasf & ((in_rows >> k) & 1u);
             const S *fk = fr + (int64_t)k * jb.ld;
-            const float a = (rk & c.cin0) ? Store<S>::load(fk) : 0.0f;
-            const float b = (rk & c.cin1) ? Store<S>::load(fk + 32) : 0.0f;
+            const float a = (rk & c.st0) ? Store<S>::load(fk + c.jc0) : 0.0f;
+            const float b = (rk & c.st1) ? Store<S>::load(fk + c.jc1) : 0.0f;
             g[k] = __fmul2_rn(cf, make_float2(a, b));
         }
     }
@@ -305,10 +366,11 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
             return false;
         }
         if (ftma) {  // f as loaded by TMA: zero outside the image, like the plain loads' predicates
-            const S *fr = static_cast<const S *>(fwin) + c.ib * LW + c.j;
+            const S *fr = static_cast<const S *>(fwin) + c.ib * LW;
 #pragma unroll
             for (int k = 0; k < kRY; ++k)
-                g[k] = __fmul2_rn(cf, make_float2(Store<S>::to_float(fr[k * LW]), Store<S>::to_float(fr[k * LW + 32])));
+                g[k] = __fmul2_rn(cf, make_float2(Store<S>::to_float(fr[k * LW + c.jc0]),
+                                                  Store<S>::to_float(fr[k * LW + c.jc1])));
         }
         if constexpr (sizeof(S) != 4) {  // widen the staged 16-bit box, 8 elements per 16-byte access
             static_assert((LH * LW) % 8 == 0, "the staged box is a whole number of 16-byte chunks");
@@ -347,12 +409,13 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
             tile_step<WRITE_INTERIOR, S, BND, NW>(src, dst, c, g);
             __syncthreads();
         } else {
-            if (!idle) tile_step<WRITE_BORDER, S, BND, NW>(src, dst, c, g);
-            __syncthreads();
-            if (BND == BND_REPLICATE) {
-                refresh_ring<S, LH, NT>(dst, X0, Y0, h, w, tid);
-                __syncthreads();
+            if (!idle) {
+                if constexpr (BND == BND_REPLICATE)
+                    tile_step_replicate_border<S, NW>(src, dst, c, g);
+                else
+                    tile_step<WRITE_BORDER, S, BND, NW>(src, dst, c, g);
             }
+            __syncthreads();
         }
     };
     // Single images and 16-warp batch tiles unroll the T - 1 steps (T is a template parameter):
