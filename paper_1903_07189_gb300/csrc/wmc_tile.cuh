@@ -32,9 +32,11 @@
 //
 // Image boundary.  ZERO: the TMA fill supplies the zeros; in tiles touching the border, cells
 // outside the image are rewritten as 0 every step.  REPLICATE: the ring of cells just outside
-// the image is kept equal to its nearest in-image cell (refreshed after the load and after every
-// step, in tiles touching the border only), so in-image cells read their neighbours without any
-// clamping and produce exactly what clamped reads would.  Warps whose cells all lie beyond that
+// the image is kept equal to its nearest in-image cell (refreshed once after the load; after each
+// step the ring-column cells are computed at their source columns and the ring rows stored by the
+// edge rows' threads, in tiles touching the border only), so in-image cells read their
+// neighbours without any clamping and produce exactly what clamped reads would.  Warps whose
+// cells all lie beyond that
 // ring (tiles overhanging the image) skip the arithmetic: no in-image cell reads those cells.
 //
 // The update's f term (c_f f, constant over the T steps) sits in registers, 8 rows x 2 columns
