@@ -3,20 +3,24 @@
 //   U^{t+1} = U^t + step * (lambda * H^w(U^t) - (2 d^{t+1} - d^t) / alpha).
 // The step reads U^t (3x3 neighbourhood), f and d^t, and writes U^{t+1} and d^{t+1}: 20 bytes per
 // pixel in FP32, so it streams like the single-pass flow kernel -- a warp owns 64 columns (lane =
-// column pair, neighbours by shuffle), a thread walks a strip of kStreamRY rows with every load
-// issued up front.  d is per pixel (no neighbours), so it is updated in place.
+// column pair, neighbours by shuffle), a thread walks a strip of kL1Rows rows with every load
+// issued up front.  d is per pixel (no neighbours), so it is updated in place.  Strips of 4 rows
+// with 4 CTAs per SM: 8-row strips at 3 CTAs per SM spilled 64-112 bytes (the stencil's per-row
+// values shared down the strip are many registers) and ran 248 against 303 Gpix-iter/s at 4096^2.
 #include "wmc_device.cuh"
 #include "wmc_internal.h"
 #include "wmc_stream.cuh"
 
 namespace wmc {
 
+constexpr int kL1Rows = 4;
+
 template <int BND, bool VEC>
-__global__ void __launch_bounds__(kStreamWarps * 32, 3)
+__global__ void __launch_bounds__(kStreamWarps * 32, 4)
     l1_step_kernel(const float *__restrict__ u, const float *__restrict__ f, float *__restrict__ d,
                    float *__restrict__ out, int h, int w, int64_t ld, float c_h, float c_d,
                    float alpha) {
-    constexpr int R = kStreamRY;
+    constexpr int R = kL1Rows;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
@@ -80,7 +84,7 @@ cudaError_t launch_l1_step(int bnd, const float *u, const float *f, float *d, fl
                            int32_t w, int64_t ld, float c_h, float c_d, float alpha, bool vec,
                            cudaStream_t st) {
     const int64_t nbx = (w + kStreamWarps * 64 - 1) / (kStreamWarps * 64);
-    const int64_t nby = (h + kStreamRY - 1) / kStreamRY;
+    const int64_t nby = (h + kL1Rows - 1) / kL1Rows;
     if (nbx * nby > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const unsigned g = (unsigned)(nbx * nby), b = kStreamWarps * 32;
     if (bnd == BND_ZERO) {
