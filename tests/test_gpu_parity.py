@@ -419,12 +419,13 @@ def test_denoise_graph_capture_replay():
 
 @pytest.mark.parametrize("bnd", ["replicate", "zero"])
 @pytest.mark.parametrize("shape", [(59, 123), (117, 245), (51, 115), (27, 123), (53, 245), (175, 65),
-                                   (3, 130), (130, 3), (61, 61)])
+                                   (3, 130), (130, 3), (61, 61), (1, 1), (1, 200), (200, 1), (2, 300)])
 def test_overhanging_tiles_bitwise_invariant(bnd, shape):
     """Images one cell past a whole number of output tiles (128 x 64 regions: 122 x 58 at T = 4,
     114 x 50 at T = 8; 128 x 32 regions: 122 x 26 at T = 4), where the last tile row or column
-    overhangs the image and its outer warps skip work: every T and tile shape still gives the
-    one-step-per-launch bits."""
+    overhangs the image and its outer warps skip work, and images one or two cells high or wide,
+    whose border tiles compute every cell from a clamped column or store it into a ring row: every
+    T and tile shape still gives the one-step-per-launch bits."""
     f = to_gpu(synth.make_image(*shape, seed=sum(shape), sigma=0.1))
     ref = wmc().denoise(f, 1.0, 0.25, 11, bnd, steps_per_launch=1)
     for tile in (1, 2):
