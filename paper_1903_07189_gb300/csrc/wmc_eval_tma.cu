@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
     __syncthreads();  // the barriers are initialised before anyone waits on them
     const float2 sc = make_float2(p.scale, p.scale);
     int n = 0;
+    // box coordinates stepped along with b (no division per box)
+    int cbx = (int)blockIdx.x % p.nbx, cby = (int)blockIdx.x / p.nbx;
+    const int sdx = stride % p.nbx, sdy = stride / p.nbx;
     for (int b = blockIdx.x; b < p.nboxes; b += stride, ++n) {
         const int k = n % NS;
         const uint32_t phase = (uint32_t)(n / NS) & 1u;
@@ -98,8 +101,13 @@ __global__ void __launch_bounds__(kTileThreadsV2, 2)
                   mbar_wait_bounded(smem_u32(&full[k]), phase, kWaitLimitNs);
         if (tid == 0 && ok) pending &= ~(1u << k);
         if (!ok) *static_cast<volatile int *>(&abort_flag) = 1;
-        int X0, Y0;
-        box_xy(b, X0, Y0);
+        const int X0 = cbx * kEvalBoxW - kEvalX, Y0 = cby * kEvalBoxH - 1;
+        cbx += sdx;
+        cby += sdy;
+        if (cbx >= p.nbx) {
+            cbx -= p.nbx;
+            ++cby;
+        }
         const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
         if (BND == BND_REPLICATE && border) {  // the same decision in every thread of the CTA
             const bool bad = __syncthreads_or(!ok);

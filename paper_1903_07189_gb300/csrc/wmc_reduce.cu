@@ -426,6 +426,9 @@ __global__ void __launch_bounds__(kEThreads, 1)
     volatile int *abort_v = &abort_flag;
     DF acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     int n = 0;
+    // box coordinates stepped along with b (no division per box)
+    int cbx = (int)blockIdx.x % nbx, cby = (int)blockIdx.x / nbx;
+    const int sdx = stride % nbx, sdy = stride / nbx;
     for (int b = blockIdx.x; b < nboxes; b += stride, ++n) {
         const int k = n & 1;
         const uint32_t phase = (uint32_t)(n >> 1) & 1u;
@@ -434,7 +437,13 @@ __global__ void __launch_bounds__(kEThreads, 1)
         bool ok = !*abort_v && mbar_wait_bounded(smem_u32(&full[k]), phase, kWaitLimitNs);
         if (tid == 0 && ok) pending &= ~(1u << k);
         if (!ok) *abort_v = 1;
-        const int by = b / nbx, bx = b - by * nbx;
+        const int bx = cbx, by = cby;
+        cbx += sdx;
+        cby += sdy;
+        if (cbx >= nbx) {
+            cbx -= nbx;
+            ++cby;
+        }
         const int X0 = bx * kEBoxW - 4, Y0 = by * kEBoxH - 1;
         const bool border = (X0 < 0) | (Y0 < 0) | (X0 + LW > w) | (Y0 + LH > h);
         if (BND == BND_REPLICATE && border) {  // the same decision in every thread of the CTA
