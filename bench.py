@@ -236,6 +236,21 @@ def oracle_parity(u, gpu_result, crop: int, iters: int, threads: int):
                     "is valid and moves the pixel by about 2 step lambda |H^w|"}
 
 
+def energy_parity(wmc, f, out, ws, ews, iters: int, T: int, u_host):
+    """The CPU-baseline leg's check of the step's energies (Eq. wmcr with q = 1 and the data term
+    of Eq. 1): the GPU's sum |H^w| and 1/2 sum (U - f)^2 of its U^iters over the whole image
+    against the FP64 oracle's sums of the same U (read back) and f.  The GPU sums FP32 per-pixel
+    terms in 16-cell FP32 partials and double-float accumulators; the relative errors say what
+    that leaves of FP64."""
+    import oracle
+    uf = wmc.denoise(f, LAM, STEP, iters, out=out, steps_per_launch=T, workspace=ws)
+    eg = wmc.energy(uf, f, None, workspace=ews).cpu().tolist()
+    eo = oracle.energies(uf.double().cpu().numpy(), np.asarray(u_host, dtype=np.float64))
+    return {"image": f"{H}x{W}, U after {iters} iterations", "gpu": eg[:2], "oracle": list(eo[:2]),
+            "rel_err": [abs(eg[k] - eo[k]) / abs(eo[k]) if eo[k] else abs(eg[k]) for k in range(2)],
+            "terms": ["sum |H^w|", "1/2 sum (U - f)^2"]}
+
+
 def host_threads() -> int:
     return os.cpu_count() or 1
 
@@ -688,6 +703,8 @@ def run_gpu(args):
                                  "sample": f"512x512 top-left crop, 32 iterations ({dt1:.1f} s)"},
                "sample": f"2048x2048 top-left crop, 32 iterations (FP64 oracle, {threads} threads, {dt:.1f} s wall, "
                          f"{dt * threads:.0f} core-s)"}
+        # the step's FP64 energies (of U^iters and f, whole image) against the oracle's on the same U
+        cpu["energy_parity"] = energy_parity(wmc, f, out, ws, ews, iters, T, u_host)
         # the same crop and iterations on the GPU, in the bench's launch configuration, against it
         g32 = wmc.denoise(f, LAM, STEP, 32, out=out, steps_per_launch=T, workspace=ws)
         cpu["parity"] = oracle_parity(u_host, g32[:2048, :2048].double().cpu().numpy(), 2048, 32, threads)
