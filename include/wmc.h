@@ -114,7 +114,10 @@ wmc_status_t wmc_eval_status(wmc_stream_t stream);
  *   iters >= 0 (0 copies U^0 to u).
  *   workspace: device, >= wmc_denoise_workspace_size() bytes, WMC_WORKSPACE_ALIGN-aligned,
  *   must not overlap f, u0 or u (not needed when iters == 0).  It holds a status word (first
- *   bytes, cleared by every call) and one ping-pong image; see wmc_denoise_status().  When the
+ *   bytes, cleared by every call), one ping-pong image and one flag word per tile of the
+ *   multi-step launches (at the end, cleared by every call that makes more than one such
+ *   launch: a tile of a launch waits for the flags of the tiles of the previous launch that it
+ *   reads, not for that whole launch); see wmc_denoise_status().  When the
  *   row pitch is not a multiple of 16 bytes (ld not a multiple of 4 elements for FP32, of 8 for
  *   BF16/FP16) the multi-step kernels cannot read the images through TMA: the workspace then
  *   holds three images of the next aligned pitch, the call copies U^0 and f into two of them,
@@ -148,9 +151,10 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
 
 /* wmc_denoise_status: synchronises `stream` and reads the status word of a workspace last used
  * by wmc_denoise / wmc_denoise_ex / wmc_denoise_host.  The multi-step kernels wait for their
- * asynchronous (TMA) tile loads with a time limit of 0.2 s; a wait that runs out makes that CTA
- * skip its tile and sets the word, and this returns WMC_ERR_TIMEOUT (the output is then
- * incomplete).  WMC_OK otherwise.  workspace: device pointer passed to that call. */
+ * asynchronous (TMA) tile loads, and for the flags of the previous launch's tiles they read, with
+ * a time limit of 0.2 s; a load wait that runs out makes that CTA skip its tile, a flag wait that
+ * runs out lets it go ahead, both set the word, and this returns WMC_ERR_TIMEOUT (the output is
+ * then wrong or incomplete).  WMC_OK otherwise.  workspace: device pointer passed to that call. */
 wmc_status_t wmc_denoise_status(const void *workspace, wmc_stream_t stream);
 
 /* wmc_selftest_wait_timeout: exercises the failure path of those bounded waits without a fault.

@@ -175,14 +175,47 @@ int64_t aligned_pitch(int32_t w, size_t es) {
     return (w + A - 1) / A * A;
 }
 
-// The flow on device buffers; all checks done by the caller.  `ws` holds the status word (first
-// kStatusBytes) followed by one image of pitch ld, or, for pitches TMA cannot describe, three
-// images of an aligned pitch (two ping-pong images and a copy of f), so that every buffer a
-// multi-step launch reads is TMA-readable and only the last launch touches u.
+// Output tile of T steps per launch with tile shape `tile`: the region less T - 1 cells (plus the
+// region's own halo) on each side.
+void out_tile(int T, int tile, int *owt, int *oht) {
+    *owt = wmc::kCW + 2 - 2 * T;
+    *oht = wmc::kQR * wmc::tile_warps(tile) + 2 - 2 * T;
+}
+
+// Per-tile completion flags of a flow run: one word per tile of the largest tile grid any
+// multi-step launch of an h x w image can have (8 steps per launch, the 128 x 32 region).
+int64_t flow_flag_words(int32_t h, int32_t w) {
+    int64_t most = 0;
+    for (int tile = 1; tile <= kTileShapes; ++tile)
+        for (int T = 2; T <= wmc::kMaxSteps; ++T) {
+            int owt, oht;
+            out_tile(T, tile, &owt, &oht);
+            most = std::max(most, (int64_t)((w + owt - 1) / owt) * ((h + oht - 1) / oht));
+        }
+    return most;
+}
+
+// Workspace of run_flow without the flags: the status word (first kStatusBytes) followed by one
+// image of pitch ld, or, for pitches TMA cannot describe, three images of an aligned pitch (two
+// ping-pong images and a copy of f), and at least one image of pitch ld for the calls that are
+// not staged (one launch, or one step per launch).
+size_t flow_core_bytes(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype) {
+    const size_t es = elem_size(dtype);
+    if (staged_pitch(ld, es))
+        return std::max(3 * image_bytes(h, aligned_pitch(w, es), dtype), image_bytes(h, ld, dtype)) + kStatusBytes;
+    return image_bytes(h, ld, dtype) + kStatusBytes;
+}
+
+// The flow on device buffers; all checks done by the caller.  `ws` holds what flow_core_bytes
+// counts, so that every buffer a multi-step launch reads is TMA-readable and only the last launch
+// touches u.  `flags` (flow_flag_words words, or nullptr): the tiles of consecutive launches with
+// the same tile grid then wait only for the tiles of the previous launch they depend on, instead
+// of for that whole launch.
 wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t w, int64_t ld,
                       wmc_dtype_t dtype, float lambda, float step, int32_t iters,
                       wmc_boundary_t bnd, int steps_per_launch, void *ws, cudaStream_t st,
-                      bool fd = false, int tile = kDefaultTile, bool default_config = false) {
+                      bool fd = false, int tile = kDefaultTile, bool default_config = false,
+                      unsigned int *flags = nullptr) {
     const size_t es = elem_size(dtype);
     if (!u0) u0 = f;
     if (h == 0 || w == 0) return WMC_OK;
@@ -263,9 +296,16 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
     memset(&fmap, 0, sizeof fmap);
     const bool f_tma = T > 1 && f_read != nullptr && encode_window_map(&fmap, f_read, dtype, h, w, ld_in, tile);
 
+    // the flags start at 0 in every run; launch number e (1, 2, ...) stores e into each of its tiles'
+    if (T == 1 || nl == 1) flags = nullptr;
+    if (flags) {
+        e = cudaMemsetAsync(flags, 0, (size_t)flow_flag_words(h, w) * sizeof(unsigned int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "clear tile flags");
+    }
     int src_id = 0;
     int done = 0;
     bool prev_tile = false;
+    int prev_s = 0, epoch = 0;
     for (int k = 0; k < nl; ++k) {
         const int s = (iters - done) < T ? (iters - done) : T;
         const bool last = k == nl - 1;
@@ -301,11 +341,18 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
             tp.status = status;
             tp.pdl = prev_tile ? 1 : 0;  // follows a tile launch: may overlap its tail
             tp.f_tma = (f_tma && tma[src_id]) ? 1 : 0;
+            if (flags) {
+                // the previous launch has the same tile grid: wait for its tiles, not for all of it
+                tp.flags = flags;
+                tp.flag_wait = (prev_tile && prev_s == s && tma[src_id]) ? epoch : 0;
+                tp.flag_set = ++epoch;
+            }
             alignas(64) CUtensorMap pair[2] = {maps[src_id], fmap};
             e = launch_tile(dtype, bnd, tile, s, pair, tp, -1, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "flow kernel launch");
         prev_tile = s > 1;
+        prev_s = s;
         src = dst;
         src_id = 1 + (k & 1);
         done += s;
@@ -365,13 +412,6 @@ struct BatchPlan {
     uint32_t magic;
 };
 static_assert(sizeof(BatchPlan) <= sizeof(wmc_batch_t), "plan does not fit wmc_batch_t");
-
-// Output tile of T steps per launch with tile shape `tile`: the region less T - 1 cells (plus the
-// region's own halo) on each side.
-void out_tile(int T, int tile, int *owt, int *oht) {
-    *owt = wmc::kCW + 2 - 2 * T;
-    *oht = wmc::kQR * wmc::tile_warps(tile) + 2 - 2 * T;
-}
 
 struct BatchLayout {
     size_t off_images, off_tiles, off_bufs, total;
@@ -687,11 +727,14 @@ wmc_status_t wmc_eval_fd(const void *u, void *hw, int32_t h, int32_t w, int64_t 
 size_t wmc_denoise_workspace_size(int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype) {
     const size_t es = elem_size(dtype);
     if (h <= 0 || w <= 0 || ld < w || es == 0) return 0;
-    // staged pitches: three aligned images, and at least one image of pitch ld for the calls that
-    // are not staged (one launch, or one step per launch)
-    if (staged_pitch(ld, es))
-        return std::max(3 * image_bytes(h, aligned_pitch(w, es), dtype), image_bytes(h, ld, dtype)) + kStatusBytes;
-    return image_bytes(h, ld, dtype) + kStatusBytes;
+    // run_flow's images and status word, then the per-tile flags
+    return flow_core_bytes(h, w, ld, dtype) +
+           round_up((size_t)flow_flag_words(h, w) * sizeof(unsigned int), WMC_WORKSPACE_ALIGN);
+}
+
+// The flags' place in a workspace of wmc_denoise_workspace_size bytes.
+unsigned int *flow_flags(void *workspace, int32_t h, int32_t w, int64_t ld, wmc_dtype_t dtype) {
+    return reinterpret_cast<unsigned int *>(static_cast<char *>(workspace) + flow_core_bytes(h, w, ld, dtype));
 }
 
 wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, int32_t w,
@@ -718,7 +761,8 @@ wmc_status_t wmc_denoise_ex(const void *f, const void *u0, void *u, int32_t h, i
             return fail(WMC_ERR_ALIAS, "workspace overlaps an image");
     }
     return run_flow(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, T, workspace,
-                    (cudaStream_t)stream, false, tile, dflt);
+                    (cudaStream_t)stream, false, tile, dflt,
+                    iters > 0 ? flow_flags(workspace, h, w, ld, dtype) : nullptr);
 }
 
 int32_t wmc_denoise_cluster_size(int32_t h, int32_t w, int32_t iters) {
@@ -803,7 +847,7 @@ wmc_status_t wmc_denoise_host(const void *f_host, const void *u0_host, void *u_h
                                        cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_fail(e, "copy u0 to device");
     s = run_flow(d_f, d_u0, d_u, h, w, ld, dtype, lambda, step, iters, bnd, T, d_ws, st, false,
-                 kDefaultTile, true);
+                 kDefaultTile, true, flow_flags(d_ws, h, w, ld, dtype));
     if (s != WMC_OK) return s;
     if ((e = cudaMemcpy2DAsync(u_host, pitch, d_u, pitch, w * es, h, cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
@@ -1374,6 +1418,7 @@ wmc_status_t wmc_denoise_noalloc(const void *f, const void *u0, void *u, int32_t
         check_flow_args(f, u0, u, h, w, ld, dtype, lambda, step, iters, bnd, nullptr, &T);
     if (s != WMC_OK) return s;
     if (h == 0 || w == 0) return WMC_OK;
+    // (this entry point chains its launches without the per-tile flags, which the size counts)
     const size_t need = wmc_denoise_workspace_size(h, w, ld, dtype);
     if (need > kNoAllocScratchBytes)
         return fail(WMC_ERR_INVALID_ARG,

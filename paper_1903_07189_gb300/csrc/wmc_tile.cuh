@@ -126,6 +126,13 @@ struct TileParams {
     unsigned int *status; // device status word (bit 0: a bounded wait gave up) or nullptr
     int32_t pdl;          // host side: launch as a programmatic dependent of the previous launch
     int32_t f_tma;        // single image: f is read through the second tensor map
+    // single image: per-tile completion flags of this run (one word per tile of this launch's tile
+    // grid, zeroed before the run's first launch).  flag_wait > 0: before reading U^t a tile waits
+    // until the flags of its 3 x 3 neighbouring tiles are >= flag_wait (the previous launch, same
+    // tile grid, has finished those tiles) instead of waiting for the whole previous launch;
+    // flag_set > 0: the tile stores flag_set into its own flag once its output is written.
+    unsigned int *flags;
+    int32_t flag_wait, flag_set;
 };
 
 // ------------------------------------------------------------------------------- kernel
@@ -257,10 +264,10 @@ template <typename S> struct TileJob {
 // write the output tile through `out_of()` (called after the steps, so the output pointer is not
 // kept in registers through them).  `phase` is the mbarrier parity this tile's load completes.
 // Returns false if the window load timed out (the status word is set).
-template <int T, typename S, int BND, int NW, bool UNROLL, typename OutFn>
+template <int T, typename S, int BND, int NW, bool UNROLL, typename OutFn, typename DepFn>
 __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht, unsigned int *status,
                                          float *buf0, float *buf1, uint64_t *bar, uint32_t phase,
-                                         OutFn out_of) {
+                                         OutFn out_of, DepFn wait_input) {
     using G = TGeom<S, NW>;
     constexpr int LW = G::LW, LH = G::LH, BUF = G::BUF, P = G::P, NT = G::THREADS;
     TileCtx c;
@@ -276,8 +283,10 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
 
     // ---- issue the load of the window of U^t (thread 0 alone owns the barrier: it issues the
     // copy and later waits for it, so the other threads never poll it).  U^t is the previous
-    // launch's output: wait for that launch first (every later access of this CTA to U^t or to
-    // the output buffer comes after this thread's wait through the CTA barriers below).
+    // launch's output: wait for it first (`wait_input`: the whole previous launch, or the tiles
+    // of it that this window reads and this output tile overwrites; every later access of this CTA
+    // to U^t or to the output buffer comes after this thread's wait through the CTA barriers
+    // below).
     // f's window (same box and origin as U's) completes the same barrier: FP32 into the third
     // buffer, 16-bit storage into buffer 1 (read into registers before the first step writes
     // buffer 1).  f is never written by a flow launch, so its copy goes out before the wait for
@@ -289,7 +298,7 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
         if (tid == 0) {
             mbar_expect_tx(smem_u32(bar), (uint32_t)(LW * LH * sizeof(S)) * (ftma ? 2u : 1u));
             if (ftma) tma_load_2d(smem_u32(fwin), jb.fmap, X0, Y0, smem_u32(bar));
-            griddep_wait();
+            wait_input();
             tma_load_2d(smem_u32(stage), jb.map, X0, Y0, smem_u32(bar));
         }
     } else {
@@ -439,6 +448,49 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     return true;
 }
 
+// Thread 0 of a tile of a chained launch: wait (bounded) until the 3 x 3 tiles around (tx, ty) of
+// the previous launch have stored a flag >= need.  Their outputs are this window's U^t (a window
+// reaches at most T + 4 < one tile into its neighbours), and they are the only tiles of that
+// launch whose windows cover this tile's output region, so their completion also ends every read
+// of it.  Every tile they wait for is already running: a chained launch is scheduled only once
+// every CTA of the previous one has started.  A wait that gives up sets bit 0 of the status word
+// (and then the load goes ahead: the run's result is reported as failed); a tile that finds the
+// bit set does not wait, so one late tile does not make every later one wait out its limit.
+__device__ __forceinline__ void wait_tile_flags(const unsigned int *flags, int tx, int ty, int ntx, int nty,
+                                                unsigned int need, unsigned int *status) {
+    // the least of the nine flags, read at once (relaxed loads: one memory round trip); only a
+    // tile whose neighbours are not all done polls again
+    auto least = [&]() {
+        unsigned int v[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {  // all nine loads issued before any result is used
+            const int x = tx + q % 3 - 1, y = ty + q / 3 - 1;
+            v[q] = ((x >= 0) & (x < ntx) & (y >= 0) & (y < nty)) ? ld_relaxed_gpu(flags + (int64_t)y * ntx + x)
+                                                                 : need;
+        }
+        unsigned int low = need;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) low = min(low, v[q]);
+        return low;
+    };
+    if (least() < need) {
+        const uint64_t t0 = global_timer_ns();
+        for (;;) {
+            __nanosleep(64);
+            if (least() >= need) break;
+            if (status && (*static_cast<volatile unsigned int *>(status) & 1u)) break;  // another wait gave up
+            if (global_timer_ns() - t0 > kWaitLimitNs) {
+                if (status) atomicOr(status, 1u);
+                break;
+            }
+        }
+    }
+    // the relaxed loads that saw the flags, then this fence: an acquire of the neighbours' release
+    // stores; then what it made visible is ordered before this thread's TMA reads
+    __threadfence();
+    fence_proxy_async_global();
+}
+
 template <int T, typename S, int BND, bool BATCH, int NW>
 __global__ void __launch_bounds__(32 * NW, 32 / NW)
     tile_flow_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap fmap,
@@ -487,6 +539,16 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW)
         jb.x0 = tx * p.owt;
         jb.y0 = ty * p.oht;
     }
+    // U^t ready: the tiles of the previous launch that this one depends on (flags), else that
+    // whole launch
+    auto wait_input = [&]() {
+        if (!BATCH && p.flag_wait > 0) {
+            const int ty = blockIdx.x / p.ntx, tx = blockIdx.x - ty * p.ntx;
+            wait_tile_flags(p.flags, tx, ty, p.ntx, ((int)gridDim.x) / p.ntx, (unsigned)p.flag_wait, p.status);
+        } else {
+            griddep_wait();
+        }
+    };
     // the next launch may be scheduled once every CTA of this one is running
     griddep_launch_dependents();
     if (jb.use_tma && threadIdx.x == 0) mbar_init(smem_u32(&bar), 1);
@@ -500,7 +562,13 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW)
         }
         *ldo = p.ld_out;
         return static_cast<S *>(p.out);
-    });
+    }, wait_input);
+    // publish this tile's completion: every thread's output stores (and its reads of U^t) come
+    // before the CTA barrier, and so before thread 0's release store of the flag
+    if (!BATCH && p.flag_set > 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) st_release_gpu(p.flags + blockIdx.x, (unsigned)p.flag_set);
+    }
 }
 
 template <int T, typename S, int BND, bool BATCH, int NW>

@@ -66,19 +66,30 @@ def test_status_strings(lib):
     assert lib.wmc_version() >= 100
 
 
+def _flag_bytes(h, w):
+    """One 4-byte flag per tile of the largest tile grid of a multi-step launch: output tiles of
+    (130 - 2T) x (4 NW + 2 - 2T) cells for T = 2..8 steps and NW = 16 or 8 warps, rounded up to
+    256 bytes."""
+    most = max(-(-w // (130 - 2 * T)) * -(-h // (4 * nw + 2 - 2 * T)) for T in range(2, 9) for nw in (16, 8))
+    return -(-4 * most // 256) * 256
+
+
 def test_workspace_sizes(lib):
     assert lib.wmc_denoise_workspace_size(0, 5, 5, 0) == 0
-    # status word (256 bytes) + one image rounded up to 256 bytes
-    assert lib.wmc_denoise_workspace_size(3, 5, 8, 0) == 256 + 256
-    assert lib.wmc_denoise_workspace_size(100, 100, 128, 1) == 256 + (100 * 128 * 2 + 255) // 256 * 256
+    # status word (256 bytes) + one image rounded up to 256 bytes + the tile flags
+    assert _flag_bytes(3, 5) == 256 and _flag_bytes(4096, 4096) == 129 * 256  # 36 x 228 tiles
+    assert lib.wmc_denoise_workspace_size(3, 5, 8, 0) == 256 + 256 + 256
+    assert lib.wmc_denoise_workspace_size(100, 100, 128, 1) == 256 + (100 * 128 * 2 + 255) // 256 * 256 + 256
+    assert lib.wmc_denoise_workspace_size(4096, 4096, 4096, 0) == 256 + 4096 * 4096 * 4 + 129 * 256
     assert lib.wmc_denoise_workspace_size(4, 5, 4, 0) == 0  # ld < w
     # pitches that are not a multiple of 16 bytes are staged: three images of the aligned pitch
     # (FP32: a multiple of 4 elements; 16-bit: of 8), or one of pitch ld if that is larger
-    assert lib.wmc_denoise_workspace_size(10, 10, 10, 0) == 256 + 3 * 512  # pitch 12: 480 -> 512 B
-    assert lib.wmc_denoise_workspace_size(10, 10, 12, 0) == 256 + 512      # aligned: one image
-    assert lib.wmc_denoise_workspace_size(10, 10, 11, 1) == 256 + 3 * 512  # 16-bit, pitch 16: 320 -> 512 B
-    assert lib.wmc_denoise_workspace_size(2, 3, 201, 0) == 256 + (2 * 201 * 4 + 255) // 256 * 256
-    assert lib.wmc_denoise_host_workspace_size(10, 10, 10, 0) == 3 * 512 + 256 + 3 * 512
+    assert lib.wmc_denoise_workspace_size(10, 10, 10, 0) == 256 + 3 * 512 + 256  # pitch 12: 480 -> 512 B
+    assert lib.wmc_denoise_workspace_size(10, 10, 12, 0) == 256 + 512 + 256      # aligned: one image
+    assert lib.wmc_denoise_workspace_size(10, 10, 11, 1) == 256 + 3 * 512 + 256  # 16-bit, pitch 16: 320 -> 512 B
+    assert lib.wmc_denoise_workspace_size(2, 3, 201, 0) == 256 + (2 * 201 * 4 + 255) // 256 * 256 + 256
+    # f, U^0 and U on the device, then wmc_denoise's workspace (tile flags included)
+    assert lib.wmc_denoise_host_workspace_size(10, 10, 10, 0) == 3 * 512 + 256 + 3 * 512 + 256
     assert lib.wmc_energy_workspace_size(10, 10) % 256 == 0
 
 
