@@ -296,8 +296,20 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
     memset(&fmap, 0, sizeof fmap);
     const bool f_tma = T > 1 && f_read != nullptr && encode_window_map(&fmap, f_read, dtype, h, w, ld_in, tile);
 
-    // the flags start at 0 in every run; launch number e (1, 2, ...) stores e into each of its tiles'
+    // the flags start at 0 in every run; launch number e (1, 2, ...) stores e into each of its
+    // tiles'.  They pay where a launch spans more than one wave of CTAs (2 per SM): below that,
+    // a launch's tiles depend on most of the previous launch anyway and the wait for all of it
+    // is cheaper than the flags' round trips.
     if (T == 1 || nl == 1) flags = nullptr;
+    if (flags) {
+        int owt, oht, dev = 0, nsm = 0;
+        out_tile(T, tile, &owt, &oht);
+        const int64_t ntiles = (int64_t)((w + owt - 1) / owt) * ((h + oht - 1) / oht);
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "query the SM count");
+        if (ntiles <= 2 * (int64_t)nsm) flags = nullptr;
+    }
     if (flags) {
         e = cudaMemsetAsync(flags, 0, (size_t)flow_flag_words(h, w) * sizeof(unsigned int), st);
         if (e != cudaSuccess) return cuda_fail(e, "clear tile flags");

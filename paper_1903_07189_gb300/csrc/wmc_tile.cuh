@@ -297,8 +297,9 @@ __device__ __forceinline__ bool tile_job(const TileJob<S> &jb, int owt, int oht,
     if (jb.use_tma) {
         if (tid == 0) {
             mbar_expect_tx(smem_u32(bar), (uint32_t)(LW * LH * sizeof(S)) * (ftma ? 2u : 1u));
+            wait_input(false);  // per-tile dependencies: before f's copy, which their fence need not wait for
             if (ftma) tma_load_2d(smem_u32(fwin), jb.fmap, X0, Y0, smem_u32(bar));
-            wait_input();
+            wait_input(true);   // the whole previous launch: after f's copy, which then overlaps the wait
             tma_load_2d(smem_u32(stage), jb.map, X0, Y0, smem_u32(bar));
         }
     } else {
@@ -541,11 +542,12 @@ __global__ void __launch_bounds__(32 * NW, 32 / NW)
     }
     // U^t ready: the tiles of the previous launch that this one depends on (flags), else that
     // whole launch
-    auto wait_input = [&]() {
-        if (!BATCH && p.flag_wait > 0) {
+    auto wait_input = [&](bool late) {
+        const bool by_flags = !BATCH && p.flag_wait > 0;
+        if (by_flags && !late) {
             const int ty = blockIdx.x / p.ntx, tx = blockIdx.x - ty * p.ntx;
             wait_tile_flags(p.flags, tx, ty, p.ntx, ((int)gridDim.x) / p.ntx, (unsigned)p.flag_wait, p.status);
-        } else {
+        } else if (!by_flags && late) {
             griddep_wait();
         }
     };
