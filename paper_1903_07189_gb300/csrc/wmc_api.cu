@@ -182,6 +182,9 @@ void out_tile(int T, int tile, int *owt, int *oht) {
     *oht = wmc::kQR * wmc::tile_warps(tile) + 2 - 2 * T;
 }
 
+// Launches of more waves of CTAs than this wait for the whole previous launch (see run_flow).
+constexpr int kFlagMaxWaves = 10;
+
 // Per-tile completion flags of a flow run: one word per tile of the largest tile grid any
 // multi-step launch of an h x w image can have (8 steps per launch, the 128 x 32 region).
 int64_t flow_flag_words(int32_t h, int32_t w) {
@@ -297,9 +300,11 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
     const bool f_tma = T > 1 && f_read != nullptr && encode_window_map(&fmap, f_read, dtype, h, w, ld_in, tile);
 
     // the flags start at 0 in every run; launch number e (1, 2, ...) stores e into each of its
-    // tiles'.  They pay where a launch spans more than one wave of CTAs (2 per SM): below that,
-    // a launch's tiles depend on most of the previous launch anyway and the wait for all of it
-    // is cheaper than the flags' round trips.
+    // tiles'.  They cost each tile a memory round trip before its load and a release after its
+    // stores (about 5 % of a launch on its own), and save the previous launch's last wave, which
+    // the wait for that whole launch leaves partly idle: a gain for launches of a few waves of
+    // CTAs (2 per SM), a loss for one wave or less (a launch's tiles then depend on most of the
+    // previous launch anyway) and for many waves (the last wave is then a small part).
     if (T == 1 || nl == 1) flags = nullptr;
     if (flags) {
         int owt, oht, dev = 0, nsm = 0;
@@ -308,7 +313,7 @@ wmc_status_t run_flow(const void *f, const void *u0, void *u, int32_t h, int32_t
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_fail(e, "query the SM count");
-        if (ntiles <= 2 * (int64_t)nsm) flags = nullptr;
+        if (ntiles <= 2 * (int64_t)nsm || ntiles > kFlagMaxWaves * 2 * (int64_t)nsm) flags = nullptr;
     }
     if (flags) {
         e = cudaMemsetAsync(flags, 0, (size_t)flow_flag_words(h, w) * sizeof(unsigned int), st);
