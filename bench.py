@@ -62,7 +62,7 @@ DEFAULT_T = 4
 # image, from the ncu capture of one warm-L2 launch of the current kernel summarised in
 # profiles/flow_tile_t4_4096x4096_full.md; reported as roofline.traffic for the default 4 steps
 # per launch and the full 500 iterations only
-TILE_T4_DRAM_BYTES = 88.47e6  # 67.18 MB read + 21.28 MB written
+TILE_T4_DRAM_BYTES = 89.02e6  # 67.19 MB read + 21.83 MB written
 # GB300 HBM3e nominal bandwidth (GB/s); fractions are reported against it and against the
 # measured copy bandwidth
 NOMINAL_HBM_GBS = 8000.0
