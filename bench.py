@@ -658,7 +658,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        ne = max(1, min(args.steps, 3))
+        ne = max(1, min(args.steps, 10))
         for _ in range(ne):
             wmc.denoise_host(fh, LAM, STEP, iters, out=oh, workspace=hws, device=dev)
             st.synchronize()
