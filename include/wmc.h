@@ -173,6 +173,21 @@ wmc_status_t wmc_selftest_wait_timeout(void *workspace, int64_t limit_ns, wmc_st
  * (wmc_denoise_noalloc_status then returns WMC_ERR_TIMEOUT until the next wmc_denoise_noalloc
  * call clears it).  limit_ns as above.  Errors: WMC_ERR_INVALID_ARG (target, limit_ns),
  * WMC_ERR_CUDA. */
+/* wmc_selftest_flag_timeout: makes the per-tile flag wait of chained flow launches run out,
+ * without a fault.  It runs ONE 4-step flow launch (FP32, lambda 1, step 0.25, replicate
+ * boundary, U^0 = f) whose tiles wait for the flags of a previous launch that never ran: the
+ * flags are cleared and nothing stores the launch number they wait for.  The first tiles give up
+ * after the 0.2 s limit and set the status word; the tiles after them see the word and do not
+ * wait.  The launch then computes its 4 steps from f, so u holds the same bits as wmc_denoise with
+ * iters = 4, while wmc_denoise_status(workspace) reports WMC_ERR_TIMEOUT until the next flow call
+ * on that workspace clears it.
+ *   f, u: device, h x w FP32 images of pitch ld; f's start and pitch 16-byte aligned (TMA).
+ *   workspace: device, >= wmc_denoise_workspace_size(h, w, ld, WMC_F32) bytes, aligned as above.
+ * Errors: WMC_ERR_INVALID_ARG, WMC_ERR_ALIAS, WMC_ERR_WORKSPACE, WMC_ERR_UNSUPPORTED (f not
+ * TMA-readable), WMC_ERR_CUDA. */
+wmc_status_t wmc_selftest_flag_timeout(const void *f, void *u, int32_t h, int32_t w, int64_t ld,
+                                       void *workspace, size_t workspace_bytes, wmc_stream_t stream);
+
 #define WMC_SELFTEST_EVAL 0
 #define WMC_SELFTEST_NOALLOC 1
 wmc_status_t wmc_selftest_status_timeout(int32_t target, int64_t limit_ns, wmc_stream_t stream);

@@ -1479,6 +1479,60 @@ wmc_status_t wmc_selftest_status_timeout(int32_t target, int64_t limit_ns, wmc_s
     return WMC_OK;
 }
 
+wmc_status_t wmc_selftest_flag_timeout(const void *f, void *u, int32_t h, int32_t w, int64_t ld,
+                                       void *workspace, size_t workspace_bytes, wmc_stream_t stream) {
+    g_last_error[0] = 0;
+    int T = 0;
+    wmc_status_t s = check_flow_args(f, nullptr, u, h, w, ld, WMC_F32, 1.0f, 0.25f, 4,
+                                     WMC_BOUNDARY_REPLICATE, nullptr, &T);
+    if (s != WMC_OK) return s;
+    if (h == 0 || w == 0) return fail(WMC_ERR_INVALID_ARG, "empty image");
+    if (!f) return fail(WMC_ERR_INVALID_ARG, "f is NULL");
+    const size_t need = wmc_denoise_workspace_size(h, w, ld, WMC_F32);
+    if (!workspace || workspace_bytes < need)
+        return fail(WMC_ERR_WORKSPACE, "workspace of %zu bytes needed, %zu given", need,
+                    workspace ? workspace_bytes : (size_t)0);
+    if ((uintptr_t)workspace % WMC_WORKSPACE_ALIGN)
+        return fail(WMC_ERR_WORKSPACE, "workspace not %d-byte aligned", WMC_WORKSPACE_ALIGN);
+    const size_t n = span_bytes(h, w, ld, sizeof(float));
+    if (overlap(workspace, need, f, n) || overlap(workspace, need, u, n))
+        return fail(WMC_ERR_ALIAS, "workspace overlaps an image");
+    alignas(64) CUtensorMap maps[2];
+    memset(maps, 0, sizeof maps);
+    if (!encode_window_map(&maps[0], f, WMC_F32, h, w, ld) || !encode_window_map(&maps[1], f, WMC_F32, h, w, ld))
+        return fail(WMC_ERR_UNSUPPORTED, "f must be readable by TMA (16-byte aligned start and pitch)");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int *status = static_cast<unsigned int *>(workspace);
+    unsigned int *flags = flow_flags(workspace, h, w, ld, WMC_F32);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(flags, 0, (size_t)flow_flag_words(h, w) * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "clear status word and tile flags");
+    // the coefficients of wmc_denoise with lambda 1, step 0.25; U^0 = f
+    const float lambda = 1.0f, step = 0.25f;
+    wmc::TileParams tp{};
+    tp.u = f;
+    tp.f = f;
+    tp.out = u;
+    tp.ld = ld;
+    tp.ld_out = ld;
+    tp.h = h;
+    tp.w = w;
+    tp.use_tma = 1;
+    tp.c_keep = 1.0f - step;
+    tp.c_f = step;
+    tp.c_h = step * lambda / 12.0f;
+    tp.status = status;
+    tp.pdl = 0;
+    tp.f_tma = 1;
+    tp.flags = flags;
+    tp.flag_wait = 1;  // a launch number no launch stores
+    tp.flag_set = 1;
+    e = launch_tile(WMC_F32, WMC_BOUNDARY_REPLICATE, kDefaultTile, 4, maps, tp, -1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "flow kernel launch");
+    return WMC_OK;
+}
+
 size_t wmc_backward_workspace_size(int32_t n, int32_t h, int32_t w, int64_t ld, int32_t K,
                                    int32_t ckpt_every) {
     const size_t base = wmc_unrolled_workspace_size(n, h, w, ld, K, ckpt_every);

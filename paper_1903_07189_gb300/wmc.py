@@ -91,6 +91,7 @@ SIGNATURES = {
     "wmc_energy_grad": (_i32, [_vp, _vp, _i32, _i32, _i64, _i32, _vp]),
     "wmc_shard_lpt": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     "wmc_selftest_wait_timeout": (_i32, [_vp, _i64, _vp]),
+    "wmc_selftest_flag_timeout": (_i32, [_vp, _vp, _i32, _i32, _i64, _vp, _sz, _vp]),
     "wmc_eval_status": (_i32, [_vp]),
     "wmc_probe_fma_threads": (_i32, []),
     "wmc_probe_fma": (_i32, [_vp, _i32, _i32, _vp]),
@@ -300,6 +301,19 @@ def selftest_wait_timeout(workspace: torch.Tensor, limit_ns: int = 10_000_000):
 
 
 SELFTEST_TARGETS = {"eval": 0, "noalloc": 1}
+
+
+def selftest_flag_timeout(f: torch.Tensor, out: torch.Tensor, workspace: torch.Tensor):
+    """Make the per-tile flag wait of a chained flow launch run out on purpose
+    (wmc_selftest_flag_timeout): out gets 4 flow steps from f, and check_status(workspace) then
+    raises WMC_ERR_TIMEOUT until the next flow call on that workspace."""
+    p, h, w, ld = _img(f, "f")
+    po, ho, wo, ldo = _img(out, "out")
+    if (ho, wo, ldo) != (h, w, ld) or f.dtype != torch.float32 or out.dtype != torch.float32:
+        raise ValueError("f and out must be FP32 images of one shape and pitch")
+    _check(load().wmc_selftest_flag_timeout(p, po, h, w, ld, workspace.data_ptr(), workspace.numel(),
+                                            _stream(f.device)), "wmc_selftest_flag_timeout")
+    return out
 
 
 def selftest_status_timeout(target: str, limit_ns: int = 10_000_000, device=None):

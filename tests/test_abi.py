@@ -233,6 +233,19 @@ def test_selftest_wait_validation(lib):
     assert lib.wmc_selftest_wait_timeout(ws, 2_000_000_000, None) == INVALID
 
 
+def test_selftest_flag_validation(lib):
+    f, u, ws = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000), ctypes.c_void_p(0x10000000)
+    need = lib.wmc_denoise_workspace_size(8, 8, 8, 0)
+    assert lib.wmc_selftest_flag_timeout(None, u, 8, 8, 8, ws, need, None) == INVALID
+    assert lib.wmc_selftest_flag_timeout(f, None, 8, 8, 8, ws, need, None) == INVALID
+    assert lib.wmc_selftest_flag_timeout(f, u, 0, 8, 8, ws, need, None) == INVALID
+    assert lib.wmc_selftest_flag_timeout(f, u, 8, 8, 4, ws, need, None) == INVALID  # ld < w
+    assert lib.wmc_selftest_flag_timeout(f, f, 8, 8, 8, ws, need, None) == ALIAS
+    assert lib.wmc_selftest_flag_timeout(f, u, 8, 8, 8, ws, need - 1, None) == WORKSPACE
+    assert lib.wmc_selftest_flag_timeout(f, u, 8, 8, 8, ctypes.c_void_p(0x10000004), need, None) == WORKSPACE
+    assert lib.wmc_selftest_flag_timeout(f, u, 8, 8, 8, ctypes.c_void_p(0x100000), 1 << 20, None) == ALIAS
+
+
 def test_selftest_status_validation(lib):
     assert lib.wmc_selftest_status_timeout(0, 0, None) == INVALID
     assert lib.wmc_selftest_status_timeout(1, 2_000_000_000, None) == INVALID

@@ -9,7 +9,9 @@ oracle, Sec. V-B, Eq. MCF).  Covered: 2 to 8 steps per launch, both tile shapes,
 launch of 2 steps (another tile grid: it waits for the whole launch before it) or of 1 step, both
 boundary rules, BF16/FP16 storage, U^0 given in the output buffer, a pitch that is staged through
 the workspace, repeated calls on one workspace (the flags are cleared by every call), and the
-status word (no wait ran out).
+status word (no wait ran out).  And the failure path without a fault: a launch whose tiles wait
+for flags that no launch stores gives up after its time limit, reports WMC_ERR_TIMEOUT through the
+status word, and leaves the context usable.
 """
 import pytest
 import torch
@@ -64,3 +66,18 @@ def test_chained_launches_in_place_and_staged(image):
     f = big[:, :N - 1]
     ref = wmc().denoise(f, 1.0, 0.25, 13, steps_per_launch=1)
     assert torch.equal(wmc().denoise(f, 1.0, 0.25, 13, steps_per_launch=4), ref)
+
+
+def test_flag_wait_that_runs_out_is_reported(image):
+    ws = torch.empty(wmc().load().wmc_denoise_workspace_size(N, N, N, 0), dtype=torch.uint8, device=DEV)
+    out = torch.empty_like(image)
+    wmc().selftest_flag_timeout(image, out, ws)
+    with pytest.raises(wmc().WMCError) as err:
+        wmc().check_status(ws)
+    assert err.value.status == 5  # WMC_ERR_TIMEOUT
+    # the launch went ahead after the wait (its input, f, was ready): 4 steps from f
+    assert torch.equal(out, wmc().denoise(image, 1.0, 0.25, 4))
+    # the next flow call on the workspace clears the word and gives the exact result
+    got = wmc().denoise(image, 1.0, 0.25, 9, workspace=ws)
+    wmc().check_status(ws)
+    assert torch.equal(got, wmc().denoise(image, 1.0, 0.25, 9, steps_per_launch=1))
