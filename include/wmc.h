@@ -115,10 +115,10 @@ wmc_status_t wmc_eval_status(wmc_stream_t stream);
  *   workspace: device, >= wmc_denoise_workspace_size() bytes, WMC_WORKSPACE_ALIGN-aligned,
  *   must not overlap f, u0 or u (not needed when iters == 0).  It holds a status word (first
  *   bytes, cleared by every call), one ping-pong image and one flag word per tile of the
- *   multi-step launches (at the end; a call whose chained launches each span more than one and
- *   at most ten waves of CTAs clears them first and then has a tile wait for the flags of the
- *   tiles of the previous launch that it reads, not for that whole launch; other calls leave
- *   them alone); see wmc_denoise_status().  When the
+ *   multi-step launches (at the end; a call whose chained launches each span more than one
+ *   and at most ten waves of CTAs, a wave being two CTAs per SM, clears them first and has a
+ *   tile wait for the flags of the tiles of the previous launch that it reads, not for that
+ *   whole launch; other calls leave them alone); see wmc_denoise_status().  When the
  *   row pitch is not a multiple of 16 bytes (ld not a multiple of 4 elements for FP32, of 8 for
  *   BF16/FP16) the multi-step kernels cannot read the images through TMA: the workspace then
  *   holds three images of the next aligned pitch, the call copies U^0 and f into two of them,
